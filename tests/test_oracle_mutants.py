@@ -1,0 +1,103 @@
+"""Each pin must catch a plausible mistake: plant one in a copy of the oracle
+source (a dropped term, a wrong sign, index or operand), build that copy, run
+the CPU pin suite against it and require a failure.  Mistakes are planted in
+the oracle only, on the CPU."""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = [os.path.join(ROOT, "tests", f) for f in
+        ("test_oracle_hllc.py", "test_oracle_riemann.py", "test_oracle_scheme.py")]
+
+# (name, original text, planted text)
+MUTANTS = [
+    ("minmod picks the larger slope", "return (a <= b) ? a : b;", "return (a <= b) ? b : a;"),
+    ("left face state sign", "qL[f] = W[1][f] + 0.5 * dqi;", "qL[f] = W[1][f] - 0.5 * dqi;"),
+    ("right face state sign", "qR[f] = W[2][f] - 0.5 * dqi1;", "qR[f] = W[2][f] + 0.5 * dqi1;"),
+    ("right face uses left slope", "qR[f] = W[2][f] - 0.5 * dqi1;", "qR[f] = W[2][f] - 0.5 * dqi;"),
+    ("pressure kinetic sign", "W[4] = (gamma - 1.0) * (U[4] - kin);",
+     "W[4] = (gamma - 1.0) * (U[4] + kin);"),
+    ("kinetic energy drops w", "double kin = 0.5 * rho * (u * u + v * v + w * w);",
+     "double kin = 0.5 * rho * (u * u + v * v);"),
+    ("sound speed without gamma", "double cL = sqrt(gamma * pL / rL);",
+     "double cL = sqrt(pL / rL);"),
+    ("contact speed pressure sign", "(pR - pL + rL", "(pL - pR + rL"),
+    ("contact speed denominator", "/ (rL * (SL - uL) - rR * (SR - uR));",
+     "/ (rL * (SL - uL) + rR * (SR - uR));"),
+    ("star energy sign", "(Sstar + p / (r * (SK - u)))", "(Sstar - p / (r * (SK - u)))"),
+    ("star energy term dropped",
+     "Us[4] = fac * (UK[4] / r + (Sstar - u) * (Sstar + p / (r * (SK - u))));",
+     "Us[4] = fac * (UK[4] / r);"),
+    ("momentum flux without p", "F[1] = rho * un * un + p;", "F[1] = rho * un * un;"),
+    ("energy flux without p", "F[4] = (E + p) * un;", "F[4] = E * un;"),
+    ("face energy drops t2",
+     "double E = p / (gamma - 1.0) + 0.5 * rho * (un * un + t1 * t1 + t2 * t2);",
+     "double E = p / (gamma - 1.0) + 0.5 * rho * (un * un + t1 * t1);"),
+    ("reflect index", "return m < 0 ? -1 - m : 2 * n - 1 - m;",
+     "return m < 0 ? -m : 2 * n - 1 - m;"),
+    ("reflect keeps momentum", "if (flip) out[1 + d] = -out[1 + d];",
+     "if (flip) out[1 + d] = out[1 + d];"),
+    ("periodic wrap off by one", "return r < 0 ? r + n : r;", "return r < 0 ? r + n - 1 : r;"),
+    ("outflow copies the wrong cell", "if (bc == BC_OUTFLOW) return m < 0 ? 0 : n - 1;",
+     "if (bc == BC_OUTFLOW) return m < 0 ? 1 : n - 1;"),
+    ("stage 2 half dt", "Uout[q] = 0.5 * U0[q] + 0.5 * (Ucur[q] + dt * L[q]);",
+     "Uout[q] = 0.5 * U0[q] + 0.5 * (Ucur[q] + 0.5 * dt * L[q]);"),
+    ("stage 2 weights", "Uout[q] = 0.5 * U0[q] + 0.5 * (Ucur[q] + dt * L[q]);",
+     "Uout[q] = 0.25 * U0[q] + 0.75 * (Ucur[q] + dt * L[q]);"),
+    ("divergence uses dx for every axis",
+     "(Ff[f * nfaces + fhi] - Ff[f * nfaces + flo]) / g->dx[d];",
+     "(Ff[f * nfaces + fhi] - Ff[f * nfaces + flo]) / g->dx[0];"),
+    ("y sweep uses the x normal", "{{1, 2, 3}, {2, 1, 3}, {3, 1, 2}}",
+     "{{1, 2, 3}, {1, 2, 3}, {3, 1, 2}}"),
+    ("z sweep uses the y normal", "{{1, 2, 3}, {2, 1, 3}, {3, 1, 2}}",
+     "{{1, 2, 3}, {2, 1, 3}, {2, 1, 3}}"),
+    ("rate without sound speed", "r += (fabs(W[1 + d]) + cs) / g.dx[d];",
+     "r += (fabs(W[1 + d])) / g.dx[d];"),
+    ("rate uses dx for every axis", "r += (fabs(W[1 + d]) + cs) / g.dx[d];",
+     "r += (fabs(W[1 + d]) + cs) / g.dx[0];"),
+    ("face flux shifted by one cell", "c[d] -= 1;                        /* left cell of the face */",
+     ""),
+    ("HLLC side swapped", "double SK = (Sstar >= 0.0) ? SL : SR;",
+     "double SK = (Sstar >= 0.0) ? SR : SL;"),
+    ("Davis bound mixes sides", "double SL = fmin(uL - cL, uR - cR);",
+     "double SL = fmin(uL - cL, uL - cR);"),
+    ("stencil shifted", "fetch_cons(g, U, d, i, j, k, s - 1, Uc);",
+     "fetch_cons(g, U, d, i, j, k, s - 2, Uc);"),
+    ("exact shock density", "W3[0] = rL * (ps / pL + gm) / (gm * ps / pL + 1.0);",
+     "W3[0] = rL * (ps / pL + gm) / (gm * ps / pL - 1.0);"),
+    ("exact fan velocity", "W3[1] = 2.0 / (g + 1.0) * (cL + 0.5 * (g - 1.0) * uL + xi);",
+     "W3[1] = 2.0 / (g + 1.0) * (cL + 0.5 * (g - 1.0) * uL - xi);"),
+    ("exact shock pressure function", "*f = (p - pK) * q;", "*f = (p + pK) * q;"),
+    ("Heun weights", "Unew[q] = Un[q] + dt * (0.5 * k1[q] + 0.5 * k2[q]);",
+     "Unew[q] = Un[q] + dt * (0.5 * k1[q] + 0.5 * k1[q]);"),
+]
+
+
+def _run_mutant(args):
+    idx, (name, old, new), tmp = args
+    src = open(os.path.join(ROOT, "oracle", "hard_oracle.c")).read()
+    assert old in src, f"mutation site of '{name}' not found"
+    cpath = os.path.join(tmp, f"m{idx}.c")
+    with open(cpath, "w") as fh:
+        fh.write(src.replace(old, new, 1))
+    so = oracle.compile_oracle(cpath, os.path.join(tmp, f"m{idx}.so"))
+    env = dict(os.environ, HARD_ORACLE_LIB=so, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider"],
+                       env=env, capture_output=True, text=True, cwd=ROOT)
+    return name, r.returncode
+
+
+def test_every_planted_mistake_is_caught(tmp_path):
+    if os.environ.get("HARD_ORACLE_LIB"):
+        pytest.skip("already running against a planted copy")
+    jobs = [(i, m, str(tmp_path)) for i, m in enumerate(MUTANTS)]
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(_run_mutant, jobs))
+    survivors = [name for name, rc in results if rc == 0]
+    assert not survivors, f"pins did not catch: {survivors}"
