@@ -1,0 +1,146 @@
+/*
+ * hard_hydro.h -- C ABI of the GB300 (sm_103a) explicit finite-volume hydro
+ * stage update.
+ *
+ * The library advances the ideal-gas Euler equations, the hydrodynamic rows of
+ * the conservation law of the HARD paper (arXiv 2509.08971), Eq. "conservative
+ * form" with S = 0 and the fluxes of Eq. "fluxes":
+ *     d_t U + d_j F^j = 0,   U = [rho, rho v^i, e + rho v^2/2],  p = (gamma-1) e,
+ * on a uniform Cartesian mesh of cell-centred values (Sec. 2.2.2).  One stage
+ * is the fused chain
+ *     ghost fill -> conserved-to-primitive -> minmod-limited piecewise-linear
+ *     face states -> HLLC face flux -> flux difference (F*_{i+1/2}-F*_{i-1/2})/dx
+ *     -> Runge-Kutta stage combine,
+ * and a step is the two stages of Heun's method (Table "Butcher tableau for
+ * Heun's method"), evaluated in Shu-Osher form:
+ *     U1 = Un + dt L(Un),   U^{n+1} = Un/2 + (U1 + dt L(U1))/2.
+ * The time step is dt = cfl / max_cells sum_d (|v_d| + c)/dx_d, c = sqrt(gamma p/rho).
+ *
+ * Conventions shared by every call
+ *   Layout    U is a structure of arrays U[5][nz][ny][nx], x fastest, fields
+ *             (rho, rho*u, rho*v, rho*w, E_total), contiguous, element type
+ *             float (HARD_F32) or double (HARD_F64) as set on the handle.
+ *             Ghost cells are not stored.  An axis with one cell is inactive.
+ *   Memory    U pointers are DEVICE pointers owned by the caller (e.g. torch
+ *             tensors), 16-byte aligned, unless the name says _host.  The
+ *             handle owns its scratch (the intermediate stage U1, reduction
+ *             slots, the status flag) and frees it in hard_hydro_destroy.
+ *   Streams   `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *             default stream).  Calls are asynchronous on it unless stated.
+ *   Errors    Every int-returning call returns HARD_OK (0) or a negative
+ *             HARD_E* code and never aborts, exits or traps.  Argument errors
+ *             are returned at once.  A non-physical state met on the device
+ *             (rho <= 0, p <= 0 or NaN) raises a device flag that the next
+ *             synchronising call (cfl_dt, totals, *_host) returns as
+ *             HARD_ENONPHYS, or that hard_hydro_get_error reads and clears.
+ *   Threads   A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef HARD_HYDRO_H
+#define HARD_HYDRO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hard_hydro_s* hard_hydro_t;
+
+/* boundary kinds (per face): periodic wrap, outflow (zero gradient: the two
+ * ghost layers repeat the edge cell), reflecting wall (mirror image with the
+ * normal momentum negated) */
+enum { HARD_BC_PERIODIC = 0, HARD_BC_OUTFLOW = 1, HARD_BC_REFLECT = 2 };
+
+/* element type of U */
+enum { HARD_F32 = 0, HARD_F64 = 1 };
+
+/* stage kernel variant: TMA-staged fused z-march, or the same kernel fed by
+ * plain per-thread loads */
+enum { HARD_KERNEL_FUSED = 0, HARD_KERNEL_PLAIN = 1 };
+
+enum {
+    HARD_OK = 0,
+    HARD_EINVAL = -1,        /* bad argument                                  */
+    HARD_ENOMEM = -2,        /* device allocation failed                      */
+    HARD_ECUDA = -3,         /* a CUDA runtime call failed                    */
+    HARD_ENONPHYS = -4,      /* non-physical state met on the device          */
+    HARD_ETIMEOUT = -5,      /* a bounded device wait ran out                 */
+    HARD_EUNSUPPORTED = -6   /* valid request this build does not support     */
+};
+
+/* Create a handle for an nx x ny x nz mesh (each >= 1) on the unit box with
+ * ratio of specific heats gamma > 1 and the boundary kind `bc` on all six
+ * faces.  Defaults: HARD_F32, HARD_KERNEL_FUSED.  Allocates nothing on the
+ * device yet.  Returns NULL on a bad argument or host allocation failure. */
+hard_hydro_t hard_hydro_create(int nx, int ny, int nz, double gamma, int bc);
+
+/* Set the element type, the domain extents (cell width = extent / cells) and
+ * the boundary kind of each face, ordered x-, x+, y-, y+, z-, z+ (NULL keeps
+ * the current kinds).  Periodic must be set on both faces of an axis or on
+ * neither.  Frees scratch of a previous element type. */
+int hard_hydro_set(hard_hydro_t h, int dtype, double lx, double ly, double lz,
+                   const int bc_per_face[6]);
+
+/* Choose the stage kernel variant and tile configuration (tile < 0 picks the
+ * built-in default).  Tile ids index a table that depends on the number of
+ * active axes of the handle's mesh: hard_hydro_tile_count returns its size
+ * (or a negative error code) and hard_hydro_tile_info writes
+ * {tile_x, tile_y, z_chunk, threads_per_block} of one entry. */
+int hard_hydro_set_kernel(hard_hydro_t h, int kernel, int tile);
+int hard_hydro_tile_count(hard_hydro_t h);
+int hard_hydro_tile_info(hard_hydro_t h, int tile, int out4[4]);
+
+/* One Runge-Kutta stage (Sec. 2.2.2 flux difference, Heun tableau):
+ *   stage 1: Uout = Ucur + dt L(Ucur)                       (U0 ignored)
+ *   stage 2: Uout = U0/2 + (Ucur + dt L(Ucur))/2
+ * Uout must not alias Ucur; it may alias U0. */
+int hard_hydro_stage(hard_hydro_t h, int stage, const void* U0, const void* Ucur, void* Uout,
+                     double dt, void* stream);
+
+/* One full step (both stages) with a fixed dt > 0.  U_out may alias U_in.
+ * The intermediate stage lives in handle-owned scratch. */
+int hard_hydro_step(hard_hydro_t h, const void* U_in, void* U_out, double dt, void* stream);
+
+/* CFL time step of U: dt = cfl / max_cells sum_d (|v_d| + c)/dx_d.  Computed
+ * in the element type, returned in double.  _host synchronises the stream and
+ * writes *dt_host; _dev writes the double at device address dt_dev and does
+ * not synchronise. */
+int hard_hydro_cfl_dt(hard_hydro_t h, const void* U, double cfl, double* dt_host, void* stream);
+int hard_hydro_cfl_dt_dev(hard_hydro_t h, const void* U, double cfl, double* dt_dev, void* stream);
+
+/* Device-resident time loop, in place on U: nsteps steps, each with
+ * dt = cfl / r(U^n) clipped so that t + dt <= t_end when t_end > 0 (steps
+ * after t reaches t_end leave U unchanged).  The signal rate of U^{n+1} is
+ * reduced in the epilogue of each step's second stage, so a step reads the
+ * state once per stage.  t_dev is a device double (read as the start time,
+ * advanced in place, FP64); it may be NULL when t_end == 0 (then t starts at
+ * 0 in handle scratch).  dt_log_dev, if not NULL, is a device array of nsteps
+ * doubles receiving each dt.  totals_log_dev, if not NULL, is a device array
+ * of 5*nsteps doubles receiving the conserved totals of U^{n+1} after each
+ * step, summed in FP64 in the second stage's epilogue.  Asynchronous. */
+int hard_hydro_advance(hard_hydro_t h, void* U, int nsteps, double cfl, double t_end,
+                       double* t_dev, double* dt_log_dev, double* totals_log_dev, void* stream);
+
+/* The same loop from and to HOST memory: copies U_host_in to a handle-owned
+ * device buffer, advances, copies the result to U_host_out (may alias) and
+ * writes the final time to *t_host (read as the start time).  Synchronises
+ * the stream.  Pinned host memory gives the full copy bandwidth. */
+int hard_hydro_advance_host(hard_hydro_t h, const void* U_host_in, void* U_host_out, int nsteps,
+                            double cfl, double t_end, double* t_host, void* stream);
+
+/* Conserved totals sum_cells U_f dV for the 5 fields, summed in FP64 from the
+ * warp level up in a fixed order (deterministic).  Synchronises the stream. */
+int hard_hydro_totals(hard_hydro_t h, const void* U, double out5[5], void* stream);
+
+/* Device status flag: returns HARD_OK or HARD_ENONPHYS and clears the flag.
+ * Synchronises the handle's last stream. */
+int hard_hydro_get_error(hard_hydro_t h);
+
+/* Static description of an error code. */
+const char* hard_hydro_strerror(int code);
+
+void hard_hydro_destroy(hard_hydro_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HARD_HYDRO_H */

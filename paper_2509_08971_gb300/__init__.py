@@ -1,0 +1,259 @@
+"""GB300 (sm_103a) explicit finite-volume hydro stage update.
+
+Thin Python binding of the C ABI in ``include/hard_hydro.h``: the functions
+below carry the C names and only marshal arguments; every step of the update
+runs in ``libhard_hydro.so`` (built in-tree by :mod:`.build`).  There is no
+CPU fallback: without the library every call raises.
+
+``HardHydro`` wraps a handle for torch tensors of shape (5, nz, ny, nx) on the
+current CUDA device and stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhard_hydro.so")
+
+HARD_BC_PERIODIC, HARD_BC_OUTFLOW, HARD_BC_REFLECT = 0, 1, 2
+HARD_F32, HARD_F64 = 0, 1
+HARD_KERNEL_FUSED, HARD_KERNEL_PLAIN = 0, 1
+HARD_OK, HARD_EINVAL, HARD_ENOMEM, HARD_ECUDA = 0, -1, -2, -3
+HARD_ENONPHYS, HARD_ETIMEOUT, HARD_EUNSUPPORTED = -4, -5, -6
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class HardHydroError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = hard_hydro_strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+def _declare(lib):
+    sig = {
+        "hard_hydro_create": (_vp, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int]),
+        "hard_hydro_set": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, _ip]),
+        "hard_hydro_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+        "hard_hydro_tile_count": (ctypes.c_int, [_vp]),
+        "hard_hydro_tile_info": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
+        "hard_hydro_stage": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double,
+                                            _vp]),
+        "hard_hydro_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
+        "hard_hydro_cfl_dt": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _dp, _vp]),
+        "hard_hydro_cfl_dt_dev": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
+        "hard_hydro_advance": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_double, _vp, _vp, _vp, _vp]),
+        "hard_hydro_advance_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
+                                                   ctypes.c_double, _dp, _vp]),
+        "hard_hydro_totals": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
+        "hard_hydro_get_error": (ctypes.c_int, [_vp]),
+        "hard_hydro_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "hard_hydro_destroy": (None, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def lib():
+    """The loaded CUDA library.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with paper_2509_08971_gb300.build.build() "
+                "(nvcc, sm_103a); there is no CPU fallback")
+        _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+# ---- C names, argument marshalling only ------------------------------------
+
+def hard_hydro_create(nx, ny, nz, gamma, bc):
+    return lib().hard_hydro_create(int(nx), int(ny), int(nz), float(gamma), int(bc))
+
+
+def hard_hydro_set(h, dtype, lx, ly, lz, bc_per_face=None):
+    arr = None if bc_per_face is None else (ctypes.c_int * 6)(*[int(b) for b in bc_per_face])
+    return lib().hard_hydro_set(h, int(dtype), float(lx), float(ly), float(lz), arr)
+
+
+def hard_hydro_set_kernel(h, kernel, tile):
+    return lib().hard_hydro_set_kernel(h, int(kernel), int(tile))
+
+
+def hard_hydro_tile_count(h):
+    return lib().hard_hydro_tile_count(h)
+
+
+def hard_hydro_tile_info(h, tile):
+    out = (ctypes.c_int * 4)()
+    rc = lib().hard_hydro_tile_info(h, int(tile), out)
+    return rc, tuple(out)
+
+
+def hard_hydro_stage(h, stage, U0, Ucur, Uout, dt, stream):
+    return lib().hard_hydro_stage(h, int(stage), U0, Ucur, Uout, float(dt), stream)
+
+
+def hard_hydro_step(h, U_in, U_out, dt, stream):
+    return lib().hard_hydro_step(h, U_in, U_out, float(dt), stream)
+
+
+def hard_hydro_cfl_dt(h, U, cfl, stream):
+    dt = ctypes.c_double(0.0)
+    rc = lib().hard_hydro_cfl_dt(h, U, float(cfl), ctypes.byref(dt), stream)
+    return rc, dt.value
+
+
+def hard_hydro_cfl_dt_dev(h, U, cfl, dt_dev, stream):
+    return lib().hard_hydro_cfl_dt_dev(h, U, float(cfl), dt_dev, stream)
+
+
+def hard_hydro_advance(h, U, nsteps, cfl, t_end, t_dev, dt_log_dev, totals_log_dev, stream):
+    return lib().hard_hydro_advance(h, U, int(nsteps), float(cfl), float(t_end), t_dev,
+                                    dt_log_dev, totals_log_dev, stream)
+
+
+def hard_hydro_advance_host(h, U_host_in, U_host_out, nsteps, cfl, t_end, t_host, stream):
+    t = ctypes.c_double(float(t_host))
+    rc = lib().hard_hydro_advance_host(h, U_host_in, U_host_out, int(nsteps), float(cfl),
+                                       float(t_end), ctypes.byref(t), stream)
+    return rc, t.value
+
+
+def hard_hydro_totals(h, U, stream):
+    out = (ctypes.c_double * 5)()
+    rc = lib().hard_hydro_totals(h, U, out, stream)
+    return rc, list(out)
+
+
+def hard_hydro_get_error(h):
+    return lib().hard_hydro_get_error(h)
+
+
+def hard_hydro_strerror(code):
+    return lib().hard_hydro_strerror(int(code)).decode()
+
+
+def hard_hydro_destroy(h):
+    if h:
+        lib().hard_hydro_destroy(h)
+
+
+def check(rc, what=""):
+    if rc != HARD_OK:
+        raise HardHydroError(rc, what)
+    return rc
+
+
+# ---- torch convenience ----------------------------------------------------
+
+class HardHydro:
+    """A mesh handle bound to torch tensors U of shape (5, nz, ny, nx)."""
+
+    def __init__(self, shape, gamma, bc=HARD_BC_PERIODIC, dtype=None, extent=(1.0, 1.0, 1.0),
+                 kernel=HARD_KERNEL_FUSED, tile=-1):
+        import torch
+        self.torch = torch
+        nz, ny, nx = (int(s) for s in shape)
+        self.shape = (nz, ny, nx)
+        self.gamma = float(gamma)
+        self.dtype = dtype or torch.float32
+        if self.dtype not in (torch.float32, torch.float64):
+            raise ValueError("dtype must be torch.float32 or torch.float64")
+        bc6 = [bc] * 6 if isinstance(bc, int) else list(bc)
+        self.h = hard_hydro_create(nx, ny, nz, gamma, bc6[0])
+        if not self.h:
+            raise HardHydroError(HARD_EINVAL, "hard_hydro_create")
+        check(hard_hydro_set(self.h, HARD_F64 if self.dtype == torch.float64 else HARD_F32,
+                             *extent, bc6), "hard_hydro_set")
+        check(hard_hydro_set_kernel(self.h, kernel, tile), "hard_hydro_set_kernel")
+
+    def __del__(self):
+        h, self.h = getattr(self, "h", None), None
+        if h and _lib is not None:
+            hard_hydro_destroy(h)
+
+    def set_kernel(self, kernel, tile=-1):
+        check(hard_hydro_set_kernel(self.h, kernel, tile), "hard_hydro_set_kernel")
+
+    def tile_count(self):
+        return hard_hydro_tile_count(self.h)
+
+    def tile_info(self, tile):
+        rc, info = hard_hydro_tile_info(self.h, tile)
+        check(rc, "hard_hydro_tile_info")
+        return info
+
+    def _stream(self):
+        return self.torch.cuda.current_stream().cuda_stream
+
+    def _check(self, U):
+        if not (U.is_cuda and U.is_contiguous() and U.dtype == self.dtype
+                and tuple(U.shape) == (5, *self.shape)):
+            raise ValueError(f"U must be a contiguous CUDA {self.dtype} tensor of shape "
+                             f"{(5, *self.shape)}, got {tuple(U.shape)} {U.dtype} {U.device}")
+        return U.data_ptr()
+
+    def empty(self):
+        return self.torch.empty((5, *self.shape), dtype=self.dtype, device="cuda")
+
+    def stage(self, stage, U0, Ucur, dt, out=None):
+        out = self.empty() if out is None else out
+        p0 = self._check(U0) if U0 is not None else None
+        check(hard_hydro_stage(self.h, stage, p0, self._check(Ucur), self._check(out), dt,
+                               self._stream()), "hard_hydro_stage")
+        return out
+
+    def step(self, U, dt, out=None):
+        out = self.empty() if out is None else out
+        check(hard_hydro_step(self.h, self._check(U), self._check(out), dt, self._stream()),
+              "hard_hydro_step")
+        return out
+
+    def cfl_dt(self, U, cfl):
+        rc, dt = hard_hydro_cfl_dt(self.h, self._check(U), cfl, self._stream())
+        check(rc, "hard_hydro_cfl_dt")
+        return dt
+
+    def advance(self, U, nsteps, cfl, t_end=0.0, t=None, log_dt=False, log_totals=False):
+        """In place on U.  Returns (t_tensor, dt_log or None, totals_log or None),
+        all device tensors (float64)."""
+        torch = self.torch
+        if t is None:
+            t = torch.zeros((), dtype=torch.float64, device=U.device)
+        dtl = torch.zeros(max(nsteps, 1), dtype=torch.float64, device=U.device) if log_dt else None
+        tl = (torch.zeros((max(nsteps, 1), 5), dtype=torch.float64, device=U.device)
+              if log_totals else None)
+        check(hard_hydro_advance(self.h, self._check(U), nsteps, cfl, t_end, t.data_ptr(),
+                                 dtl.data_ptr() if dtl is not None else None,
+                                 tl.data_ptr() if tl is not None else None, self._stream()),
+              "hard_hydro_advance")
+        return t, dtl, tl
+
+    def advance_host(self, U_host, nsteps, cfl, t_end=0.0, t0=0.0, out=None):
+        """U_host: a contiguous host torch tensor (pinned for full bandwidth)."""
+        out = U_host if out is None else out
+        rc, t = hard_hydro_advance_host(self.h, U_host.data_ptr(), out.data_ptr(), nsteps, cfl,
+                                        t_end, t0, self._stream())
+        check(rc, "hard_hydro_advance_host")
+        return out, t
+
+    def totals(self, U):
+        rc, out = hard_hydro_totals(self.h, self._check(U), self._stream())
+        check(rc, "hard_hydro_totals")
+        return out
+
+    def get_error(self):
+        return hard_hydro_get_error(self.h)

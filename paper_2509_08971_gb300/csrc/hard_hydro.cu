@@ -1,0 +1,481 @@
+// C ABI of the hydro stage update: handles, argument checks, scratch
+// ownership, the device-resident time loop and the small finalize kernels.
+// The declarations and their contracts are in include/hard_hydro.h.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "hard_hydro.h"
+#include "launch.h"
+
+using hh::MeshDesc;
+using hh::StageCall;
+
+struct hard_hydro_s {
+    int n[3];
+    double gamma;
+    int bc[6];
+    double ext[3];
+    int dtype = HARD_F32;
+    int kernel = HARD_KERNEL_FUSED;
+    int tile = -1;
+    MeshDesc mesh;
+    // device scratch, allocated on first use
+    void* U1 = nullptr;              // intermediate stage
+    size_t U1_bytes = 0;
+    void* Udev = nullptr;            // state buffer of advance_host
+    size_t Udev_bytes = 0;
+    unsigned char* slots = nullptr;  // rate | dt | t | status | totals[5]
+    double* tot_partial = nullptr;
+    long long tot_rows = 0;
+    cudaStream_t last = nullptr;
+};
+
+namespace {
+
+constexpr size_t SLOT_RATE = 0, SLOT_DT = 8, SLOT_T = 16, SLOT_STATUS = 24, SLOT_TOT = 32;
+constexpr size_t SLOT_BYTES = 128;
+
+int from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return HARD_OK;
+    if (e == cudaErrorMemoryAllocation) return HARD_ENOMEM;
+    return HARD_ECUDA;
+}
+
+bool alloc_fail_injected() {
+    const char* v = std::getenv("HARD_HYDRO_FAIL_ALLOC");
+    return v && v[0] == '1';
+}
+
+int dev_alloc(void** p, size_t bytes) {
+    if (alloc_fail_injected()) return HARD_ENOMEM;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    return HARD_OK;
+}
+
+size_t elem_size(const hard_hydro_s* h) { return h->dtype == HARD_F64 ? 8 : 4; }
+size_t state_bytes(const hard_hydro_s* h) { return 5 * (size_t)h->mesh.N * elem_size(h); }
+
+bool valid_bc(int b) { return b == HARD_BC_PERIODIC || b == HARD_BC_OUTFLOW || b == HARD_BC_REFLECT; }
+
+// Active axes become kernel axes in order; see launch.h.
+void build_mesh(hard_hydro_s* h) {
+    MeshDesc& m = h->mesh;
+    int a = 0;
+    for (int d = 0; d < 3; ++d) {
+        m.dx[d] = h->ext[d] / h->n[d];
+        m.act[d] = h->n[d] > 1;
+    }
+    m.px = 0;
+    m.py = 1;
+    for (int k = 0; k < 3; ++k) {
+        m.n[k] = 1;
+        m.bc_lo[k] = m.bc_hi[k] = HARD_BC_PERIODIC;
+        m.dxk[k] = 1.0;
+    }
+    for (int d = 0; d < 3; ++d) {
+        if (!m.act[d]) continue;
+        m.n[a] = h->n[d];
+        m.bc_lo[a] = h->bc[2 * d];
+        m.bc_hi[a] = h->bc[2 * d + 1];
+        m.dxk[a] = m.dx[d];
+        if (a == 0) m.px = d;
+        if (a == 1) m.py = d;
+        ++a;
+    }
+    m.dim = a;
+    m.gamma = h->gamma;
+    m.N = (long long)h->n[0] * h->n[1] * h->n[2];
+}
+
+void free_scratch(hard_hydro_s* h) {
+    if (h->U1) cudaFree(h->U1);
+    if (h->Udev) cudaFree(h->Udev);
+    if (h->tot_partial) cudaFree(h->tot_partial);
+    h->U1 = h->Udev = nullptr;
+    h->tot_partial = nullptr;
+    h->U1_bytes = h->Udev_bytes = 0;
+    h->tot_rows = 0;
+}
+
+int ensure_slots(hard_hydro_s* h) {
+    if (h->slots) return HARD_OK;
+    int rc = dev_alloc(reinterpret_cast<void**>(&h->slots), SLOT_BYTES);
+    if (rc) return rc;
+    return from_cuda(cudaMemset(h->slots, 0, SLOT_BYTES));
+}
+
+int ensure_U1(hard_hydro_s* h) {
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    size_t need = state_bytes(h);
+    if (h->U1 && h->U1_bytes >= need) return HARD_OK;
+    if (h->U1) cudaFree(h->U1);
+    h->U1 = nullptr;
+    h->U1_bytes = 0;
+    rc = dev_alloc(&h->U1, need);
+    if (rc) return rc;
+    h->U1_bytes = need;
+    return HARD_OK;
+}
+
+int ensure_partial(hard_hydro_s* h, long long rows) {
+    if (h->tot_partial && h->tot_rows >= rows) return HARD_OK;
+    if (h->tot_partial) cudaFree(h->tot_partial);
+    h->tot_partial = nullptr;
+    h->tot_rows = 0;
+    int rc = dev_alloc(reinterpret_cast<void**>(&h->tot_partial), (size_t)rows * 5 * sizeof(double));
+    if (rc) return rc;
+    h->tot_rows = rows;
+    return HARD_OK;
+}
+
+unsigned long long* rate_slot(hard_hydro_s* h) {
+    return reinterpret_cast<unsigned long long*>(h->slots + SLOT_RATE);
+}
+double* dt_slot(hard_hydro_s* h) { return reinterpret_cast<double*>(h->slots + SLOT_DT); }
+double* t_slot(hard_hydro_s* h) { return reinterpret_cast<double*>(h->slots + SLOT_T); }
+int* status_slot(hard_hydro_s* h) { return reinterpret_cast<int*>(h->slots + SLOT_STATUS); }
+double* tot_slot(hard_hydro_s* h) { return reinterpret_cast<double*>(h->slots + SLOT_TOT); }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int tile_of(const hard_hydro_s* h) { return h->tile < 0 ? 0 : h->tile; }
+
+cudaError_t stage_launch(hard_hydro_s* h, const StageCall& c, cudaStream_t s) {
+    if (h->dtype == HARD_F64) return hh::launch_stage_f64(h->mesh, h->kernel, tile_of(h), c, s);
+    return hh::launch_stage_f32(h->mesh, h->kernel, tile_of(h), c, s);
+}
+
+cudaError_t rate_launch(hard_hydro_s* h, const void* U, cudaStream_t s) {
+    if (h->dtype == HARD_F64) return hh::launch_rate_f64(h->mesh, U, rate_slot(h), status_slot(h), s);
+    return hh::launch_rate_f32(h->mesh, U, rate_slot(h), status_slot(h), s);
+}
+
+int read_status(hard_hydro_s* h, cudaStream_t s) {
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, status_slot(h), sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (st) {
+        e = cudaMemsetAsync(status_slot(h), 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return from_cuda(e);
+        return HARD_ENONPHYS;
+    }
+    return HARD_OK;
+}
+
+// ---- finalize kernels ----
+
+__global__ void finalize_dt_kernel(unsigned long long* slot, double cfl, double t_end, double* t,
+                                   double* dt_out, double* dt_log, int step, int* status) {
+    const double r = __longlong_as_double((long long)*slot);
+    *slot = 0ull;                                  // ready for this step's stage-2 epilogue
+    double dt;
+    if (!(r > 0.0) || isinf(r)) {                  // NaN, zero or infinite rate
+        dt = 0.0;
+        atomicOr(status, 2);
+    } else {
+        dt = cfl / r;
+        if (t && t_end > 0.0) {
+            const double tc = *t;
+            if (tc >= t_end) dt = 0.0;
+            else if (tc + dt > t_end) dt = t_end - tc;
+        }
+    }
+    if (t) *t = *t + dt;
+    *dt_out = dt;
+    if (dt_log) dt_log[step] = dt;
+}
+
+// Fixed-order sum of the per-block partials: warp f sums field f, lane l the
+// rows l, l+32, ..., then a fixed xor tree.  Deterministic for a fixed grid.
+__global__ void finalize_totals_kernel(const double* partial, long long rows, double dV,
+                                       double* out5) {
+    const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (f >= 5) return;
+    double s = 0.0;
+    for (long long r = lane; r < rows; r += 32) s += partial[r * 5 + f];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out5[f] = s * dV;
+}
+
+}  // namespace
+
+namespace hh {
+
+cudaError_t launch_finalize_dt(unsigned long long* rs, double cfl, double t_end, double* t_dev,
+                               double* dt_dev, double* dt_log, int step, int* status,
+                               cudaStream_t s) {
+    finalize_dt_kernel<<<1, 1, 0, s>>>(rs, cfl, t_end, t_dev, dt_dev, dt_log, step, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_totals(const double* partial, long long rows, double dV, double* out5,
+                                   cudaStream_t s) {
+    finalize_totals_kernel<<<1, 160, 0, s>>>(partial, rows, dV, out5);
+    return cudaGetLastError();
+}
+
+}  // namespace hh
+
+// ============================================================== C ABI ====
+
+extern "C" {
+
+hard_hydro_t hard_hydro_create(int nx, int ny, int nz, double gamma, int bc) {
+    if (nx < 1 || ny < 1 || nz < 1) return nullptr;
+    if (!(gamma > 1.0) || !std::isfinite(gamma)) return nullptr;
+    if (!valid_bc(bc)) return nullptr;
+    if ((long long)nx * ny * nz > (1ll << 40)) return nullptr;
+    hard_hydro_s* h = new (std::nothrow) hard_hydro_s();
+    if (!h) return nullptr;
+    h->n[0] = nx; h->n[1] = ny; h->n[2] = nz;
+    h->gamma = gamma;
+    for (int f = 0; f < 6; ++f) h->bc[f] = bc;
+    h->ext[0] = h->ext[1] = h->ext[2] = 1.0;
+    build_mesh(h);
+    return h;
+}
+
+int hard_hydro_set(hard_hydro_t h, int dtype, double lx, double ly, double lz,
+                   const int bc_per_face[6]) {
+    if (!h) return HARD_EINVAL;
+    if (dtype != HARD_F32 && dtype != HARD_F64) return HARD_EINVAL;
+    const double e[3] = {lx, ly, lz};
+    for (int d = 0; d < 3; ++d)
+        if (!(e[d] > 0.0) || !std::isfinite(e[d])) return HARD_EINVAL;
+    int bc[6];
+    for (int f = 0; f < 6; ++f) bc[f] = bc_per_face ? bc_per_face[f] : h->bc[f];
+    for (int f = 0; f < 6; ++f)
+        if (!valid_bc(bc[f])) return HARD_EINVAL;
+    for (int d = 0; d < 3; ++d)
+        if ((bc[2 * d] == HARD_BC_PERIODIC) != (bc[2 * d + 1] == HARD_BC_PERIODIC))
+            return HARD_EINVAL;
+    if (dtype != h->dtype) free_scratch(h);
+    h->dtype = dtype;
+    for (int d = 0; d < 3; ++d) h->ext[d] = e[d];
+    for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
+    build_mesh(h);
+    return HARD_OK;
+}
+
+int hard_hydro_set_kernel(hard_hydro_t h, int kernel, int tile) {
+    if (!h) return HARD_EINVAL;
+    if (kernel != HARD_KERNEL_FUSED && kernel != HARD_KERNEL_PLAIN) return HARD_EINVAL;
+    if (tile >= hh::tile_count(h->mesh.dim)) return HARD_EINVAL;
+    h->kernel = kernel;
+    h->tile = tile;
+    return HARD_OK;
+}
+
+int hard_hydro_tile_count(hard_hydro_t h) {
+    if (!h) return HARD_EINVAL;
+    return hh::tile_count(h->mesh.dim);
+}
+
+int hard_hydro_tile_info(hard_hydro_t h, int tile, int out4[4]) {
+    if (!h || !out4 || tile < 0 || tile >= hh::tile_count(h->mesh.dim)) return HARD_EINVAL;
+    hh::TileDesc t = hh::tile_desc(h->mesh.dim, tile);
+    out4[0] = t.tx;
+    out4[1] = t.ty;
+    out4[2] = t.zc;
+    out4[3] = t.tx * t.ty;
+    return HARD_OK;
+}
+
+int hard_hydro_stage(hard_hydro_t h, int stage, const void* U0, const void* Ucur, void* Uout,
+                     double dt, void* stream) {
+    if (!h || (stage != 1 && stage != 2)) return HARD_EINVAL;
+    if (!Ucur || !Uout || (stage == 2 && !U0)) return HARD_EINVAL;
+    if (!aligned16(Ucur) || !aligned16(Uout) || (stage == 2 && !aligned16(U0))) return HARD_EINVAL;
+    if (Uout == Ucur) return HARD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    StageCall c{stage, U0, Ucur, Uout, dt, nullptr, nullptr, nullptr, status_slot(h)};
+    return from_cuda(stage_launch(h, c, s));
+}
+
+int hard_hydro_step(hard_hydro_t h, const void* U_in, void* U_out, double dt, void* stream) {
+    if (!h || !U_in || !U_out) return HARD_EINVAL;
+    if (!aligned16(U_in) || !aligned16(U_out)) return HARD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    int rc = ensure_U1(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    StageCall c1{1, U_in, U_in, h->U1, dt, nullptr, nullptr, nullptr, status_slot(h)};
+    cudaError_t e = stage_launch(h, c1, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    StageCall c2{2, U_in, h->U1, U_out, dt, nullptr, nullptr, nullptr, status_slot(h)};
+    return from_cuda(stage_launch(h, c2, s));
+}
+
+static int cfl_common(hard_hydro_t h, const void* U, double cfl, cudaStream_t s) {
+    if (!h || !U || !aligned16(U)) return HARD_EINVAL;
+    if (!(cfl > 0.0) || !std::isfinite(cfl)) return HARD_EINVAL;
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    h->last = s;
+    cudaError_t e = cudaMemsetAsync(rate_slot(h), 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = rate_launch(h, U, s);
+    if (e == cudaSuccess)
+        e = hh::launch_finalize_dt(rate_slot(h), cfl, 0.0, nullptr, dt_slot(h), nullptr, 0,
+                                   status_slot(h), s);
+    return from_cuda(e);
+}
+
+int hard_hydro_cfl_dt(hard_hydro_t h, const void* U, double cfl, double* dt_host, void* stream) {
+    if (!dt_host) return HARD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = cfl_common(h, U, cfl, s);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(dt_host, dt_slot(h), sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return read_status(h, s);
+}
+
+int hard_hydro_cfl_dt_dev(hard_hydro_t h, const void* U, double cfl, double* dt_dev, void* stream) {
+    if (!dt_dev) return HARD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = cfl_common(h, U, cfl, s);
+    if (rc) return rc;
+    return from_cuda(cudaMemcpyAsync(dt_dev, dt_slot(h), sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+
+int hard_hydro_advance(hard_hydro_t h, void* U, int nsteps, double cfl, double t_end,
+                       double* t_dev, double* dt_log_dev, double* totals_log_dev, void* stream) {
+    if (!h || !U || !aligned16(U) || nsteps < 0) return HARD_EINVAL;
+    if (!(cfl > 0.0) || !std::isfinite(cfl) || !(t_end >= 0.0) || !std::isfinite(t_end))
+        return HARD_EINVAL;
+    if (t_end > 0.0 && !t_dev) return HARD_EINVAL;
+    int rc = ensure_U1(h);
+    if (rc) return rc;
+    const long long rows = hh::stage_blocks(h->mesh, tile_of(h));
+    if (totals_log_dev) {
+        rc = ensure_partial(h, rows);
+        if (rc) return rc;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    double* t = t_dev;
+    cudaError_t e = cudaSuccess;
+    if (!t) {
+        t = t_slot(h);
+        e = cudaMemsetAsync(t, 0, sizeof(double), s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(rate_slot(h), 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = rate_launch(h, U, s);
+    const double dV = h->mesh.dx[0] * h->mesh.dx[1] * h->mesh.dx[2];
+    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+        e = hh::launch_finalize_dt(rate_slot(h), cfl, t_end, t, dt_slot(h), dt_log_dev, step,
+                                   status_slot(h), s);
+        if (e != cudaSuccess) break;
+        StageCall c1{1, U, U, h->U1, 0.0, dt_slot(h), nullptr, nullptr, status_slot(h)};
+        e = stage_launch(h, c1, s);
+        if (e != cudaSuccess) break;
+        double* part = (totals_log_dev && h->mesh.dim > 0) ? h->tot_partial : nullptr;
+        StageCall c2{2, U, h->U1, U, 0.0, dt_slot(h), rate_slot(h), part, status_slot(h)};
+        e = stage_launch(h, c2, s);
+        if (e != cudaSuccess || !totals_log_dev) continue;
+        if (!part) {
+            // no active axis: the stage kernel has no totals epilogue
+            rc = ensure_partial(h, hh::totals_blocks());
+            if (rc) return rc;
+            e = h->dtype == HARD_F64 ? hh::launch_totals_f64(h->mesh, U, h->tot_partial, s)
+                                     : hh::launch_totals_f32(h->mesh, U, h->tot_partial, s);
+            if (e == cudaSuccess)
+                e = hh::launch_finalize_totals(h->tot_partial, hh::totals_blocks(), dV,
+                                               totals_log_dev + 5 * step, s);
+        } else {
+            e = hh::launch_finalize_totals(h->tot_partial, rows, dV, totals_log_dev + 5 * step, s);
+        }
+    }
+    return from_cuda(e);
+}
+
+int hard_hydro_advance_host(hard_hydro_t h, const void* U_host_in, void* U_host_out, int nsteps,
+                            double cfl, double t_end, double* t_host, void* stream) {
+    if (!h || !U_host_in || !U_host_out || !t_host) return HARD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    const size_t bytes = state_bytes(h);
+    if (!h->Udev || h->Udev_bytes < bytes) {
+        if (h->Udev) cudaFree(h->Udev);
+        h->Udev = nullptr;
+        h->Udev_bytes = 0;
+        rc = dev_alloc(&h->Udev, bytes);
+        if (rc) return rc;
+        h->Udev_bytes = bytes;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->Udev, U_host_in, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t_slot(h), t_host, sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    rc = hard_hydro_advance(h, h->Udev, nsteps, cfl, t_end, t_slot(h), nullptr, nullptr, stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(U_host_out, h->Udev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t_host, t_slot(h), sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return read_status(h, s);
+}
+
+int hard_hydro_totals(hard_hydro_t h, const void* U, double out5[5], void* stream) {
+    if (!h || !U || !out5 || !aligned16(U)) return HARD_EINVAL;
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    rc = ensure_partial(h, hh::totals_blocks());
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    const double dV = h->mesh.dx[0] * h->mesh.dx[1] * h->mesh.dx[2];
+    cudaError_t e = h->dtype == HARD_F64 ? hh::launch_totals_f64(h->mesh, U, h->tot_partial, s)
+                                         : hh::launch_totals_f32(h->mesh, U, h->tot_partial, s);
+    if (e == cudaSuccess)
+        e = hh::launch_finalize_totals(h->tot_partial, hh::totals_blocks(), dV, tot_slot(h), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out5, tot_slot(h), 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return read_status(h, s);
+}
+
+int hard_hydro_get_error(hard_hydro_t h) {
+    if (!h) return HARD_EINVAL;
+    if (!h->slots) return HARD_OK;
+    return read_status(h, h->last);
+}
+
+const char* hard_hydro_strerror(int code) {
+    switch (code) {
+        case HARD_OK: return "ok";
+        case HARD_EINVAL: return "invalid argument";
+        case HARD_ENOMEM: return "device allocation failed";
+        case HARD_ECUDA: return "CUDA runtime error";
+        case HARD_ENONPHYS: return "non-physical state (rho <= 0, p <= 0 or NaN) on the device";
+        case HARD_ETIMEOUT: return "bounded device wait timed out";
+        case HARD_EUNSUPPORTED: return "unsupported request";
+        default: return "unknown error code";
+    }
+}
+
+void hard_hydro_destroy(hard_hydro_t h) {
+    if (!h) return;
+    free_scratch(h);
+    if (h->slots) cudaFree(h->slots);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// Per-element-type instantiation of the stage, rate and totals kernels and
+// their launchers.  Included by exactly one translation unit per type with
+// HH_T defined (float or double) and HH_SUFFIX (f32 or f64).
+#pragma once
+#include "launch.h"
+#include "stage_kernel.cuh"
+
+namespace hh {
+
+namespace {
+
+using T = HH_T;
+
+template <typename V> __host__ __device__ inline V cdiv(V a, V b) { return (a + b - 1) / b; }
+
+inline T width_param(double dx) {
+    // FP64 kernels divide by dx; FP32 kernels multiply by 1/dx
+    return sizeof(T) == 8 ? (T)dx : (T)(1.0 / dx);
+}
+
+StageArgs<T> make_args(const MeshDesc& m, const TileDesc& td, const StageCall& c) {
+    StageArgs<T> A;
+    A.U0 = static_cast<const T*>(c.U0);
+    A.Uc = static_cast<const T*>(c.Uc);
+    A.Uo = static_cast<T*>(c.Uo);
+    A.N = m.N;
+    for (int a = 0; a < 3; ++a) {
+        A.n[a] = m.n[a];
+        A.bc_lo[a] = m.bc_lo[a];
+        A.bc_hi[a] = m.bc_hi[a];
+        A.dxk[a] = width_param(m.dxk[a]);
+        A.rdx[a] = width_param(m.dx[a]);
+        A.act[a] = m.act[a];
+    }
+    A.gamma = (T)m.gamma;
+    A.gm1 = (T)(m.gamma - 1.0);
+    A.dt = c.dt;
+    A.dt_dev = c.dt_dev;
+    A.stage = c.stage;
+    A.zchunk = td.zc > 0 ? td.zc : 1;
+    A.rate_slot = c.rate_slot;
+    A.tot_partial = c.tot_partial;
+    A.status = c.status;
+    A.tmap = nullptr;
+    return A;
+}
+
+template <int TX, int TY, int DIM, int PX, int PY>
+cudaError_t run_stage(const MeshDesc& m, const TileDesc& td, const StageCall& c, cudaStream_t s) {
+    StageArgs<T> A = make_args(m, td, c);
+    dim3 grid(cdiv(m.n[0], TX), DIM >= 2 ? cdiv(m.n[1], TY) : 1,
+              DIM == 3 ? cdiv(m.n[2], A.zchunk) : 1);
+    const size_t smem = StageSmem<T, TX, TY, DIM>::bytes;
+    auto kern = stage_kernel<T, TX, TY, DIM, PX, PY, false>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    kern<<<grid, TX * TY, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+// No active axis: L(U) = 0, the stage combine alone.
+__global__ void pointwise_stage_kernel(const T* U0, const T* Uc, T* Uo, long long n5, double dt,
+                                       const double* dt_dev, int stage) {
+    const T d = (T)(dt_dev ? *dt_dev : dt);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n5;
+         q += (long long)gridDim.x * blockDim.x) {
+        T L = T(0);
+        Uo[q] = stage == 1 ? Uc[q] + d * L : T(0.5) * U0[q] + T(0.5) * (Uc[q] + d * L);
+    }
+}
+
+__global__ void rate_kernel(const T* __restrict__ U, long long N, T gamma, T gm1, bool a0,
+                            bool a1, bool a2, T r0, T r1, T r2, unsigned long long* slot,
+                            int* status) {
+    const bool act[3] = {a0, a1, a2};
+    const T rdx[3] = {r0, r1, r2};
+    T rmax = T(0);
+    bool bad = false;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        T Uc[NF], W[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) Uc[f] = __ldg(U + f * N + c);
+        cons_to_prim(Uc, gm1, W);
+        bad |= nonphys(W);
+        T r = cell_rate(W, gamma, act, rdx);
+        rmax = (r > rmax || r != r) ? r : rmax;
+    }
+    __shared__ unsigned long long red[32];
+    unsigned long long b = rate_bits(rmax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+        b = v > b ? v : b;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = b;
+    const int any_bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = red[w] > b ? red[w] : b;
+        b = red[0] > b ? red[0] : b;
+        atomicMax(slot, b);
+        if (any_bad) atomicOr(status, 1);
+    }
+}
+
+constexpr int TOT_BLOCKS = TOTALS_BLOCKS;
+constexpr int TOT_THREADS = 256;
+
+__global__ void totals_kernel(const T* __restrict__ U, long long N, double* partial) {
+    double s[NF] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) s[f] += (double)__ldg(U + f * N + c);
+    }
+    __shared__ double red[TOT_THREADS / 32][NF];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        double v = s[f];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][f] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NF) {
+        double v = 0.0;
+        for (int w = 0; w < TOT_THREADS / 32; ++w) v += red[w][threadIdx.x];
+        partial[blockIdx.x * NF + threadIdx.x] = v;
+    }
+}
+
+template <int DIM, int PX, int PY>
+cudaError_t dispatch_tile(const MeshDesc& m, int tile, const StageCall& c, cudaStream_t s) {
+    const TileDesc td = tile_desc(DIM, tile);
+    if constexpr (DIM == 3) {
+        switch (tile) {
+            case 0: case 1: return run_stage<32, 8, 3, 0, 1>(m, td, c, s);
+            case 2: return run_stage<32, 16, 3, 0, 1>(m, td, c, s);
+            case 3: return run_stage<64, 8, 3, 0, 1>(m, td, c, s);
+            default: return run_stage<32, 4, 3, 0, 1>(m, td, c, s);
+        }
+    } else if constexpr (DIM == 2) {
+        if constexpr (PX != 0 || PY != 1) {
+            return run_stage<32, 8, 2, PX, PY>(m, tile_desc(2, 0), c, s);
+        } else {
+            switch (tile) {
+                case 0: return run_stage<32, 8, 2, 0, 1>(m, td, c, s);
+                case 1: return run_stage<32, 16, 2, 0, 1>(m, td, c, s);
+                default: return run_stage<64, 8, 2, 0, 1>(m, td, c, s);
+            }
+        }
+    } else {
+        if constexpr (PX != 0) {
+            return run_stage<128, 1, 1, PX, 0>(m, tile_desc(1, 0), c, s);
+        } else {
+            if (tile == 0) return run_stage<128, 1, 1, 0, 0>(m, td, c, s);
+            return run_stage<256, 1, 1, 0, 0>(m, td, c, s);
+        }
+    }
+}
+
+}  // namespace
+
+#define HH_CAT2(a, b) a##b
+#define HH_CAT(a, b) HH_CAT2(a, b)
+
+cudaError_t HH_CAT(launch_stage_, HH_SUFFIX)(const MeshDesc& m, int kernel, int tile,
+                                              const StageCall& c, cudaStream_t s) {
+    (void)kernel;
+    if (m.dim == 0) {
+        long long n5 = 5 * m.N;
+        int blocks = (int)((n5 + 255) / 256 < 4096 ? (n5 + 255) / 256 : 4096);
+        pointwise_stage_kernel<<<blocks, 256, 0, s>>>(
+            static_cast<const T*>(c.U0), static_cast<const T*>(c.Uc), static_cast<T*>(c.Uo), n5,
+            c.dt, c.dt_dev, c.stage);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess || !c.rate_slot) return e;
+        return HH_CAT(launch_rate_, HH_SUFFIX)(m, c.Uo, c.rate_slot, c.status, s);
+    }
+    if (m.dim == 3) return dispatch_tile<3, 0, 1>(m, tile, c, s);
+    if (m.dim == 2) {
+        if (m.px == 0 && m.py == 1) return dispatch_tile<2, 0, 1>(m, tile, c, s);
+        if (m.px == 0 && m.py == 2) return dispatch_tile<2, 0, 2>(m, tile, c, s);
+        return dispatch_tile<2, 1, 2>(m, tile, c, s);
+    }
+    if (m.px == 0) return dispatch_tile<1, 0, 0>(m, tile, c, s);
+    if (m.px == 1) return dispatch_tile<1, 1, 0>(m, tile, c, s);
+    return dispatch_tile<1, 2, 0>(m, tile, c, s);
+}
+
+cudaError_t HH_CAT(launch_rate_, HH_SUFFIX)(const MeshDesc& m, const void* U,
+                                             unsigned long long* rate_slot, int* status,
+                                             cudaStream_t s) {
+    long long blocks = (m.N + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    rate_kernel<<<(int)blocks, 256, 0, s>>>(
+        static_cast<const T*>(U), m.N, (T)m.gamma, (T)(m.gamma - 1.0), m.act[0], m.act[1],
+        m.act[2], width_param(m.dx[0]), width_param(m.dx[1]), width_param(m.dx[2]), rate_slot,
+        status);
+    return cudaGetLastError();
+}
+
+cudaError_t HH_CAT(launch_totals_, HH_SUFFIX)(const MeshDesc& m, const void* U, double* partial,
+                                               cudaStream_t s) {
+    totals_kernel<<<TOT_BLOCKS, TOT_THREADS, 0, s>>>(static_cast<const T*>(U), m.N, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace hh

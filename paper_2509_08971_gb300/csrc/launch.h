@@ -1,0 +1,86 @@
+// Internal launch interface between the C ABI (hard_hydro.cu) and the kernel
+// translation units (one per element type, so that the FP64 one can be built
+// without FMA contraction).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hh {
+
+struct TileDesc {
+    int tx, ty, zc;        // tile extents along kernel x', y' and the z chunk
+};
+
+// Mesh as the kernels see it: the active axes become kernel axes x', y', z'.
+struct MeshDesc {
+    int dim;               // number of active axes (0..3)
+    int px, py;            // physical axis of kernel x', y'
+    int n[3];              // kernel-axis extents (inactive: 1)
+    int bc_lo[3], bc_hi[3];
+    double dxk[3];         // cell width per kernel axis
+    double dx[3];          // cell width per physical axis
+    bool act[3];           // physical axis active
+    double gamma;
+    long long N;           // total cells
+};
+
+struct StageCall {
+    int stage;                     // 1 or 2
+    const void* U0;
+    const void* Uc;
+    void* Uo;
+    double dt;                     // used when dt_dev == nullptr
+    const double* dt_dev;
+    unsigned long long* rate_slot; // nullptr = no rate epilogue
+    double* tot_partial;           // nullptr = no totals epilogue
+    int* status;
+};
+
+// Tile configurations per number of active axes (the autotuner's space).
+inline constexpr TileDesc TILES3[] = {{32, 8, 32}, {32, 8, 64}, {32, 16, 64}, {64, 8, 64},
+                                      {32, 4, 64}};
+inline constexpr TileDesc TILES2[] = {{32, 8, 0}, {32, 16, 0}, {64, 8, 0}};
+inline constexpr TileDesc TILES1[] = {{128, 1, 0}, {256, 1, 0}};
+
+inline int tile_count(int dim) {
+    return dim == 3 ? 5 : dim == 2 ? 3 : dim == 1 ? 2 : 1;
+}
+inline TileDesc tile_desc(int dim, int tile) {
+    if (dim == 3) return TILES3[tile];
+    if (dim == 2) return TILES2[tile];
+    if (dim == 1) return TILES1[tile];
+    return TileDesc{256, 1, 0};
+}
+// Blocks the stage kernel launches (rows of the totals partial array).
+inline long long stage_blocks(const MeshDesc& m, int tile) {
+    if (m.dim == 0) return 1;
+    TileDesc t = tile_desc(m.dim, tile);
+    long long gx = (m.n[0] + t.tx - 1) / t.tx;
+    long long gy = m.dim >= 2 ? (m.n[1] + t.ty - 1) / t.ty : 1;
+    long long gz = m.dim == 3 ? (m.n[2] + t.zc - 1) / t.zc : 1;
+    return gx * gy * gz;
+}
+
+cudaError_t launch_stage_f32(const MeshDesc& m, int kernel, int tile, const StageCall& c,
+                             cudaStream_t s);
+cudaError_t launch_stage_f64(const MeshDesc& m, int kernel, int tile, const StageCall& c,
+                             cudaStream_t s);
+// Signal-rate max of U into *rate_slot (which must be zeroed first).
+cudaError_t launch_rate_f32(const MeshDesc& m, const void* U, unsigned long long* rate_slot,
+                            int* status, cudaStream_t s);
+cudaError_t launch_rate_f64(const MeshDesc& m, const void* U, unsigned long long* rate_slot,
+                            int* status, cudaStream_t s);
+// Per-block partial sums of the 5 fields; returns the number of partial rows.
+inline constexpr int TOTALS_BLOCKS = 608;
+inline long long totals_blocks() { return TOTALS_BLOCKS; }
+cudaError_t launch_totals_f32(const MeshDesc& m, const void* U, double* partial, cudaStream_t s);
+cudaError_t launch_totals_f64(const MeshDesc& m, const void* U, double* partial, cudaStream_t s);
+
+// Shared helpers (hard_hydro.cu).
+cudaError_t launch_finalize_dt(unsigned long long* rate_slot, double cfl, double t_end,
+                               double* t_dev, double* dt_dev, double* dt_log, int step,
+                               int* status, cudaStream_t s);
+cudaError_t launch_finalize_totals(const double* partial, long long rows, double dV,
+                                   double* out5, cudaStream_t s);
+
+}  // namespace hh

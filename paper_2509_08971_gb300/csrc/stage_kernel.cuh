@@ -1,0 +1,303 @@
+// Fused stage kernel: ghost fill -> conserved-to-primitive -> PLM/minmod face
+// states -> HLLC -> flux difference -> RK stage combine, one launch per stage,
+// with the signal-rate max and the conserved totals fused into the epilogue.
+//
+// Tiling (2.5D z-march).  A CTA owns a TX x TY column of the mesh and marches
+// its z-chunk plane by plane.  For each plane it stages the haloed
+// (TX+4) x (TY+4) primitive plane in shared memory, evaluates every x and y
+// face flux once into shared memory and forms the x/y part of the flux
+// difference.  The z direction needs no shared memory: each thread keeps its
+// own column's z stencil (last primitive, last difference, pending left face
+// state, previous z-face flux) in registers and completes cell k when plane
+// k+2 arrives.
+//
+// Kernel axes vs physical axes.  The layout U[5][nz][ny][nx] is reinterpreted
+// so that the active axes become kernel axes x', y', z' in the same order
+// (e.g. nx = 1 makes physical y the kernel x').  PX / PY name the physical
+// axis of kernel x' / y' (kernel z' is always physical z), which fixes the
+// normal momentum component of each sweep.
+#pragma once
+#include "hydro_math.cuh"
+#include "tma.cuh"
+
+namespace hh {
+
+template <typename T>
+struct StageArgs {
+    const T* U0;                  // Un (stage 2), may alias Uo
+    const T* Uc;                  // state the flux difference is taken of
+    T* Uo;                        // output
+    long long N;                  // cells = field stride
+    int n[3];                     // kernel-axis extents
+    int bc_lo[3], bc_hi[3];       // boundary kind per kernel axis
+    T gamma, gm1;
+    T dxk[3];                     // per kernel axis: dx (FP64) or 1/dx (FP32)
+    T rdx[3];                     // per physical axis, same convention
+    bool act[3];                  // per physical axis: active
+    double dt;                    // used when dt_dev == nullptr
+    const double* dt_dev;
+    int stage;                    // 1 or 2
+    int zchunk;
+    unsigned long long* rate_slot;    // epilogue max-rate (nullptr = off)
+    double* tot_partial;              // epilogue totals [nblocks][5] (nullptr = off)
+    int* status;                      // non-physical flag
+    const CUtensorMap* tmap;          // TMA descriptor of Uc (fused variant)
+};
+
+// Flux difference scaled by the cell width: FP64 divides, FP32 multiplies by 1/dx.
+__device__ __forceinline__ double over_dx(double a, double d) { return a / d; }
+__device__ __forceinline__ float over_dx(float a, float d) { return a * d; }
+
+// Boundary map of one kernel axis: m in [-2, n+1] -> interior index, flip set
+// for a reflecting wall.  Indices beyond the ghost layers (ragged tiles only)
+// clamp to any valid cell; their values feed faces nobody uses.
+__device__ __forceinline__ int bc_map(int m, int n, int lo, int hi, bool& flip) {
+    flip = false;
+    if (m >= 0 && m < n) return m;
+    if (m < -2 || m > n + 1) return m < 0 ? 0 : n - 1;
+    int bc = m < 0 ? lo : hi;
+    if (bc == 0) {
+        int r = m % n;
+        return r < 0 ? r + n : r;
+    }
+    if (bc == 1) return m < 0 ? 0 : n - 1;
+    flip = true;
+    int s = m < 0 ? -1 - m : 2 * n - 1 - m;
+    return s < 0 ? 0 : (s >= n ? n - 1 : s);
+}
+
+template <typename T, int TX, int TY, int DIM>
+struct StageSmem {
+    static constexpr int HX = TX + 4;
+    static constexpr int HY = DIM >= 2 ? TY + 4 : 1;
+    static constexpr int NP = NF * HX * HY;                       // primitive plane
+    static constexpr int NFX = NF * TY * (TX + 1);                // x-face fluxes
+    static constexpr int NFY = DIM >= 2 ? NF * (TY + 1) * TX : 0; // y-face fluxes
+    static constexpr size_t bytes = sizeof(T) * (NP + NFX + NFY);
+};
+
+// Load the conserved values of kernel cell (gx, gy, gz) with the boundary map
+// applied along the active kernel axes, as primitives.
+template <typename T, int DIM, int PX, int PY>
+__device__ __forceinline__ void load_prim(const StageArgs<T>& A, int gx, int gy, int gz, T W[NF],
+                                          bool& bad) {
+    bool fx, fy = false, fz = false;
+    int sx = bc_map(gx, A.n[0], A.bc_lo[0], A.bc_hi[0], fx);
+    int sy = 0, sz = 0;
+    if (DIM >= 2) sy = bc_map(gy, A.n[1], A.bc_lo[1], A.bc_hi[1], fy);
+    if (DIM >= 3) sz = bc_map(gz, A.n[2], A.bc_lo[2], A.bc_hi[2], fz);
+    long long c = ((long long)sz * A.n[1] + sy) * A.n[0] + sx;
+    T U[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) U[f] = __ldg(A.Uc + f * A.N + c);
+    if (fx) U[1 + PX] = -U[1 + PX];
+    if (DIM >= 2 && fy) U[1 + PY] = -U[1 + PY];
+    if (DIM >= 3 && fz) U[3] = -U[3];
+    cons_to_prim(U, A.gm1, W);
+    bad |= nonphys(W);
+}
+
+template <typename T, int TX, int TY, int DIM, int PX, int PY, bool TMA>
+__global__ void __launch_bounds__(TX * TY)
+stage_kernel(const StageArgs<T> A) {
+    using S = StageSmem<T, TX, TY, DIM>;
+    constexpr int NT = TX * TY;
+    constexpr int HX = S::HX, HY = S::HY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* Ps = reinterpret_cast<T*>(smem_raw);          // [NF][HY][HX]
+    T* Fx = Ps + S::NP;                               // [NF][TY][TX+1]
+    T* Fy = Fx + S::NFX;                              // [NF][TY+1][TX]
+    __shared__ double red_tot[NT / 32][NF];
+    __shared__ unsigned long long red_rate[NT / 32];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX;
+    const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own = x < A.n[0] && (DIM < 2 || y < A.n[1]);
+    const int z0 = DIM == 3 ? blockIdx.z * A.zchunk : 0;
+    const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.n[2]) : 1;
+    const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
+    const T gamma = A.gamma, gm1 = A.gm1;
+    bool bad = false;
+    T rate_max = T(0);
+    T tot[NF] = {T(0), T(0), T(0), T(0), T(0)};
+
+    // z stencil state of this thread's column
+    T qm1[NF], dprev[NF], qLp[NF], Fzp[NF], Da[NF], Db[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        qm1[f] = dprev[f] = qLp[f] = Fzp[f] = Da[f] = Db[f] = T(0);
+    }
+
+    const int jbeg = DIM == 3 ? z0 - 2 : 0;
+    const int jend = DIM == 3 ? z1 + 2 : 1;
+    for (int j = jbeg; j < jend; ++j) {
+        const bool xy = DIM < 3 || (j >= z0 && j < z1);
+        T qj[NF];
+        T Dj[NF];
+        if (xy) {
+            __syncthreads();                       // previous plane fully consumed
+            for (int e = tid; e < HX * HY; e += NT) {
+                int hx = e % HX, hy = e / HX;
+                T W[NF];
+                load_prim<T, DIM, PX, PY>(A, x0 - 2 + hx, y0 - 2 + hy, j, W, bad);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) Ps[(f * HY + hy) * HX + hx] = W[f];
+            }
+            __syncthreads();
+            // x faces: (TX+1) per row; face fx sits left of tile cell fx
+            for (int e = tid; e < (TX + 1) * TY; e += NT) {
+                int fx = e % (TX + 1), row = e / (TX + 1);
+                int hy = DIM >= 2 ? row + 2 : 0;
+                T q[4][NF];
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HY + hy) * HX + fx + s];
+                T F[NF];
+                face_flux4<PX>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + fx] = F[f];
+            }
+            if (DIM >= 2) {
+                for (int e = tid; e < TX * (TY + 1); e += NT) {
+                    int col = e % TX, fy = e / TX;
+                    T q[4][NF];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HY + fy + s) * HX + col + 2];
+                    T F[NF];
+                    face_flux4<PY>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + fy) * TX + col] = F[f];
+                }
+            }
+            __syncthreads();
+            const int hyc = DIM >= 2 ? ty + 2 : 0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                qj[f] = Ps[(f * HY + hyc) * HX + tx + 2];
+                T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fx[(f * TY + ty) * (TX + 1) + tx];
+                Dj[f] = T(0) - over_dx(a, A.dxk[0]);
+                if (DIM >= 2) {
+                    T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fy[(f * (TY + 1) + ty) * TX + tx];
+                    Dj[f] = Dj[f] - over_dx(b, A.dxk[1]);
+                }
+            }
+        } else {
+            // warm-up / look-ahead plane: only this column's primitives
+            load_prim<T, DIM, PX, PY>(A, min(x, A.n[0] - 1), min(y, A.n[1] - 1), j, qj, bad);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Dj[f] = T(0);
+        }
+
+        int k;                 // cell completed in this iteration (-1: none)
+        T L[NF];
+        if (DIM == 3) {
+            const int cnt = j - jbeg;
+            T dcur[NF], Fz[NF];
+            if (cnt >= 2) {
+                T qL[NF], qR[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    dcur[f] = qj[f] - qm1[f];
+                    T d = minmod(dprev[f], dcur[f]);
+                    qR[f] = qm1[f] - T(0.5) * d;
+                    qL[f] = qm1[f] + T(0.5) * d;
+                }
+                if (cnt >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, Fz);   // face j-3/2
+#pragma unroll
+                for (int f = 0; f < NF; ++f) qLp[f] = qL[f];
+            } else {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) dcur[f] = qj[f] - qm1[f];
+            }
+            k = cnt >= 4 ? j - 2 : -1;
+            if (k >= 0) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) L[f] = Da[f] - over_dx(Fz[f] - Fzp[f], A.dxk[2]);
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (cnt >= 3) Fzp[f] = Fz[f];
+                dprev[f] = dcur[f];
+                qm1[f] = qj[f];
+                Da[f] = Db[f];
+                Db[f] = Dj[f];
+            }
+        } else {
+            k = 0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) L[f] = Dj[f];
+        }
+
+        if (k >= 0 && own) {
+            const long long c = ((long long)k * A.n[1] + y) * A.n[0] + x;
+            T Uo[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                T uc = A.Uc[f * A.N + c];
+                if (A.stage == 1) {
+                    Uo[f] = uc + dt * L[f];
+                } else {
+                    T u0 = A.U0[f * A.N + c];
+                    Uo[f] = T(0.5) * u0 + T(0.5) * (uc + dt * L[f]);
+                }
+                A.Uo[f * A.N + c] = Uo[f];
+            }
+            if (A.rate_slot) {
+                T W[NF];
+                cons_to_prim(Uo, gm1, W);
+                T r = cell_rate(W, gamma, A.act, A.rdx);
+                rate_max = (r > rate_max || r != r) ? r : rate_max;
+            }
+            if (A.tot_partial) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) tot[f] += Uo[f];
+            }
+        }
+    }
+
+    // ---- epilogue: block reductions ----
+    const int lane = tid & 31, warp = tid >> 5;
+    if (A.rate_slot) {
+        unsigned long long b = rate_bits(rate_max);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+            b = v > b ? v : b;
+        }
+        if (lane == 0) red_rate[warp] = b;
+    }
+    if (A.tot_partial) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            double v = (double)tot[f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red_tot[warp][f] = v;
+        }
+    }
+    const int any_bad = __syncthreads_or(bad);
+    if (tid == 0) {
+        if (any_bad) atomicOr(A.status, 1);
+        if (A.rate_slot) {
+            unsigned long long b = 0;
+            for (int w = 0; w < NT / 32; ++w) b = red_rate[w] > b ? red_rate[w] : b;
+            atomicMax(A.rate_slot, b);
+        }
+        if (A.tot_partial) {
+            const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            for (int f = 0; f < NF; ++f) {
+                double s = 0.0;
+                for (int w = 0; w < NT / 32; ++w) s += red_tot[w][f];
+                A.tot_partial[blk * NF + f] = s;
+            }
+        }
+    }
+}
+
+}  // namespace hh
