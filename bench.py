@@ -1,0 +1,322 @@
+"""Benchmark of the fused hydro stage update on GB300.
+
+Workload: the 3D periodic smooth flow on a 256^3 mesh (gamma = 5/3, entropy
+wave rho = 1 + 0.2 sin(2 pi (x+y+z)) advected at (1,1,1), p = 1, plus seeded
+acoustic modes of amplitude 1e-3 in the 8 lowest wave vectors), CFL 0.4.
+A step is one pass of the whole path: the CFL time step from the fused
+signal-rate reduction, both Runge-Kutta stages, and the FP64 conserved totals
+of the new state.  The state (336 MB in FP32) is larger than the 129 MB L2.
+
+metric: cell-updates per RK stage per second = cells * 2 * steps / time.
+
+Prints one JSON line.  Multi-GPU (torchrun): every rank advances its own
+replica of the workload (no collective on the data path), timing is the max
+over ranks and ``value`` counts the cells of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage (FP32 fused vs FP64 plain) and % HBM roofline"
+UNIT = "cell-updates/s"
+N_SIDE = 256
+GAMMA = 5.0 / 3.0
+CFL = 0.4
+WORKLOAD = ("3D periodic smooth flow 256^3, gamma=5/3, entropy wave + 8 seeded acoustic "
+            "modes (amplitude 1e-3), CFL 0.4")
+BYTES_PER_CELL_STAGE = {4: 50.0, 8: 100.0}     # algorithmic: (5+5 + 10+5)/2 values
+L2_BYTES = 129 * 2 ** 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.06)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_threads():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def time_oracle(shape, steps, threads):
+    """The oracle as it stands (FP64 C, OpenMP over cells) on the same
+    per-cell arithmetic.  Returns (cell-stages/s, seconds, threads used)."""
+    import hydro_inputs as H
+    import oracle
+    oracle.set_threads(threads)
+    used = oracle.get_threads()
+    U = H.smooth_3d(0, seed=0, gamma=GAMMA, shape=shape)
+    g = oracle.Grid(shape, GAMMA, oracle.BC_PERIODIC)
+    t0 = time.perf_counter()
+    g.run(U, steps, CFL)
+    sec = time.perf_counter() - t0
+    cells = shape[0] * shape[1] * shape[2]
+    return cells * 2 * steps / sec, sec, used
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle on the host cores, each step a
+    bounded sample of the workload (a 256 x 256 x 8 periodic slab of the same
+    flow: the same per-cell arithmetic at 1/32 of the cells)."""
+    if rank != 0:
+        return
+    shape = (8, N_SIDE, N_SIDE)
+    threads = cpu_threads()
+    time_oracle(shape, max(args.warmup, 0), threads) if args.warmup else None
+    rate, sec, used = time_oracle(shape, args.steps, threads)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "256x256x8 periodic slab per step",
+                   "cells_per_step": shape[0] * shape[1] * shape[2]},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{args.steps} RK2 steps of a 256x256x8 slab"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--f64-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_SIDE, help="mesh side (profiling runs only)")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import hydro_inputs as H
+    import paper_2509_08971_gb300 as hh
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    shape = (n, n, n)
+    cells = n ** 3
+    U64 = H.smooth_3d(n, seed=rank, gamma=GAMMA)
+    stream = torch.cuda.current_stream()
+
+    # ---------------- FP32 fused: the headline ----------------
+    m32 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32,
+                       kernel=hh.HARD_KERNEL_FUSED)
+    U = torch.tensor(U64, dtype=torch.float32, device=dev)
+    t_dev = torch.zeros((), dtype=torch.float64, device=dev)
+    tot_log = torch.zeros((max(args.steps, args.warmup, 3), 5), dtype=torch.float64, device=dev)
+
+    def advance(m, Ud, k, tlog):
+        hh.check(hh.hard_hydro_advance(m.h, Ud.data_ptr(), k, CFL, 0.0, t_dev.data_ptr(), None,
+                                       tlog.data_ptr(), stream.cuda_stream), "advance")
+
+    advance(m32, U, max(args.warmup, 3), tot_log)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(dev.index)
+    with ClockSampler(gpu_id) as clk:
+        barrier()
+        ev0.record(stream)
+        advance(m32, U, args.steps, tot_log)
+        ev1.record(stream)
+        barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = world * cells * 2 * args.steps / (ms * 1e-3)
+    status = m32.get_error()
+    clocks = clk.summary()
+    # kernels of this library launched in the timed region:
+    # 1 signal rate + per step (finalize dt, stage 1, stage 2, finalize totals)
+    launches = 1 + 4 * args.steps
+
+    # ---------------- stage kernel alone: roofline ----------------
+    U1 = torch.empty_like(U)
+    U2 = torch.empty_like(U)
+    dt = m32.cfl_dt(U, CFL)
+    for _ in range(3):
+        m32.stage(1, None, U, dt, out=U1)
+        m32.stage(2, U, U1, dt, out=U2)
+    reps = max(20, min(200, args.steps))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        m32.stage(1, None, U, dt, out=U1)
+        m32.stage(2, U, U1, dt, out=U2)
+    e1.record(stream)
+    barrier()
+    stage_ms = e0.elapsed_time(e1) / (2 * reps)
+    hbm, peak_kind = peaks()
+    alg_bytes = BYTES_PER_CELL_STAGE[4] * cells
+    achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "stage_kernel<float,32,8,3> (mean of stage 1 and stage 2)",
+                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": stage_ms}
+    del U1, U2
+
+    # ---------------- FP64 plain ----------------
+    m64 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float64,
+                       kernel=hh.HARD_KERNEL_PLAIN)
+    V = torch.tensor(U64, dtype=torch.float64, device=dev)
+    k64 = max(1, args.f64_steps)
+    tl64 = torch.zeros((max(k64, 3), 5), dtype=torch.float64, device=dev)
+    advance(m64, V, 3, tl64)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    advance(m64, V, k64, tl64)
+    f1.record(stream)
+    barrier()
+    ms64 = max_over_ranks(f0.elapsed_time(f1))
+    value64 = world * cells * 2 * k64 / (ms64 * 1e-3)
+    del V, m64
+
+    # ---------------- end to end through the C ABI, host buffers ----------------
+    Uh = torch.tensor(U64, dtype=torch.float32).pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    m32.advance_host(Uh, 1, CFL, out=Uo)          # warm the handle's device buffer
+    barrier()
+    t0 = time.perf_counter()
+    m32.advance_host(Uh, args.steps, CFL, out=Uo)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * cells * 2 * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": Uh.numel() * 4 / args.steps,
+           "d2h_bytes_per_step": Uo.numel() * 4 / args.steps,
+           "call": f"hard_hydro_advance_host: one call of {args.steps} steps, pinned host "
+                   "buffers, copies in the timed region"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "global_cells": world * cells,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "state 336 MB > 129 MB L2 (no flush needed)", "kernel": "fused",
+                   "step": "CFL rate + stage 1 + stage 2 + FP64 totals"},
+        "roofline": roofline,
+        "fp64_plain": {"value": value64, "unit": UNIT, "steps": k64,
+                       "ms_per_step": ms64 / k64, "fp32_fused_speedup": value / value64},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "status": hh.hard_hydro_strerror(status),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = cpu_threads()
+        rate, sec, used = time_oracle(shape, 2, threads)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": f"2 RK2 steps of the full 256^3 workload ({sec:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

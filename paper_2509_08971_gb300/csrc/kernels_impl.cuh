@@ -4,6 +4,7 @@
 #pragma once
 #include "launch.h"
 #include "stage_kernel.cuh"
+#include "stage_tma.cuh"
 
 namespace hh {
 
@@ -61,6 +62,87 @@ cudaError_t run_stage(const MeshDesc& m, const TileDesc& td, const StageCall& c,
     }
     kern<<<grid, TX * TY, smem, s>>>(A);
     return cudaGetLastError();
+}
+
+// ---- TMA path (3D meshes whose rows are 16-byte multiples) ----
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map of U as a 4D tensor (x, y, z, field) with box (bx, by, 1, 5).
+bool encode_state_map(CUtensorMap* map, const void* base, const MeshDesc& m, int bx, int by) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t es = sizeof(T);
+    const cuuint64_t dims[4] = {(cuuint64_t)m.n[0], (cuuint64_t)m.n[1], (cuuint64_t)m.n[2], 5};
+    const cuuint64_t strides[3] = {m.n[0] * es, (cuuint64_t)m.n[0] * m.n[1] * es,
+                                   (cuuint64_t)m.N * es};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 5};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                          4, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// The TMA kernel needs 3 active axes, rows (and so every stride) a multiple of
+// 16 bytes, at least 4 cells along x (the periodic x strip) and a 16-byte
+// aligned base; otherwise the plain kernel runs.
+bool tma_eligible(const MeshDesc& m, const void* Uc) {
+    const int per16 = 16 / (int)sizeof(T);
+    return m.dim == 3 && m.n[0] % per16 == 0 && m.n[0] >= 4 &&
+           (reinterpret_cast<uintptr_t>(Uc) & 15u) == 0 && encode_fn() != nullptr;
+}
+
+constexpr size_t SMEM_LIMIT = 232448;     // 227 KB opt-in per block
+
+template <int TX, int TY>
+cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall& c,
+                          cudaStream_t s, bool& used) {
+    using L = TmaLayout<T, TX, TY>;
+    used = false;
+    if constexpr (L::bytes > SMEM_LIMIT) {
+        return cudaSuccess;
+    } else {
+        TmaMaps maps;
+        if (!encode_state_map(&maps.main, c.Uc, m, TX + 8, TY + 4) ||
+            !encode_state_map(&maps.xstrip, c.Uc, m, 4, TY + 4) ||
+            !encode_state_map(&maps.ystrip, c.Uc, m, TX + 8, 2))
+            return cudaSuccess;
+        StageArgs<T> A = make_args(m, td, c);
+        dim3 grid(cdiv(m.n[0], TX), cdiv(m.n[1], TY), cdiv(m.n[2], A.zchunk));
+        auto kern = stage_tma_kernel<T, TX, TY>;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)L::bytes);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        kern<<<grid, TX * TY, L::bytes, s>>>(A, maps);
+        used = true;
+        return cudaGetLastError();
+    }
 }
 
 // No active axis: L(U) = 0, the stage combine alone.
@@ -137,9 +219,21 @@ __global__ void totals_kernel(const T* __restrict__ U, long long N, double* part
 }
 
 template <int DIM, int PX, int PY>
-cudaError_t dispatch_tile(const MeshDesc& m, int tile, const StageCall& c, cudaStream_t s) {
+cudaError_t dispatch_tile(const MeshDesc& m, int kernel, int tile, const StageCall& c,
+                          cudaStream_t s) {
     const TileDesc td = tile_desc(DIM, tile);
     if constexpr (DIM == 3) {
+        if (kernel == 0 && tma_eligible(m, c.Uc)) {
+            bool used = false;
+            cudaError_t e;
+            switch (tile) {
+                case 0: case 1: e = run_stage_tma<32, 8>(m, td, c, s, used); break;
+                case 2: e = run_stage_tma<32, 16>(m, td, c, s, used); break;
+                case 3: e = run_stage_tma<64, 8>(m, td, c, s, used); break;
+                default: e = run_stage_tma<32, 4>(m, td, c, s, used); break;
+            }
+            if (used || e != cudaSuccess) return e;
+        }
         switch (tile) {
             case 0: case 1: return run_stage<32, 8, 3, 0, 1>(m, td, c, s);
             case 2: return run_stage<32, 16, 3, 0, 1>(m, td, c, s);
@@ -173,7 +267,6 @@ cudaError_t dispatch_tile(const MeshDesc& m, int tile, const StageCall& c, cudaS
 
 cudaError_t HH_CAT(launch_stage_, HH_SUFFIX)(const MeshDesc& m, int kernel, int tile,
                                               const StageCall& c, cudaStream_t s) {
-    (void)kernel;
     if (m.dim == 0) {
         long long n5 = 5 * m.N;
         int blocks = (int)((n5 + 255) / 256 < 4096 ? (n5 + 255) / 256 : 4096);
@@ -184,15 +277,15 @@ cudaError_t HH_CAT(launch_stage_, HH_SUFFIX)(const MeshDesc& m, int kernel, int 
         if (e != cudaSuccess || !c.rate_slot) return e;
         return HH_CAT(launch_rate_, HH_SUFFIX)(m, c.Uo, c.rate_slot, c.status, s);
     }
-    if (m.dim == 3) return dispatch_tile<3, 0, 1>(m, tile, c, s);
+    if (m.dim == 3) return dispatch_tile<3, 0, 1>(m, kernel, tile, c, s);
     if (m.dim == 2) {
-        if (m.px == 0 && m.py == 1) return dispatch_tile<2, 0, 1>(m, tile, c, s);
-        if (m.px == 0 && m.py == 2) return dispatch_tile<2, 0, 2>(m, tile, c, s);
-        return dispatch_tile<2, 1, 2>(m, tile, c, s);
+        if (m.px == 0 && m.py == 1) return dispatch_tile<2, 0, 1>(m, kernel, tile, c, s);
+        if (m.px == 0 && m.py == 2) return dispatch_tile<2, 0, 2>(m, kernel, tile, c, s);
+        return dispatch_tile<2, 1, 2>(m, kernel, tile, c, s);
     }
-    if (m.px == 0) return dispatch_tile<1, 0, 0>(m, tile, c, s);
-    if (m.px == 1) return dispatch_tile<1, 1, 0>(m, tile, c, s);
-    return dispatch_tile<1, 2, 0>(m, tile, c, s);
+    if (m.px == 0) return dispatch_tile<1, 0, 0>(m, kernel, tile, c, s);
+    if (m.px == 1) return dispatch_tile<1, 1, 0>(m, kernel, tile, c, s);
+    return dispatch_tile<1, 2, 0>(m, kernel, tile, c, s);
 }
 
 cudaError_t HH_CAT(launch_rate_, HH_SUFFIX)(const MeshDesc& m, const void* U,

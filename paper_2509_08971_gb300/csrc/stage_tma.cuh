@@ -1,0 +1,361 @@
+// TMA-fed fused stage kernel for 3D meshes (the bench path).
+//
+// Same arithmetic as stage_kernel (each face flux evaluated once, in the same
+// operation order), different data movement:
+//   * one elected thread streams the haloed conserved plane of the CTA's
+//     column, box (TX+8) x (TY+4) x 5 fields, with one 4D bulk tensor load per
+//     plane into a 5-slot shared-memory ring, two planes ahead, completing on
+//     one mbarrier per slot;
+//   * periodic x/y ghosts of boundary tiles arrive as narrow extra boxes of
+//     the wrapped columns / rows on the same mbarrier; outflow and reflecting
+//     ghosts are read from the tile's own interior;
+//   * the conserved value of a cell, needed by the RK combine two planes
+//     later, is read back from the ring instead of from HBM.
+// The x start of every box is x0 - 4 (x0 a multiple of TX): 16-byte aligned
+// for 4- and 8-byte elements.
+#pragma once
+#include "stage_kernel.cuh"
+#include "tma.cuh"
+
+namespace hh {
+
+struct TmaMaps {
+    CUtensorMap main;    // box (TX+8, TY+4, 1, 5)
+    CUtensorMap xstrip;  // box (4, TY+4, 1, 5)
+    CUtensorMap ystrip;  // box (TX+8, 2, 1, 5)
+};
+
+template <typename T, int TX, int TY>
+struct TmaLayout {
+    static constexpr int D = 5;                         // ring slots
+    static constexpr int P = 2;                         // planes loaded ahead
+    static constexpr int HXC = TX + 8, HYC = TY + 4;    // conserved box
+    static constexpr int MAIN = NF * HYC * HXC;
+    static constexpr int XS = NF * HYC * 4;             // x strip box
+    static constexpr int YS = NF * 2 * HXC;             // y strip box
+    static constexpr int SLOT = MAIN + 2 * XS + 2 * YS; // elements per slot
+    static constexpr int HXP = TX + 4, HYP = TY + 4;    // primitive plane
+    static constexpr int NP = NF * HYP * HXP;
+    static constexpr int NFX = NF * TY * (TX + 1);
+    static constexpr int NFY = NF * (TY + 1) * TX;
+    static constexpr size_t BAR_BYTES = 128;
+    static constexpr size_t bytes = BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NP + NFX + NFY);
+    static_assert((MAIN * sizeof(T)) % 16 == 0 && (XS * sizeof(T)) % 16 == 0 &&
+                  (YS * sizeof(T)) % 16 == 0, "TMA destinations must stay 16-byte aligned");
+    static_assert(P < D - 2, "a slot is read until two planes after it lands");
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__ TmaMaps M) {
+    using L = TmaLayout<T, TX, TY>;
+    constexpr int NT = TX * TY;
+    constexpr int D = L::D, P = L::P;
+    constexpr int HXC = L::HXC, HYC = L::HYC, HXP = L::HXP, HYP = L::HYP;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    T* ring = reinterpret_cast<T*>(smem_raw + L::BAR_BYTES);
+    T* Ps = ring + D * L::SLOT;                       // [NF][HYP][HXP]
+    T* Fx = Ps + L::NP;                               // [NF][TY][TX+1]
+    T* Fy = Fx + L::NFX;                              // [NF][TY+1][TX]
+    __shared__ double red_tot[NT / 32][NF];
+    __shared__ unsigned long long red_rate[NT / 32];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own = x < nx && y < ny;
+    const int z0 = blockIdx.z * A.zchunk;
+    const int z1 = min(z0 + A.zchunk, nz);
+    const int jbeg = z0 - 2;
+    const int niter = (z1 + 2) - jbeg;
+    // boundary tiles and their periodic strips (uniform over the CTA)
+    const bool xlo = x0 == 0, xhi = x0 + TX + 2 > nx;
+    const bool ylo = y0 == 0, yhi = y0 + TY + 2 > ny;
+    const bool px_lo = xlo && A.bc_lo[0] == 0, px_hi = xhi && A.bc_hi[0] == 0;
+    const bool py_lo = ylo && A.bc_lo[1] == 0, py_hi = yhi && A.bc_hi[1] == 0;
+    const bool edge = xlo || xhi || ylo || yhi;
+    const uint32_t tx_bytes = (uint32_t)sizeof(T) *
+        (L::MAIN + (px_lo ? L::XS : 0) + (px_hi ? L::XS : 0) + (py_lo ? L::YS : 0) +
+         (py_hi ? L::YS : 0));
+
+    const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
+    const T gamma = A.gamma, gm1 = A.gm1;
+
+    auto slot_main = [&](int it) { return ring + (it % D) * L::SLOT; };
+    auto issue = [&](int it) {
+        T* s = slot_main(it);
+        uint64_t* bar = bars + (it % D);
+        bool fz;
+        const int jj = bc_map(jbeg + it, nz, A.bc_lo[2], A.bc_hi[2], fz);
+        mbar_arrive_expect_tx(bar, tx_bytes);
+        tma_load_4d(s, &M.main, x0 - 4, y0 - 2, jj, 0, bar);
+        if (px_lo) tma_load_4d(s + L::MAIN, &M.xstrip, nx - 4, y0 - 2, jj, 0, bar);
+        if (px_hi) tma_load_4d(s + L::MAIN + L::XS, &M.xstrip, 0, y0 - 2, jj, 0, bar);
+        if (py_lo) tma_load_4d(s + L::MAIN + 2 * L::XS, &M.ystrip, x0 - 4, ny - 2, jj, 0, bar);
+        if (py_hi) tma_load_4d(s + L::MAIN + 2 * L::XS + L::YS, &M.ystrip, x0 - 4, 0, jj, 0, bar);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < D; ++s) mbar_init(bars + s, 1);
+        mbar_fence_init();
+        s_abort = 0;
+        prefetch_tmap(&M.main);
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int it = 0; it < P && it < niter; ++it) issue(it);
+
+    bool bad = false;
+    T rate_max = T(0);
+    T tot[NF] = {T(0), T(0), T(0), T(0), T(0)};
+    T qm1[NF], dprev[NF], qLp[NF], Fzp[NF], Da[NF], Db[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) qm1[f] = dprev[f] = qLp[f] = Fzp[f] = Da[f] = Db[f] = T(0);
+
+    int it = 0;
+    for (; it < niter; ++it) {
+        const int j = jbeg + it;
+        __syncthreads();                              // iteration it-1 done with its slots
+        if (s_abort) break;
+        if (tid == 0 && it + P < niter) issue(it + P);
+        const int k = j - 2;                          // cell completed this iteration
+        const bool upd = it >= 4 && own;
+        T u0[NF];
+        if (upd && A.stage == 2) {
+            const long long c = ((long long)k * ny + y) * nx + x;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) u0[f] = A.U0[f * A.N + c];
+        }
+        if (!mbar_wait(bars + (it % D), (uint32_t)((it / D) & 1))) {
+            atomicOr(A.status, 4);
+            s_abort = 1;
+        }
+        const T* S = slot_main(it);
+        const bool xy = j >= z0 && j < z1;
+        T qj[NF], Dj[NF];
+        if (xy) {
+            // conserved -> primitive over the haloed (TX+4) x (TY+4) plane
+            for (int e = tid; e < HXP * HYP; e += NT) {
+                const int cx = e % HXP - 2, cy = e / HXP - 2;
+                const T* src = S;
+                int sx = cx + 4, sy = cy + 2, pitch = HXC, fstride = HYC * HXC;
+                bool flip_x = false, flip_y = false, use = true;
+                if (edge) {
+                    const int gx = x0 + cx, gy = y0 + cy;
+                    const bool gxo = gx < 0 || gx >= nx, gyo = gy < 0 || gy >= ny;
+                    if (gxo && gyo) {
+                        use = false;                  // corner: no face reads it
+                    } else if (gxo) {
+                        const int bc = gx < 0 ? A.bc_lo[0] : A.bc_hi[0];
+                        if (gx > nx + 1) {
+                            use = false;              // beyond the ghosts of a ragged tile
+                        } else if (bc == 0) {
+                            src = S + L::MAIN + (gx < 0 ? 0 : L::XS);
+                            sx = gx < 0 ? gx + 4 : gx - nx;
+                            pitch = 4;
+                            fstride = HYC * 4;
+                        } else if (bc == 1) {
+                            sx = (gx < 0 ? 0 : nx - 1) - x0 + 4;
+                        } else {
+                            sx = (gx < 0 ? -1 - gx : 2 * nx - 1 - gx) - x0 + 4;
+                            flip_x = true;
+                        }
+                    } else if (gyo) {
+                        const int bc = gy < 0 ? A.bc_lo[1] : A.bc_hi[1];
+                        if (gy > ny + 1) {
+                            use = false;
+                        } else if (bc == 0) {
+                            src = S + L::MAIN + 2 * L::XS + (gy < 0 ? 0 : L::YS);
+                            sy = gy < 0 ? gy + 2 : gy - ny;
+                            fstride = 2 * HXC;
+                        } else if (bc == 1) {
+                            sy = (gy < 0 ? 0 : ny - 1) - y0 + 2;
+                        } else {
+                            sy = (gy < 0 ? -1 - gy : 2 * ny - 1 - gy) - y0 + 2;
+                            flip_y = true;
+                        }
+                    }
+                }
+                T U[NF], W[NF];
+                if (use) {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) U[f] = src[f * fstride + sy * pitch + sx];
+                    if (flip_x) U[1] = -U[1];
+                    if (flip_y) U[2] = -U[2];
+                } else {
+                    U[0] = T(1); U[1] = U[2] = U[3] = T(0); U[4] = T(1);
+                }
+                cons_to_prim(U, gm1, W);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) Ps[(f * HYP + cy + 2) * HXP + cx + 2] = W[f];
+            }
+            __syncthreads();
+            // each thread: the x face left of its cell and the y face below it
+            {
+                T q[4][NF], F[NF];
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HYP + ty + 2) * HXP + tx + s];
+                face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) Fx[(f * TY + ty) * (TX + 1) + tx] = F[f];
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HYP + ty + s) * HXP + tx + 2];
+                face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + ty) * TX + tx] = F[f];
+            }
+            // the TX faces above the top row and the TY faces right of the last column
+            if (tid < TX + TY) {
+                T q[4][NF], F[NF];
+                if (tid < TX) {
+                    const int col = tid;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            q[s][f] = Ps[(f * HYP + TY + s) * HXP + col + 2];
+                    face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + TY) * TX + col] = F[f];
+                } else {
+                    const int row = tid - TX;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            q[s][f] = Ps[(f * HYP + row + 2) * HXP + TX + s];
+                    face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + TX] = F[f];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                qj[f] = Ps[(f * HYP + ty + 2) * HXP + tx + 2];
+                const T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fx[(f * TY + ty) * (TX + 1) + tx];
+                const T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fy[(f * (TY + 1) + ty) * TX + tx];
+                Dj[f] = T(0) - over_dx(a, A.dxk[0]);
+                Dj[f] = Dj[f] - over_dx(b, A.dxk[1]);
+            }
+            if (own) bad |= nonphys(qj);
+        } else {
+            // warm-up / look-ahead plane: this column only
+            T U[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) U[f] = S[(f * HYC + ty + 2) * HXC + tx + 4];
+            bool fz;
+            bc_map(j, nz, A.bc_lo[2], A.bc_hi[2], fz);
+            if (fz) U[3] = -U[3];
+            cons_to_prim(U, gm1, qj);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Dj[f] = T(0);
+        }
+
+        // z direction: streaming stencil of this column
+        T Fz[NF] = {T(0), T(0), T(0), T(0), T(0)};
+        T dcur[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dcur[f] = qj[f] - qm1[f];
+        if (it >= 2) {
+            T qL[NF], qR[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T d = minmod(dprev[f], dcur[f]);
+                qR[f] = qm1[f] - T(0.5) * d;
+                qL[f] = qm1[f] + T(0.5) * d;
+            }
+            if (it >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, Fz);      // face j-3/2
+#pragma unroll
+            for (int f = 0; f < NF; ++f) qLp[f] = qL[f];
+        }
+        if (upd) {
+            const long long c = ((long long)k * ny + y) * nx + x;
+            const T* Sk = slot_main(it - 2);
+            T Uo[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T Lf = Da[f] - over_dx(Fz[f] - Fzp[f], A.dxk[2]);
+                const T uc = Sk[(f * HYC + ty + 2) * HXC + tx + 4];
+                Uo[f] = A.stage == 1 ? uc + dt * Lf : T(0.5) * u0[f] + T(0.5) * (uc + dt * Lf);
+                A.Uo[f * A.N + c] = Uo[f];
+            }
+            if (A.rate_slot) {
+                T W[NF];
+                cons_to_prim(Uo, gm1, W);
+                const T r = cell_rate(W, gamma, A.act, A.rdx);
+                rate_max = (r > rate_max || r != r) ? r : rate_max;
+            }
+            if (A.tot_partial) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) tot[f] += Uo[f];
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (it >= 3) Fzp[f] = Fz[f];
+            dprev[f] = dcur[f];
+            qm1[f] = qj[f];
+            Da[f] = Db[f];
+            Db[f] = Dj[f];
+        }
+    }
+    if (s_abort) {
+        // a transfer never completed: wait (bounded) for the loads still in
+        // flight so none lands after this block has left, then return
+        // the failed wait was iteration it-1; loads were issued up to it-1+P
+        if (tid == 0)
+            for (int r = it > 0 ? it - 1 : 0; r < niter && r <= it - 1 + P; ++r)
+                mbar_wait(bars + (r % D), (uint32_t)((r / D) & 1));
+        __syncthreads();
+        return;
+    }
+
+    // ---- epilogue: block reductions ----
+    const int lane = tid & 31, warp = tid >> 5;
+    if (A.rate_slot) {
+        unsigned long long b = rate_bits(rate_max);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+            b = v > b ? v : b;
+        }
+        if (lane == 0) red_rate[warp] = b;
+    }
+    if (A.tot_partial) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            double v = (double)tot[f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red_tot[warp][f] = v;
+        }
+    }
+    const int any_bad = __syncthreads_or(bad);
+    if (tid == 0) {
+        if (any_bad) atomicOr(A.status, 1);
+        if (A.rate_slot) {
+            unsigned long long b = 0;
+            for (int w = 0; w < NT / 32; ++w) b = red_rate[w] > b ? red_rate[w] : b;
+            atomicMax(A.rate_slot, b);
+        }
+        if (A.tot_partial) {
+            const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            for (int f = 0; f < NF; ++f) {
+                double s = 0.0;
+                for (int w = 0; w < NT / 32; ++w) s += red_tot[w][f];
+                A.tot_partial[blk * NF + f] = s;
+            }
+        }
+    }
+}
+
+}  // namespace hh
