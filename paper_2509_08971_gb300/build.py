@@ -1,9 +1,10 @@
 """Build the CUDA library ``libhard_hydro.so`` for sm_103a with nvcc.
 
-Each element type is its own translation unit so the FP64 kernels can be
-compiled without FMA contraction (``--fmad=false``): their arithmetic is then
-one IEEE operation per source operation, in source order.  The translation
-units compile in parallel; the library is built in-tree next to this file.
+Each element type is its own translation unit; both compile without automatic
+FMA contraction (``--fmad=false``) so that rounding is fixed by the source:
+FP64 does one IEEE operation per source operation (the oracle's order) and FP32
+fuses only where the source calls ``fmaf``.  The translation units compile in
+parallel; the library is built in-tree next to this file.
 """
 from __future__ import annotations
 
@@ -22,8 +23,11 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
           "-Xptxas", "-warn-spills"]
+# No automatic FMA contraction anywhere: the FP64 unit then matches the
+# oracle's one-rounding-per-operation order, and the FP32 unit fuses exactly
+# where the source says fmaf, so every kernel variant rounds identically.
 UNITS = {
-    "stage_f32.cu": [],
+    "stage_f32.cu": ["--fmad=false"],
     "stage_f64.cu": ["--fmad=false"],
     "hard_hydro.cu": [],
 }

@@ -167,7 +167,7 @@ int read_status(hard_hydro_s* h, cudaStream_t s) {
         e = cudaMemsetAsync(status_slot(h), 0, sizeof(int), s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return from_cuda(e);
-        return HARD_ENONPHYS;
+        return (st & 4) ? HARD_ETIMEOUT : HARD_ENONPHYS;   // bit 4: a bounded wait ran out
     }
     return HARD_OK;
 }

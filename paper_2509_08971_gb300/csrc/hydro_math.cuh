@@ -33,23 +33,46 @@ __device__ __forceinline__ double minmod(double a, double b) {
     return 0.0;
 }
 __device__ __forceinline__ float minmod(float a, float b) {
-    // equal sign bits -> min(|a|,|b|) with a's sign (0 if either is 0);
-    // different sign bits -> 0.  Same value as the FP64 rule on FP32 inputs.
-    float m = copysignf(fminf(fabsf(a), fabsf(b)), a);
-    return ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u) ? 0.0f : m;
+    // r = min(|a|,|b|) carrying the XOR of the two signs: r >= 0 exactly when
+    // the slopes agree in sign (or one is zero).  max(r, 0) with a's sign is
+    // then the minmod; on disagreement it is a signed zero, which leaves the
+    // face state q +- d/2 unchanged.  Three ALU operations.
+    float r;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return copysignf(fmaxf(r, 0.0f), a);
+}
+
+// Single-instruction approximate reciprocal and square root (a few ulp), used
+// by the FP32 path only.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ------------------------------------------------- fused multiply-adds --
+// Both element types are compiled without automatic FMA contraction, so the
+// rounding of every expression is fixed by the source and identical in every
+// kernel that uses these functions.  FP64 keeps a*b + c as two roundings (the
+// oracle's order); FP32 fuses it explicitly.
+__device__ __forceinline__ double madd(double a, double b, double c) { return a * b + c; }
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+
+// acc - diff / dx: FP64 divides (oracle order), FP32 multiplies by the
+// precomputed 1/dx it is handed instead.
+__device__ __forceinline__ double sub_over_dx(double acc, double diff, double dx) {
+    return acc - diff / dx;
+}
+__device__ __forceinline__ float sub_over_dx(float acc, float diff, float inv_dx) {
+    return fmaf(-diff, inv_dx, acc);
 }
 
 // ------------------------------------------------------- closure helpers --
-template <typename T> struct Num;
-template <> struct Num<double> {
-    __device__ static __forceinline__ double div(double a, double b) { return a / b; }
-    __device__ static __forceinline__ double sqrt_(double a) { return sqrt(a); }
-};
-template <> struct Num<float> {
-    __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-    __device__ static __forceinline__ float sqrt_(float a) { return sqrtf(a); }
-};
-
 // Conserved -> primitive W = (rho, u, v, w, p), p = (gamma-1)(E - rho|v|^2/2).
 __device__ __forceinline__ void cons_to_prim(const double U[NF], double gm1, double W[NF]) {
     double rho = U[0];
@@ -62,9 +85,9 @@ __device__ __forceinline__ void cons_to_prim(const double U[NF], double gm1, dou
 }
 __device__ __forceinline__ void cons_to_prim(const float U[NF], float gm1, float W[NF]) {
     float rho = U[0];
-    float ir = __frcp_rn(rho);
+    float ir = rcp_approx(rho);
     float u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-    float kin = 0.5f * (U[1] * u + U[2] * v + U[3] * w);
+    float kin = 0.5f * fmaf(U[1], u, fmaf(U[2], v, U[3] * w));
     W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
     W[4] = gm1 * (U[4] - kin);
 }
@@ -138,31 +161,34 @@ __device__ __forceinline__ void hllc_normal(const double WL[NF], const double WR
 // supersonic branches (F_L or F_R) without a branch.
 __device__ __forceinline__ void hllc_normal(const float WL[NF], const float WR[NF],
                                             float gamma, float gm1, float F[NF]) {
-    float rL = WL[0], uL = WL[1], pL = WL[4];
-    float rR = WR[0], uR = WR[1], pR = WR[4];
-    float irL = __frcp_rn(rL), irR = __frcp_rn(rR);
-    float cL = sqrtf(gamma * pL * irL);
-    float cR = sqrtf(gamma * pR * irR);
-    float SL = fminf(uL - cL, uR - cR);
-    float SR = fmaxf(uL + cL, uR + cR);
-    float mL = rL * (SL - uL);                 // < 0
-    float mR = rR * (SR - uR);                 // > 0
-    float Sstar = __fdividef(pR - pL + mL * uL - mR * uR, mL - mR);
-    bool left = Sstar >= 0.0f;
-    float r = left ? rL : rR, u = left ? uL : uR, p = left ? pL : pR;
-    float t1 = left ? WL[2] : WR[2], t2 = left ? WL[3] : WR[3];
-    float m = left ? mL : mR, ir = left ? irL : irR;
-    float SK = left ? SL : SR;
-    float s = left ? fminf(SL, 0.0f) : fmaxf(SR, 0.0f);
-    float E = p * __frcp_rn(gm1) + 0.5f * r * (u * u + t1 * t1 + t2 * t2);
-    float fac = __fdividef(m, SK - Sstar);     // rho_K (S_K - u_K) / (S_K - S*)
-    float mu = r * u;
-    float es = E * ir + (Sstar - u) * (Sstar + __fdividef(p, m));
-    F[0] = mu + s * (fac - r);
-    F[1] = mu * u + p + s * (fac * Sstar - mu);
-    F[2] = mu * t1 + s * (fac * t1 - r * t1);
-    F[3] = mu * t2 + s * (fac * t2 - r * t2);
-    F[4] = (E + p) * u + s * (fac * es - E);
+    const float rL = WL[0], uL = WL[1], pL = WL[4];
+    const float rR = WR[0], uR = WR[1], pR = WR[4];
+    const float irL = rcp_approx(rL), irR = rcp_approx(rR);
+    const float cL = sqrt_approx(gamma * pL * irL);
+    const float cR = sqrt_approx(gamma * pR * irR);
+    const float SL = fminf(uL - cL, uR - cR);
+    const float SR = fmaxf(uL + cL, uR + cR);
+    const float mL = rL * (SL - uL);                    // < 0
+    const float mR = rR * (SR - uR);                    // > 0
+    const float num = fmaf(-mR, uR, fmaf(mL, uL, pR - pL));
+    const float Sstar = num * rcp_approx(mL - mR);
+    const bool left = Sstar >= 0.0f;
+    const float r = left ? rL : rR, u = left ? uL : uR, p = left ? pL : pR;
+    const float t1 = left ? WL[2] : WR[2], t2 = left ? WL[3] : WR[3];
+    const float m = left ? mL : mR, ir = left ? irL : irR;
+    const float SK = left ? SL : SR;
+    const float s = left ? fminf(SL, 0.0f) : fmaxf(SR, 0.0f);
+    const float ke = fmaf(u, u, fmaf(t1, t1, t2 * t2));
+    const float E = fmaf(p, rcp_approx(gm1), 0.5f * r * ke);
+    const float fac = m * rcp_approx(SK - Sstar);       // rho_K (S_K - u_K) / (S_K - S*)
+    const float mu = r * u;
+    const float es = fmaf(E, ir, (Sstar - u) * fmaf(p, rcp_approx(m), Sstar));
+    const float dr = fac - r;                           // (U*_K - U_K) per unit transported
+    F[0] = fmaf(s, dr, mu);
+    F[1] = fmaf(s, fmaf(fac, Sstar, -mu), fmaf(mu, u, p));
+    F[2] = fmaf(s, dr * t1, mu * t1);
+    F[3] = fmaf(s, dr * t2, mu * t2);
+    F[4] = fmaf(s, fmaf(fac, es, -E), (E + p) * u);
 }
 
 // Face flux through a face whose normal is physical axis AX, from the
@@ -192,18 +218,14 @@ __device__ __forceinline__ void face_flux4(const T q0[NF], const T q1[NF], const
     for (int f = 0; f < NF; ++f) {
         T dqi = minmod(q1[f] - q0[f], q2[f] - q1[f]);
         T dqi1 = minmod(q2[f] - q1[f], q3[f] - q2[f]);
-        qL[f] = q1[f] + T(0.5) * dqi;
-        qR[f] = q2[f] - T(0.5) * dqi1;
+        qL[f] = madd(T(0.5), dqi, q1[f]);
+        qR[f] = madd(T(-0.5), dqi1, q2[f]);
     }
     hllc_axis<AX>(qL, qR, gamma, gm1, F);
 }
 
 // Signal rate of one cell: sum over the active axes of (|v_d| + c)/dx_d.
 // `act` and `dx` are indexed by physical axis; summed in physical order.
-template <typename T>
-__device__ __forceinline__ T cell_rate(const T W[NF], T gamma, const bool act[3],
-                                       const T inv_or_dx[3]);
-
 __device__ __forceinline__ double cell_rate(const double W[NF], double gamma, const bool act[3],
                                             const double dx[3]) {
     double cs = sqrt(gamma * W[4] / W[0]);
@@ -215,11 +237,11 @@ __device__ __forceinline__ double cell_rate(const double W[NF], double gamma, co
 }
 __device__ __forceinline__ float cell_rate(const float W[NF], float gamma, const bool act[3],
                                            const float inv_dx[3]) {
-    float cs = sqrtf(gamma * W[4] * __frcp_rn(W[0]));
+    float cs = sqrt_approx(gamma * W[4] * rcp_approx(W[0]));
     float r = 0.0f;
-    if (act[0]) r += (fabsf(W[1]) + cs) * inv_dx[0];
-    if (act[1]) r += (fabsf(W[2]) + cs) * inv_dx[1];
-    if (act[2]) r += (fabsf(W[3]) + cs) * inv_dx[2];
+    if (act[0]) r = fmaf(fabsf(W[1]) + cs, inv_dx[0], r);
+    if (act[1]) r = fmaf(fabsf(W[2]) + cs, inv_dx[1], r);
+    if (act[2]) r = fmaf(fabsf(W[3]) + cs, inv_dx[2], r);
     return r;
 }
 

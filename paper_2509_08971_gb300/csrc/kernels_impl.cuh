@@ -151,8 +151,8 @@ __global__ void pointwise_stage_kernel(const T* U0, const T* Uc, T* Uo, long lon
     const T d = (T)(dt_dev ? *dt_dev : dt);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n5;
          q += (long long)gridDim.x * blockDim.x) {
-        T L = T(0);
-        Uo[q] = stage == 1 ? Uc[q] + d * L : T(0.5) * U0[q] + T(0.5) * (Uc[q] + d * L);
+        const T L = T(0);
+        Uo[q] = stage == 1 ? madd(d, L, Uc[q]) : madd(T(0.5), U0[q], T(0.5) * madd(d, L, Uc[q]));
     }
 }
 

@@ -1,4 +1,5 @@
-// FP32 instantiation of the stage, rate and totals kernels.
+// FP32 instantiation of the stage, rate and totals kernels.  Built with
+// --fmad=false: multiply-adds are fused only where the source calls fmaf.
 #define HH_T float
 #define HH_SUFFIX f32
 #include "kernels_impl.cuh"

@@ -44,10 +44,6 @@ struct StageArgs {
     const CUtensorMap* tmap;          // TMA descriptor of Uc (fused variant)
 };
 
-// Flux difference scaled by the cell width: FP64 divides, FP32 multiplies by 1/dx.
-__device__ __forceinline__ double over_dx(double a, double d) { return a / d; }
-__device__ __forceinline__ float over_dx(float a, float d) { return a * d; }
-
 // Boundary map of one kernel axis: m in [-2, n+1] -> interior index, flip set
 // for a reflecting wall.  Indices beyond the ghost layers (ragged tiles only)
 // clamp to any valid cell; their values feed faces nobody uses.
@@ -181,10 +177,10 @@ stage_kernel(const StageArgs<T> A) {
             for (int f = 0; f < NF; ++f) {
                 qj[f] = Ps[(f * HY + hyc) * HX + tx + 2];
                 T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fx[(f * TY + ty) * (TX + 1) + tx];
-                Dj[f] = T(0) - over_dx(a, A.dxk[0]);
+                Dj[f] = sub_over_dx(T(0), a, A.dxk[0]);
                 if (DIM >= 2) {
                     T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fy[(f * (TY + 1) + ty) * TX + tx];
-                    Dj[f] = Dj[f] - over_dx(b, A.dxk[1]);
+                    Dj[f] = sub_over_dx(Dj[f], b, A.dxk[1]);
                 }
             }
         } else {
@@ -205,8 +201,8 @@ stage_kernel(const StageArgs<T> A) {
                 for (int f = 0; f < NF; ++f) {
                     dcur[f] = qj[f] - qm1[f];
                     T d = minmod(dprev[f], dcur[f]);
-                    qR[f] = qm1[f] - T(0.5) * d;
-                    qL[f] = qm1[f] + T(0.5) * d;
+                    qR[f] = madd(T(-0.5), d, qm1[f]);
+                    qL[f] = madd(T(0.5), d, qm1[f]);
                 }
                 if (cnt >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, Fz);   // face j-3/2
 #pragma unroll
@@ -218,7 +214,7 @@ stage_kernel(const StageArgs<T> A) {
             k = cnt >= 4 ? j - 2 : -1;
             if (k >= 0) {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) L[f] = Da[f] - over_dx(Fz[f] - Fzp[f], A.dxk[2]);
+                for (int f = 0; f < NF; ++f) L[f] = sub_over_dx(Da[f], Fz[f] - Fzp[f], A.dxk[2]);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -241,10 +237,10 @@ stage_kernel(const StageArgs<T> A) {
             for (int f = 0; f < NF; ++f) {
                 T uc = A.Uc[f * A.N + c];
                 if (A.stage == 1) {
-                    Uo[f] = uc + dt * L[f];
+                    Uo[f] = madd(dt, L[f], uc);
                 } else {
                     T u0 = A.U0[f * A.N + c];
-                    Uo[f] = T(0.5) * u0 + T(0.5) * (uc + dt * L[f]);
+                    Uo[f] = madd(T(0.5), u0, T(0.5) * madd(dt, L[f], uc));
                 }
                 A.Uo[f * A.N + c] = Uo[f];
             }

@@ -30,18 +30,32 @@ struct TmaLayout {
     static constexpr int D = 5;                         // ring slots
     static constexpr int P = 2;                         // planes loaded ahead
     static constexpr int HXC = TX + 8, HYC = TY + 4;    // conserved box
-    static constexpr int MAIN = NF * HYC * HXC;
-    static constexpr int XS = NF * HYC * 4;             // x strip box
-    static constexpr int YS = NF * 2 * HXC;             // y strip box
+    // every TMA destination starts on a 128-byte boundary
+    static constexpr int A128 = 128 / (int)sizeof(T);
+    static constexpr int pad(int n) { return (n + A128 - 1) / A128 * A128; }
+    static constexpr int MAIN = pad(NF * HYC * HXC);
+    static constexpr int XS = pad(NF * HYC * 4);        // x strip box
+    static constexpr int YS = pad(NF * 2 * HXC);        // y strip box
+    static constexpr int XLO = MAIN, XHI = MAIN + XS, YLO = MAIN + 2 * XS, YHI = YLO + YS;
     static constexpr int SLOT = MAIN + 2 * XS + 2 * YS; // elements per slot
     static constexpr int HXP = TX + 4, HYP = TY + 4;    // primitive plane
     static constexpr int NP = NF * HYP * HXP;
     static constexpr int NFX = NF * TY * (TX + 1);
     static constexpr int NFY = NF * (TY + 1) * TX;
-    static constexpr size_t BAR_BYTES = 128;
-    static constexpr size_t bytes = BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NP + NFX + NFY);
-    static_assert((MAIN * sizeof(T)) % 16 == 0 && (XS * sizeof(T)) % 16 == 0 &&
-                  (YS * sizeof(T)) % 16 == 0, "TMA destinations must stay 16-byte aligned");
+    static constexpr size_t BAR_BYTES = 128;            // D mbarriers, then the ring
+    static constexpr size_t RED_BYTES = (TX * TY / 32) * (NF + 1) * 8;
+    static constexpr size_t data_bytes =
+        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NP + NFX + NFY) + RED_BYTES;
+    static constexpr size_t bytes = data_bytes + 128;   // slack to align the base by hand
+    static constexpr uint32_t MAIN_BYTES = sizeof(T) * NF * HYC * HXC;
+    static constexpr uint32_t XS_BYTES = sizeof(T) * NF * HYC * 4;
+    static constexpr uint32_t YS_BYTES = sizeof(T) * NF * 2 * HXC;
+    static constexpr size_t RED_OFF = BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NP + NFX + NFY);
+    static_assert((SLOT * sizeof(T)) % 128 == 0 && (XLO * sizeof(T)) % 128 == 0 &&
+                  (XHI * sizeof(T)) % 128 == 0 && (YLO * sizeof(T)) % 128 == 0 &&
+                  (YHI * sizeof(T)) % 128 == 0 && BAR_BYTES % 128 == 0,
+                  "every TMA destination must start on a 128-byte boundary");
+    static_assert(RED_OFF % 8 == 0, "reduction scratch must be 8-byte aligned");
     static_assert(P < D - 2, "a slot is read until two planes after it lands");
 };
 
@@ -53,14 +67,19 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     constexpr int D = L::D, P = L::P;
     constexpr int HXC = L::HXC, HYC = L::HYC, HXP = L::HXP, HYP = L::HYP;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    T* ring = reinterpret_cast<T*>(smem_raw + L::BAR_BYTES);
+    // all shared memory is dynamic; the base is rounded up to 128 bytes here
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base);
+    int* s_abort_p = reinterpret_cast<int*>(base + 8 * D);
+    T* ring = reinterpret_cast<T*>(base + L::BAR_BYTES);
     T* Ps = ring + D * L::SLOT;                       // [NF][HYP][HXP]
     T* Fx = Ps + L::NP;                               // [NF][TY][TX+1]
     T* Fy = Fx + L::NFX;                              // [NF][TY+1][TX]
-    __shared__ double red_tot[NT / 32][NF];
-    __shared__ unsigned long long red_rate[NT / 32];
-    __shared__ int s_abort;
+    double (*red_tot)[NF] = reinterpret_cast<double (*)[NF]>(Fy + L::NFY);
+    unsigned long long* red_rate =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<double*>(red_tot) + (NT / 32) * NF);
+    int& s_abort = *s_abort_p;
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -78,9 +97,9 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     const bool px_lo = xlo && A.bc_lo[0] == 0, px_hi = xhi && A.bc_hi[0] == 0;
     const bool py_lo = ylo && A.bc_lo[1] == 0, py_hi = yhi && A.bc_hi[1] == 0;
     const bool edge = xlo || xhi || ylo || yhi;
-    const uint32_t tx_bytes = (uint32_t)sizeof(T) *
-        (L::MAIN + (px_lo ? L::XS : 0) + (px_hi ? L::XS : 0) + (py_lo ? L::YS : 0) +
-         (py_hi ? L::YS : 0));
+    const uint32_t tx_bytes = L::MAIN_BYTES + (px_lo ? L::XS_BYTES : 0) +
+                              (px_hi ? L::XS_BYTES : 0) + (py_lo ? L::YS_BYTES : 0) +
+                              (py_hi ? L::YS_BYTES : 0);
 
     const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
     const T gamma = A.gamma, gm1 = A.gm1;
@@ -93,10 +112,10 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         const int jj = bc_map(jbeg + it, nz, A.bc_lo[2], A.bc_hi[2], fz);
         mbar_arrive_expect_tx(bar, tx_bytes);
         tma_load_4d(s, &M.main, x0 - 4, y0 - 2, jj, 0, bar);
-        if (px_lo) tma_load_4d(s + L::MAIN, &M.xstrip, nx - 4, y0 - 2, jj, 0, bar);
-        if (px_hi) tma_load_4d(s + L::MAIN + L::XS, &M.xstrip, 0, y0 - 2, jj, 0, bar);
-        if (py_lo) tma_load_4d(s + L::MAIN + 2 * L::XS, &M.ystrip, x0 - 4, ny - 2, jj, 0, bar);
-        if (py_hi) tma_load_4d(s + L::MAIN + 2 * L::XS + L::YS, &M.ystrip, x0 - 4, 0, jj, 0, bar);
+        if (px_lo) tma_load_4d(s + L::XLO, &M.xstrip, nx - 4, y0 - 2, jj, 0, bar);
+        if (px_hi) tma_load_4d(s + L::XHI, &M.xstrip, 0, y0 - 2, jj, 0, bar);
+        if (py_lo) tma_load_4d(s + L::YLO, &M.ystrip, x0 - 4, ny - 2, jj, 0, bar);
+        if (py_hi) tma_load_4d(s + L::YHI, &M.ystrip, x0 - 4, 0, jj, 0, bar);
     };
 
     if (tid == 0) {
@@ -154,7 +173,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                         if (gx > nx + 1) {
                             use = false;              // beyond the ghosts of a ragged tile
                         } else if (bc == 0) {
-                            src = S + L::MAIN + (gx < 0 ? 0 : L::XS);
+                            src = S + (gx < 0 ? L::XLO : L::XHI);
                             sx = gx < 0 ? gx + 4 : gx - nx;
                             pitch = 4;
                             fstride = HYC * 4;
@@ -169,7 +188,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                         if (gy > ny + 1) {
                             use = false;
                         } else if (bc == 0) {
-                            src = S + L::MAIN + 2 * L::XS + (gy < 0 ? 0 : L::YS);
+                            src = S + (gy < 0 ? L::YLO : L::YHI);
                             sy = gy < 0 ? gy + 2 : gy - ny;
                             fstride = 2 * HXC;
                         } else if (bc == 1) {
@@ -243,8 +262,8 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                 qj[f] = Ps[(f * HYP + ty + 2) * HXP + tx + 2];
                 const T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fx[(f * TY + ty) * (TX + 1) + tx];
                 const T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fy[(f * (TY + 1) + ty) * TX + tx];
-                Dj[f] = T(0) - over_dx(a, A.dxk[0]);
-                Dj[f] = Dj[f] - over_dx(b, A.dxk[1]);
+                Dj[f] = sub_over_dx(T(0), a, A.dxk[0]);
+                Dj[f] = sub_over_dx(Dj[f], b, A.dxk[1]);
             }
             if (own) bad |= nonphys(qj);
         } else {
@@ -270,8 +289,8 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T d = minmod(dprev[f], dcur[f]);
-                qR[f] = qm1[f] - T(0.5) * d;
-                qL[f] = qm1[f] + T(0.5) * d;
+                qR[f] = madd(T(-0.5), d, qm1[f]);
+                qL[f] = madd(T(0.5), d, qm1[f]);
             }
             if (it >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, Fz);      // face j-3/2
 #pragma unroll
@@ -283,9 +302,10 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             T Uo[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                const T Lf = Da[f] - over_dx(Fz[f] - Fzp[f], A.dxk[2]);
+                const T Lf = sub_over_dx(Da[f], Fz[f] - Fzp[f], A.dxk[2]);
                 const T uc = Sk[(f * HYC + ty + 2) * HXC + tx + 4];
-                Uo[f] = A.stage == 1 ? uc + dt * Lf : T(0.5) * u0[f] + T(0.5) * (uc + dt * Lf);
+                Uo[f] = A.stage == 1 ? madd(dt, Lf, uc)
+                                     : madd(T(0.5), u0[f], T(0.5) * madd(dt, Lf, uc));
                 A.Uo[f * A.N + c] = Uo[f];
             }
             if (A.rate_slot) {
