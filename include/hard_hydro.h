@@ -130,6 +130,26 @@ int hard_hydro_advance_host(hard_hydro_t h, const void* U_host_in, void* U_host_
  * warp level up in a fixed order (deterministic).  Synchronises the stream. */
 int hard_hydro_totals(hard_hydro_t h, const void* U, double out5[5], void* stream);
 
+/* hard_hydro_step with no device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc when they
+ * step (code running during CUDA-graph stream capture, hosts whose device
+ * memory is pre-reserved by another allocator or runtime).  It computes
+ * exactly what hard_hydro_step computes with the handle's element type,
+ * kernel and tile, but keeps the intermediate stage in a fixed 64 MiB
+ * (HARD_NOALLOC_SCRATCH_BYTES) device array that the library holds on every
+ * GPU that loads it until process exit, and touches no handle scratch.
+ *   - Meshes whose state (5 * cells * element size) exceeds the array return
+ *     HARD_EUNSUPPORTED (FP32: 3,355,443 cells; FP64: 1,677,721 cells).
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (other streams
+ *     or host threads) race.  Its status word is cleared per call and is not
+ *     reported; use hard_hydro_step and hard_hydro_get_error for that check.
+ *   - U_out may alias U_in; U pointers are device pointers, 16-byte aligned. */
+#define HARD_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
+int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U_out, double dt,
+                            void* stream);
+
 /* Device status flag: returns HARD_OK or HARD_ENONPHYS and clears the flag.
  * Synchronises the handle's last stream. */
 int hard_hydro_get_error(hard_hydro_t h);

@@ -54,6 +54,7 @@ def _declare(lib):
         "hard_hydro_advance_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
                                                    ctypes.c_double, _dp, _vp]),
         "hard_hydro_totals": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
+        "hard_hydro_step_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
         "hard_hydro_get_error": (ctypes.c_int, [_vp]),
         "hard_hydro_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "hard_hydro_destroy": (None, [_vp]),
@@ -136,6 +137,12 @@ def hard_hydro_totals(h, U, stream):
     out = (ctypes.c_double * 5)()
     rc = lib().hard_hydro_totals(h, U, out, stream)
     return rc, list(out)
+
+
+def hard_hydro_step_noalloc(h, U_in, U_out, dt, stream):
+    """hard_hydro_step without any device allocation: the intermediate stage
+    lives in the library's fixed 64 MiB device array (see the C header)."""
+    return lib().hard_hydro_step_noalloc(h, U_in, U_out, float(dt), stream)
 
 
 def hard_hydro_get_error(h):

@@ -30,6 +30,7 @@ UNITS = {
     "stage_f32.cu": ["--fmad=false"],
     "stage_f64.cu": ["--fmad=false"],
     "hard_hydro.cu": [],
+    "noalloc.cu": [],
 }
 
 

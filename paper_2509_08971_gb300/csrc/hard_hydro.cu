@@ -479,3 +479,17 @@ void hard_hydro_destroy(hard_hydro_t h) {
 }
 
 }  // extern "C"
+
+namespace hh {
+
+// Read-only view of a handle for the library's other translation units.
+bool handle_view(hard_hydro_t h, const MeshDesc** mesh, int* dtype, int* kernel, int* tile) {
+    if (!h) return false;
+    *mesh = &h->mesh;
+    *dtype = h->dtype;
+    *kernel = h->kernel;
+    *tile = tile_of(h);
+    return true;
+}
+
+}  // namespace hh

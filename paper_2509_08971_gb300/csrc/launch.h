@@ -76,6 +76,12 @@ inline long long totals_blocks() { return TOTALS_BLOCKS; }
 cudaError_t launch_totals_f32(const MeshDesc& m, const void* U, double* partial, cudaStream_t s);
 cudaError_t launch_totals_f64(const MeshDesc& m, const void* U, double* partial, cudaStream_t s);
 
+// Read-only view of a handle (hard_hydro.cu); false for a NULL handle.
+}  // namespace hh
+struct hard_hydro_s;
+namespace hh {
+bool handle_view(hard_hydro_s* h, const MeshDesc** mesh, int* dtype, int* kernel, int* tile);
+
 // Shared helpers (hard_hydro.cu).
 cudaError_t launch_finalize_dt(unsigned long long* rate_slot, double cfl, double t_end,
                                double* t_dev, double* dt_dev, double* dt_log, int step,
