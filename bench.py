@@ -207,6 +207,8 @@ def main():
     m32 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32,
                        kernel=hh.HARD_KERNEL_FUSED)
     U = torch.tensor(U64, dtype=torch.float32, device=dev)
+    from paper_2509_08971_gb300 import autotune
+    tuned = autotune.tune(m32, U, kernel=hh.HARD_KERNEL_FUSED, reps=5)   # outside the timed region
     t_dev = torch.zeros((), dtype=torch.float64, device=dev)
     tot_log = torch.zeros((max(args.steps, args.warmup, 3), 5), dtype=torch.float64, device=dev)
 
@@ -255,7 +257,8 @@ def main():
     achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "stage_kernel<float,32,8,3> (mean of stage 1 and stage 2)",
+                "kernel": "stage_tma_kernel<float,%d,%d> z-chunk %d (mean of stage 1 and stage 2)"
+                          % tuple(tuned["info"][:3]),
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": stage_ms}
     del U1, U2
 
@@ -298,6 +301,7 @@ def main():
         "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "global_cells": world * cells,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "state 336 MB > 129 MB L2 (no flush needed)", "kernel": "fused",
+                   "tile": {"chosen": tuned["info"], "ms_per_stage": tuned["ms"]},
                    "step": "CFL rate + stage 1 + stage 2 + FP64 totals"},
         "roofline": roofline,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": k64,

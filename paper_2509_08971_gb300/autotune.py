@@ -1,0 +1,78 @@
+"""Tile autotuner for the stage kernel.
+
+For a mesh, element type and kernel variant it times every tile
+configuration the library offers (tile extents, threads per block, z-chunk
+length; `hard_hydro_tile_info`) on the caller's own state: each candidate
+runs a few untimed stage-1/stage-2 pairs, then a timed batch bracketed by
+CUDA events on the current stream.  The fastest tile is set on the handle and
+remembered in a JSON cache keyed by mesh shape, boundary kinds, element type
+and kernel (``HARD_HYDRO_TUNE_CACHE`` names the file; unset = in-memory only).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import HardHydro
+
+_memory: dict[str, int] = {}
+
+
+def _key(m: HardHydro, kernel: int) -> str:
+    return f"{m.shape}|{m.dtype}|k{kernel}|g{m.gamma}"
+
+
+def _load_cache(path):
+    if not path or not os.path.exists(path):
+        return {}
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def tune(m: HardHydro, U, kernel: int = 0, reps: int = 10, warmup: int = 2,
+         cache_path: str | None = None, verbose: bool = False) -> dict:
+    """Pick the fastest tile for handle `m` on state `U` and set it.
+    Returns {"tile": best, "info": (tx, ty, zc, threads), "ms": {tile: ms}}."""
+    torch = m.torch
+    cache_path = cache_path if cache_path is not None else os.environ.get("HARD_HYDRO_TUNE_CACHE")
+    key = _key(m, kernel)
+    disk = _load_cache(cache_path)
+    if key in disk or key in _memory:
+        best = int(disk.get(key, _memory.get(key)))
+        m.set_kernel(kernel, best)
+        return {"tile": best, "info": m.tile_info(best), "ms": {}, "cached": True}
+    stream = torch.cuda.current_stream()
+    U1 = torch.empty_like(U)
+    U2 = torch.empty_like(U)
+    dt = m.cfl_dt(U, 0.4)
+    times = {}
+    for tile in range(m.tile_count()):
+        m.set_kernel(kernel, tile)
+        for _ in range(warmup):
+            m.stage(1, None, U, dt, out=U1)
+            m.stage(2, U, U1, dt, out=U2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            m.stage(1, None, U, dt, out=U1)
+            m.stage(2, U, U1, dt, out=U2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[tile] = e0.elapsed_time(e1) / (2 * reps)
+        if verbose:
+            print(f"tile {tile} {m.tile_info(tile)}: {times[tile]:.4f} ms per stage")
+    best = min(times, key=times.get)
+    m.set_kernel(kernel, best)
+    _memory[key] = best
+    if cache_path:
+        disk[key] = best
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(disk, fh, indent=1)
+        os.replace(tmp, cache_path)
+    return {"tile": best, "info": m.tile_info(best), "ms": times, "cached": False}

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "vec2.cuh"
+
 namespace hh {
 
 constexpr int NF = 5;
@@ -32,28 +34,7 @@ __device__ __forceinline__ double minmod(double a, double b) {
     if (a < 0.0 && b < 0.0) return (-a <= -b) ? a : b;
     return 0.0;
 }
-__device__ __forceinline__ float minmod(float a, float b) {
-    // r = min(|a|,|b|) carrying the XOR of the two signs: r >= 0 exactly when
-    // the slopes agree in sign (or one is zero).  max(r, 0) with a's sign is
-    // then the minmod; on disagreement it is a signed zero, which leaves the
-    // face state q +- d/2 unchanged.  Three ALU operations.
-    float r;
-    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
-    return copysignf(fmaxf(r, 0.0f), a);
-}
-
-// Single-instruction approximate reciprocal and square root (a few ulp), used
-// by the FP32 path only.
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+__device__ __forceinline__ float minmod(float a, float b) { return vminmod(a, b); }
 
 // ------------------------------------------------- fused multiply-adds --
 // Both element types are compiled without automatic FMA contraction, so the
@@ -85,7 +66,7 @@ __device__ __forceinline__ void cons_to_prim(const double U[NF], double gm1, dou
 }
 __device__ __forceinline__ void cons_to_prim(const float U[NF], float gm1, float W[NF]) {
     float rho = U[0];
-    float ir = rcp_approx(rho);
+    float ir = vrcp(rho);
     float u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
     float kin = 0.5f * fmaf(U[1], u, fmaf(U[2], v, U[3] * w));
     W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
@@ -102,7 +83,8 @@ __device__ __forceinline__ bool nonphys(const T W[NF]) {
 // FP64: the four-branch textbook form, one fixed evaluation order.
 // Wn = (rho, un, t1, t2, p) in the frame whose normal is component 1.
 __device__ __forceinline__ void hllc_normal(const double WL[NF], const double WR[NF],
-                                            double gamma, double gm1, double F[NF]) {
+                                            double gamma, double gm1, double /*igm1*/,
+                                            double F[NF]) {
     double UL[NF], FL[NF], UR[NF], FR[NF];
     {
         double rho = WL[0], un = WL[1], t1 = WL[2], t2 = WL[3], p = WL[4];
@@ -156,39 +138,11 @@ __device__ __forceinline__ void hllc_normal(const double WL[NF], const double WR
     }
 }
 
-// FP32: one-sided form F = F_K + s (U*_K - U_K), K = L when S* >= 0 else R,
-// s = min(S_L, 0) for K = L and max(S_R, 0) for K = R.  s = 0 reproduces the
-// supersonic branches (F_L or F_R) without a branch.
-__device__ __forceinline__ void hllc_normal(const float WL[NF], const float WR[NF],
-                                            float gamma, float gm1, float F[NF]) {
-    const float rL = WL[0], uL = WL[1], pL = WL[4];
-    const float rR = WR[0], uR = WR[1], pR = WR[4];
-    const float irL = rcp_approx(rL), irR = rcp_approx(rR);
-    const float cL = sqrt_approx(gamma * pL * irL);
-    const float cR = sqrt_approx(gamma * pR * irR);
-    const float SL = fminf(uL - cL, uR - cR);
-    const float SR = fmaxf(uL + cL, uR + cR);
-    const float mL = rL * (SL - uL);                    // < 0
-    const float mR = rR * (SR - uR);                    // > 0
-    const float num = fmaf(-mR, uR, fmaf(mL, uL, pR - pL));
-    const float Sstar = num * rcp_approx(mL - mR);
-    const bool left = Sstar >= 0.0f;
-    const float r = left ? rL : rR, u = left ? uL : uR, p = left ? pL : pR;
-    const float t1 = left ? WL[2] : WR[2], t2 = left ? WL[3] : WR[3];
-    const float m = left ? mL : mR, ir = left ? irL : irR;
-    const float SK = left ? SL : SR;
-    const float s = left ? fminf(SL, 0.0f) : fmaxf(SR, 0.0f);
-    const float ke = fmaf(u, u, fmaf(t1, t1, t2 * t2));
-    const float E = fmaf(p, rcp_approx(gm1), 0.5f * r * ke);
-    const float fac = m * rcp_approx(SK - Sstar);       // rho_K (S_K - u_K) / (S_K - S*)
-    const float mu = r * u;
-    const float es = fmaf(E, ir, (Sstar - u) * fmaf(p, rcp_approx(m), Sstar));
-    const float dr = fac - r;                           // (U*_K - U_K) per unit transported
-    F[0] = fmaf(s, dr, mu);
-    F[1] = fmaf(s, fmaf(fac, Sstar, -mu), fmaf(mu, u, p));
-    F[2] = fmaf(s, dr * t1, mu * t1);
-    F[3] = fmaf(s, dr * t2, mu * t2);
-    F[4] = fmaf(s, fmaf(fac, es, -E), (E + p) * u);
+// FP32: the one-sided form of vec2.cuh (hllc_core), F = F_K + s (U*_K - U_K),
+// with s = 0 reproducing the supersonic branches without a branch.
+__device__ __forceinline__ void hllc_normal(const float WL[NF], const float WR[NF], float gamma,
+                                            float /*gm1*/, float igm1, float F[NF]) {
+    hllc_core<float>(WL, WR, gamma, igm1, F);
 }
 
 // Face flux through a face whose normal is physical axis AX, from the
@@ -196,13 +150,13 @@ __device__ __forceinline__ void hllc_normal(const float WL[NF], const float WR[N
 //   dq_m = minmod(q_m - q_{m-1}, q_{m+1} - q_m)
 //   q_L = q_i + dq_i/2,   q_R = q_{i+1} - dq_{i+1}/2,   F = HLLC(q_L, q_R).
 template <int AX, typename T>
-__device__ __forceinline__ void hllc_axis(const T qL[NF], const T qR[NF], T gamma, T gm1,
+__device__ __forceinline__ void hllc_axis(const T qL[NF], const T qR[NF], T gamma, T gm1, T igm1,
                                           T F[NF]) {
     using R = Rot<AX>;
     T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
     T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
     T Fn[NF];
-    hllc_normal(WL, WR, gamma, gm1, Fn);
+    hllc_normal(WL, WR, gamma, gm1, igm1, Fn);
     F[0] = Fn[0];
     F[R::n] = Fn[1];
     F[R::t1] = Fn[2];
@@ -210,18 +164,27 @@ __device__ __forceinline__ void hllc_axis(const T qL[NF], const T qR[NF], T gamm
     F[4] = Fn[4];
 }
 
-template <int AX, typename T>
-__device__ __forceinline__ void face_flux4(const T q0[NF], const T q1[NF], const T q2[NF],
-                                           const T q3[NF], T gamma, T gm1, T F[NF]) {
-    T qL[NF], qR[NF];
+template <int AX>
+__device__ __forceinline__ void face_flux4(const double q0[NF], const double q1[NF],
+                                           const double q2[NF], const double q3[NF], double gamma,
+                                           double gm1, double igm1, double F[NF]) {
+    double qL[NF], qR[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        T dqi = minmod(q1[f] - q0[f], q2[f] - q1[f]);
-        T dqi1 = minmod(q2[f] - q1[f], q3[f] - q2[f]);
-        qL[f] = madd(T(0.5), dqi, q1[f]);
-        qR[f] = madd(T(-0.5), dqi1, q2[f]);
+        double dqi = minmod(q1[f] - q0[f], q2[f] - q1[f]);
+        double dqi1 = minmod(q2[f] - q1[f], q3[f] - q2[f]);
+        qL[f] = madd(0.5, dqi, q1[f]);
+        qR[f] = madd(-0.5, dqi1, q2[f]);
     }
-    hllc_axis<AX>(qL, qR, gamma, gm1, F);
+    hllc_axis<AX>(qL, qR, gamma, gm1, igm1, F);
+}
+template <int AX>
+__device__ __forceinline__ void face_flux4(const float q0[NF], const float q1[NF],
+                                           const float q2[NF], const float q3[NF], float gamma,
+                                           float gm1, float igm1, float F[NF]) {
+    float qL[NF], qR[NF];
+    plm_faces<float>(q0, q1, q2, q3, qL, qR);
+    hllc_axis<AX>(qL, qR, gamma, gm1, igm1, F);
 }
 
 // Signal rate of one cell: sum over the active axes of (|v_d| + c)/dx_d.
@@ -237,7 +200,7 @@ __device__ __forceinline__ double cell_rate(const double W[NF], double gamma, co
 }
 __device__ __forceinline__ float cell_rate(const float W[NF], float gamma, const bool act[3],
                                            const float inv_dx[3]) {
-    float cs = sqrt_approx(gamma * W[4] * rcp_approx(W[0]));
+    float cs = vsqrt(gamma * W[4] * vrcp(W[0]));
     float r = 0.0f;
     if (act[0]) r = fmaf(fabsf(W[1]) + cs, inv_dx[0], r);
     if (act[1]) r = fmaf(fabsf(W[2]) + cs, inv_dx[1], r);

@@ -35,6 +35,7 @@ StageArgs<T> make_args(const MeshDesc& m, const TileDesc& td, const StageCall& c
     }
     A.gamma = (T)m.gamma;
     A.gm1 = (T)(m.gamma - 1.0);
+    A.igm1 = (T)(1.0 / (m.gamma - 1.0));
     A.dt = c.dt;
     A.dt_dev = c.dt_dev;
     A.stage = c.stage;

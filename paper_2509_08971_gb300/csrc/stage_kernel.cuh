@@ -31,6 +31,7 @@ struct StageArgs {
     int n[3];                     // kernel-axis extents
     int bc_lo[3], bc_hi[3];       // boundary kind per kernel axis
     T gamma, gm1;
+    T igm1;                       // 1/(gamma-1), rounded once on the host (FP32 path)
     T dxk[3];                     // per kernel axis: dx (FP64) or 1/dx (FP32)
     T rdx[3];                     // per physical axis, same convention
     bool act[3];                  // per physical axis: active
@@ -115,7 +116,7 @@ stage_kernel(const StageArgs<T> A) {
     const int z0 = DIM == 3 ? blockIdx.z * A.zchunk : 0;
     const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.n[2]) : 1;
     const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
-    const T gamma = A.gamma, gm1 = A.gm1;
+    const T gamma = A.gamma, gm1 = A.gm1, igm1 = A.igm1;
     bool bad = false;
     T rate_max = T(0);
     T tot[NF] = {T(0), T(0), T(0), T(0), T(0)};
@@ -153,7 +154,7 @@ stage_kernel(const StageArgs<T> A) {
 #pragma unroll
                     for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HY + hy) * HX + fx + s];
                 T F[NF];
-                face_flux4<PX>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+                face_flux4<PX>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + fx] = F[f];
             }
@@ -166,7 +167,7 @@ stage_kernel(const StageArgs<T> A) {
 #pragma unroll
                         for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HY + fy + s) * HX + col + 2];
                     T F[NF];
-                    face_flux4<PY>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+                    face_flux4<PY>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
                     for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + fy) * TX + col] = F[f];
                 }
@@ -204,7 +205,7 @@ stage_kernel(const StageArgs<T> A) {
                     qR[f] = madd(T(-0.5), d, qm1[f]);
                     qL[f] = madd(T(0.5), d, qm1[f]);
                 }
-                if (cnt >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, Fz);   // face j-3/2
+                if (cnt >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, igm1, Fz);   // face j-3/2
 #pragma unroll
                 for (int f = 0; f < NF; ++f) qLp[f] = qL[f];
             } else {

@@ -10,12 +10,19 @@
 //     the wrapped columns / rows on the same mbarrier; outflow and reflecting
 //     ghosts are read from the tile's own interior;
 //   * the conserved value of a cell, needed by the RK combine two planes
-//     later, is read back from the ring instead of from HBM.
+//     later, is read back from the ring instead of from HBM;
+//   * in FP32 each thread evaluates its x face and its y face together as the
+//     two lanes of paired f32x2 arithmetic (vec2.cuh), bit-identical per lane
+//     to the scalar path; the TX + TY faces on the tile's far edges take one
+//     more paired pass on the first TX threads.
 // The x start of every box is x0 - 4 (x0 a multiple of TX): 16-byte aligned
 // for 4- and 8-byte elements.
 #pragma once
+#include <type_traits>
+
 #include "stage_kernel.cuh"
 #include "tma.cuh"
+#include "vec2.cuh"
 
 namespace hh {
 
@@ -59,8 +66,10 @@ struct TmaLayout {
     static_assert(P < D - 2, "a slot is read until two planes after it lands");
 };
 
+// FP32 blocks of up to 256 threads run two per SM (register cap 128 per
+// thread); FP64 rings fill an SM's shared memory with one block.
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
 stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__ TmaMaps M) {
     using L = TmaLayout<T, TX, TY>;
     constexpr int NT = TX * TY;
@@ -102,7 +111,9 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                               (py_hi ? L::YS_BYTES : 0);
 
     const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
-    const T gamma = A.gamma, gm1 = A.gm1;
+    const T gamma = A.gamma, gm1 = A.gm1, igm1 = A.igm1;
+    constexpr int NPF = HXP * HYP;                    // one field of the primitive plane
+    constexpr int MAXE = (NPF + NT - 1) / NT;         // plane cells converted per thread
 
     auto slot_main = [&](int it) { return ring + (it % D) * L::SLOT; };
     auto issue = [&](int it) {
@@ -135,6 +146,54 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
 #pragma unroll
     for (int f = 0; f < NF; ++f) qm1[f] = dprev[f] = qLp[f] = Fzp[f] = Da[f] = Db[f] = T(0);
 
+    // Where each plane cell this thread converts comes from inside a ring slot:
+    // the same for every plane of the column, so worked out once and packed in
+    // one word per cell: bits 0-15 the slot offset of field 0 (0xFFFF: a cell
+    // no face reads), bits 16-27 the field stride, bit 28 / bit 29 negate
+    // rho*u / rho*v (reflecting walls).
+    static_assert(L::SLOT < 0xFFFF && HYC * HXC < 4096, "conversion map field widths");
+    int cv[MAXE];
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+        const int e = tid + q * NT;
+        const int cx = e % HXP - 2, cy = e / HXP - 2;
+        int src = (cy + 2) * HXC + cx + 4, fs = HYC * HXC, flip = 0;
+        if (edge) {
+            const int gx = x0 + cx, gy = y0 + cy;
+            const bool gxo = gx < 0 || gx >= nx, gyo = gy < 0 || gy >= ny;
+            if ((gxo && gyo) || gx > nx + 1 || gy > ny + 1) {
+                src = -1;                             // tile corner / beyond a ragged edge
+            } else if (gxo) {
+                const int bc = gx < 0 ? A.bc_lo[0] : A.bc_hi[0];
+                if (bc == 0) {
+                    src = (gx < 0 ? L::XLO : L::XHI) + (cy + 2) * 4 + (gx < 0 ? gx + 4 : gx - nx);
+                    fs = HYC * 4;
+                } else if (bc == 1) {
+                    src = (cy + 2) * HXC + (gx < 0 ? 0 : nx - 1) - x0 + 4;
+                } else {
+                    src = (cy + 2) * HXC + (gx < 0 ? -1 - gx : 2 * nx - 1 - gx) - x0 + 4;
+                    flip = 1;
+                }
+            } else if (gyo) {
+                const int bc = gy < 0 ? A.bc_lo[1] : A.bc_hi[1];
+                if (bc == 0) {
+                    src = (gy < 0 ? L::YLO : L::YHI) + (gy < 0 ? gy + 2 : gy - ny) * HXC + cx + 4;
+                    fs = 2 * HXC;
+                } else if (bc == 1) {
+                    src = ((gy < 0 ? 0 : ny - 1) - y0 + 2) * HXC + cx + 4;
+                } else {
+                    src = ((gy < 0 ? -1 - gy : 2 * ny - 1 - gy) - y0 + 2) * HXC + cx + 4;
+                    flip = 2;
+                }
+            }
+        }
+        cv[q] = (src < 0 ? 0xFFFF : src) | (fs << 16) | (flip << 28);
+    }
+
+    T u0c[NF], u0n[NF];                               // U0 of this and of the next update
+#pragma unroll
+    for (int f = 0; f < NF; ++f) u0c[f] = u0n[f] = T(0);
+
     int it = 0;
     for (; it < niter; ++it) {
         const int j = jbeg + it;
@@ -143,11 +202,11 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         if (tid == 0 && it + P < niter) issue(it + P);
         const int k = j - 2;                          // cell completed this iteration
         const bool upd = it >= 4 && own;
-        T u0[NF];
-        if (upd && A.stage == 2) {
-            const long long c = ((long long)k * ny + y) * nx + x;
+        if (A.stage == 2 && own && it >= 3 && it + 1 < niter) {
+            // U0 of the cell completed next iteration, one plane ahead of its use
+            const long long c = ((long long)(k + 1) * ny + y) * nx + x;
 #pragma unroll
-            for (int f = 0; f < NF; ++f) u0[f] = A.U0[f * A.N + c];
+            for (int f = 0; f < NF; ++f) u0n[f] = A.U0[f * A.N + c];
         }
         if (!mbar_wait(bars + (it % D), (uint32_t)((it / D) & 1))) {
             atomicOr(A.status, 4);
@@ -158,102 +217,126 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         T qj[NF], Dj[NF];
         if (xy) {
             // conserved -> primitive over the haloed (TX+4) x (TY+4) plane
-            for (int e = tid; e < HXP * HYP; e += NT) {
-                const int cx = e % HXP - 2, cy = e / HXP - 2;
-                const T* src = S;
-                int sx = cx + 4, sy = cy + 2, pitch = HXC, fstride = HYC * HXC;
-                bool flip_x = false, flip_y = false, use = true;
-                if (edge) {
-                    const int gx = x0 + cx, gy = y0 + cy;
-                    const bool gxo = gx < 0 || gx >= nx, gyo = gy < 0 || gy >= ny;
-                    if (gxo && gyo) {
-                        use = false;                  // corner: no face reads it
-                    } else if (gxo) {
-                        const int bc = gx < 0 ? A.bc_lo[0] : A.bc_hi[0];
-                        if (gx > nx + 1) {
-                            use = false;              // beyond the ghosts of a ragged tile
-                        } else if (bc == 0) {
-                            src = S + (gx < 0 ? L::XLO : L::XHI);
-                            sx = gx < 0 ? gx + 4 : gx - nx;
-                            pitch = 4;
-                            fstride = HYC * 4;
-                        } else if (bc == 1) {
-                            sx = (gx < 0 ? 0 : nx - 1) - x0 + 4;
-                        } else {
-                            sx = (gx < 0 ? -1 - gx : 2 * nx - 1 - gx) - x0 + 4;
-                            flip_x = true;
-                        }
-                    } else if (gyo) {
-                        const int bc = gy < 0 ? A.bc_lo[1] : A.bc_hi[1];
-                        if (gy > ny + 1) {
-                            use = false;
-                        } else if (bc == 0) {
-                            src = S + (gy < 0 ? L::YLO : L::YHI);
-                            sy = gy < 0 ? gy + 2 : gy - ny;
-                            fstride = 2 * HXC;
-                        } else if (bc == 1) {
-                            sy = (gy < 0 ? 0 : ny - 1) - y0 + 2;
-                        } else {
-                            sy = (gy < 0 ? -1 - gy : 2 * ny - 1 - gy) - y0 + 2;
-                            flip_y = true;
-                        }
-                    }
-                }
-                T U[NF], W[NF];
-                if (use) {
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) U[f] = src[f * fstride + sy * pitch + sx];
-                    if (flip_x) U[1] = -U[1];
-                    if (flip_y) U[2] = -U[2];
+            for (int q = 0; q < MAXE; ++q) {
+                const int e = tid + q * NT;
+                if (q == MAXE - 1 && e >= NPF) break;
+                T U[NF], W[NF];
+                const int off = cv[q] & 0xFFFF, fs = (cv[q] >> 16) & 0xFFF;
+                if (off != 0xFFFF) {
+                    const T* src = S + off;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) U[f] = src[f * fs];
+                    if (cv[q] & (1 << 28)) U[1] = -U[1];
+                    if (cv[q] & (1 << 29)) U[2] = -U[2];
                 } else {
                     U[0] = T(1); U[1] = U[2] = U[3] = T(0); U[4] = T(1);
                 }
                 cons_to_prim(U, gm1, W);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) Ps[(f * HYP + cy + 2) * HXP + cx + 2] = W[f];
+                for (int f = 0; f < NF; ++f) Ps[f * NPF + e] = W[f];
             }
             __syncthreads();
-            // each thread: the x face left of its cell and the y face below it
-            {
+            if constexpr (std::is_same<T, float>::value) {
+                // lane 0: the x face left of this cell; lane 1: the y face below
+                // it.  States are loaded already rotated (slot 1 = normal
+                // velocity, slot 2 = first tangent), so one HLLC serves both.
+                F2 q[4][NF], qL[NF], qR[NF], Fn[NF];
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    const float* px = Ps + (ty + 2) * HXP + tx + s4;
+                    const float* py = Ps + (ty + s4) * HXP + tx + 2;
+                    q[s4][0] = mk2(px[0], py[0]);
+                    q[s4][1] = mk2(px[NPF], py[2 * NPF]);
+                    q[s4][2] = mk2(px[2 * NPF], py[NPF]);
+                    q[s4][3] = mk2(px[3 * NPF], py[3 * NPF]);
+                    q[s4][4] = mk2(px[4 * NPF], py[4 * NPF]);
+                }
+                plm_faces<F2>(q[0], q[1], q[2], q[3], qL, qR);
+                hllc_core<F2>(qL, qR, mk2(gamma, gamma), mk2(igm1, igm1), Fn);
+                float* fx = Fx + ty * (TX + 1) + tx;
+                float* fy = Fy + ty * TX + tx;
+                fx[0] = lo(Fn[0]);
+                fx[TY * (TX + 1)] = lo(Fn[1]);
+                fx[2 * TY * (TX + 1)] = lo(Fn[2]);
+                fx[3 * TY * (TX + 1)] = lo(Fn[3]);
+                fx[4 * TY * (TX + 1)] = lo(Fn[4]);
+                fy[0] = hi(Fn[0]);
+                fy[(TY + 1) * TX] = hi(Fn[2]);
+                fy[2 * (TY + 1) * TX] = hi(Fn[1]);
+                fy[3 * (TY + 1) * TX] = hi(Fn[3]);
+                fy[4 * (TY + 1) * TX] = hi(Fn[4]);
+                if (tid < TX) {
+                    // lane 0: the y face above the top row at column tid;
+                    // lane 1: the x face right of the last column at row tid
+                    const int col = tid, row = tid < TY ? tid : TY - 1;
+#pragma unroll
+                    for (int s4 = 0; s4 < 4; ++s4) {
+                        const float* py = Ps + (TY + s4) * HXP + col + 2;
+                        const float* px = Ps + (row + 2) * HXP + TX + s4;
+                        q[s4][0] = mk2(py[0], px[0]);
+                        q[s4][1] = mk2(py[2 * NPF], px[NPF]);
+                        q[s4][2] = mk2(py[NPF], px[2 * NPF]);
+                        q[s4][3] = mk2(py[3 * NPF], px[3 * NPF]);
+                        q[s4][4] = mk2(py[4 * NPF], px[4 * NPF]);
+                    }
+                    plm_faces<F2>(q[0], q[1], q[2], q[3], qL, qR);
+                    hllc_core<F2>(qL, qR, mk2(gamma, gamma), mk2(igm1, igm1), Fn);
+                    float* gy = Fy + TY * TX + col;
+                    gy[0] = lo(Fn[0]);
+                    gy[(TY + 1) * TX] = lo(Fn[2]);
+                    gy[2 * (TY + 1) * TX] = lo(Fn[1]);
+                    gy[3 * (TY + 1) * TX] = lo(Fn[3]);
+                    gy[4 * (TY + 1) * TX] = lo(Fn[4]);
+                    if (tid < TY) {
+                        float* gx = Fx + row * (TX + 1) + TX;
+                        gx[0] = hi(Fn[0]);
+                        gx[TY * (TX + 1)] = hi(Fn[1]);
+                        gx[2 * TY * (TX + 1)] = hi(Fn[2]);
+                        gx[3 * TY * (TX + 1)] = hi(Fn[3]);
+                        gx[4 * TY * (TX + 1)] = hi(Fn[4]);
+                    }
+                }
+            } else {
+                // each thread: the x face left of its cell and the y face below it
                 T q[4][NF], F[NF];
 #pragma unroll
-                for (int s = 0; s < 4; ++s)
+                for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HYP + ty + 2) * HXP + tx + s];
-                face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+                    for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + 2) * HXP + tx + s4];
+                face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) Fx[(f * TY + ty) * (TX + 1) + tx] = F[f];
 #pragma unroll
-                for (int s = 0; s < 4; ++s)
+                for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HYP + ty + s) * HXP + tx + 2];
-                face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+                    for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + s4) * HXP + tx + 2];
+                face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + ty) * TX + tx] = F[f];
-            }
-            // the TX faces above the top row and the TY faces right of the last column
-            if (tid < TX + TY) {
-                T q[4][NF], F[NF];
-                if (tid < TX) {
-                    const int col = tid;
+                // the TX faces above the top row and the TY faces right of the last column
+                if (tid < TX + TY) {
+                    if (tid < TX) {
+                        const int col = tid;
 #pragma unroll
-                    for (int s = 0; s < 4; ++s)
+                        for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                        for (int f = 0; f < NF; ++f)
-                            q[s][f] = Ps[(f * HYP + TY + s) * HXP + col + 2];
-                    face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+                            for (int f = 0; f < NF; ++f)
+                                q[s4][f] = Ps[(f * HYP + TY + s4) * HXP + col + 2];
+                        face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + TY) * TX + col] = F[f];
-                } else {
-                    const int row = tid - TX;
+                        for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + TY) * TX + col] = F[f];
+                    } else {
+                        const int row = tid - TX;
 #pragma unroll
-                    for (int s = 0; s < 4; ++s)
+                        for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                        for (int f = 0; f < NF; ++f)
-                            q[s][f] = Ps[(f * HYP + row + 2) * HXP + TX + s];
-                    face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, F);
+                            for (int f = 0; f < NF; ++f)
+                                q[s4][f] = Ps[(f * HYP + row + 2) * HXP + TX + s4];
+                        face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + TX] = F[f];
+                        for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + TX] = F[f];
+                    }
                 }
             }
             __syncthreads();
@@ -292,7 +375,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                 qR[f] = madd(T(-0.5), d, qm1[f]);
                 qL[f] = madd(T(0.5), d, qm1[f]);
             }
-            if (it >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, Fz);      // face j-3/2
+            if (it >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, igm1, Fz);      // face j-3/2
 #pragma unroll
             for (int f = 0; f < NF; ++f) qLp[f] = qL[f];
         }
@@ -305,7 +388,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                 const T Lf = sub_over_dx(Da[f], Fz[f] - Fzp[f], A.dxk[2]);
                 const T uc = Sk[(f * HYC + ty + 2) * HXC + tx + 4];
                 Uo[f] = A.stage == 1 ? madd(dt, Lf, uc)
-                                     : madd(T(0.5), u0[f], T(0.5) * madd(dt, Lf, uc));
+                                     : madd(T(0.5), u0c[f], T(0.5) * madd(dt, Lf, uc));
                 A.Uo[f * A.N + c] = Uo[f];
             }
             if (A.rate_slot) {
@@ -326,6 +409,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             qm1[f] = qj[f];
             Da[f] = Db[f];
             Db[f] = Dj[f];
+            u0c[f] = u0n[f];
         }
     }
     if (s_abort) {

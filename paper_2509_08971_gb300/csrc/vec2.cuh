@@ -1,0 +1,157 @@
+// Lane-generic FP32 arithmetic of the face flux: one template instantiated
+// for a scalar float and for a packed pair of floats (F2), so that a thread
+// can evaluate two faces at once with sm_100-family paired FP32 instructions
+// (add/sub/mul/fma.rn.f32x2) and still round every face exactly as the scalar
+// path does.  Paired instructions halve the issue slots of the additions,
+// multiplications and FMAs; reciprocals, square roots, min/max and selects
+// stay per lane.
+//
+// Formulas: minmod-limited PLM face states and the one-sided HLLC flux with
+// Davis wave-speed bounds (see hydro_math.cuh for the statement).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hh {
+
+// Two FP32 values in one 64-bit register pair: .lo is lane 0, .hi lane 1.
+struct F2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ F2 mk2(float a, float b) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lo(F2 a) {
+    float x;
+    asm("{\n\t.reg .f32 u;\n\tmov.b64 {%0, u}, %1;\n\t}" : "=f"(x) : "l"(a.v));
+    return x;
+}
+__device__ __forceinline__ float hi(F2 a) {
+    float y;
+    asm("{\n\t.reg .f32 u;\n\tmov.b64 {u, %0}, %1;\n\t}" : "=f"(y) : "l"(a.v));
+    return y;
+}
+
+// ---- arithmetic, scalar ----
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float vrcp(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float vsqrt(float a) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+// minmod: min(|a|,|b|) carrying the XOR of the signs is >= 0 exactly when the
+// slopes agree; clamp at 0 and give it a's sign (three ALU operations)
+__device__ __forceinline__ float vminmod(float a, float b) {
+    float r;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return copysignf(fmaxf(r, 0.0f), a);
+}
+__device__ __forceinline__ bool vge0(float a) { return a >= 0.0f; }
+__device__ __forceinline__ float vsel(bool c, float a, float b) { return c ? a : b; }
+
+// ---- arithmetic, packed pair ----
+struct B2 {
+    bool x, y;
+};
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ F2 vmin(F2 a, F2 b) { return mk2(fminf(lo(a), lo(b)), fminf(hi(a), hi(b))); }
+__device__ __forceinline__ F2 vmax(F2 a, F2 b) { return mk2(fmaxf(lo(a), lo(b)), fmaxf(hi(a), hi(b))); }
+__device__ __forceinline__ F2 vrcp(F2 a) { return mk2(vrcp(lo(a)), vrcp(hi(a))); }
+__device__ __forceinline__ F2 vsqrt(F2 a) { return mk2(vsqrt(lo(a)), vsqrt(hi(a))); }
+__device__ __forceinline__ F2 vminmod(F2 a, F2 b) {
+    return mk2(vminmod(lo(a), lo(b)), vminmod(hi(a), hi(b)));
+}
+__device__ __forceinline__ B2 vge0(F2 a) { return B2{lo(a) >= 0.0f, hi(a) >= 0.0f}; }
+__device__ __forceinline__ F2 vsel(B2 c, F2 a, F2 b) {
+    return mk2(c.x ? lo(a) : lo(b), c.y ? hi(a) : hi(b));
+}
+template <class V> __device__ __forceinline__ V splat(float a);
+template <> __device__ __forceinline__ float splat<float>(float a) { return a; }
+template <> __device__ __forceinline__ F2 splat<F2>(float a) { return mk2(a, a); }
+
+// ---- face states: q_L = q_i + dq_i/2, q_R = q_{i+1} - dq_{i+1}/2 ----
+template <class V>
+__device__ __forceinline__ void plm_faces(const V q0[5], const V q1[5], const V q2[5],
+                                          const V q3[5], V qL[5], V qR[5]) {
+    const V half = splat<V>(0.5f), mhalf = splat<V>(-0.5f);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        const V d0 = vsub(q1[f], q0[f]);
+        const V d1 = vsub(q2[f], q1[f]);
+        const V d2 = vsub(q3[f], q2[f]);
+        qL[f] = vfma(half, vminmod(d0, d1), q1[f]);
+        qR[f] = vfma(mhalf, vminmod(d1, d2), q2[f]);
+    }
+}
+
+// ---- one-sided HLLC on rotated states W = (rho, un, t1, t2, p) ----
+//   F = F_K + s (U*_K - U_K), K = L if S* >= 0 else R,
+//   s = min(S_L, 0) for K = L, max(S_R, 0) for K = R.
+template <class V>
+__device__ __forceinline__ void hllc_core(const V WL[5], const V WR[5], V gamma, V igm1,
+                                          V F[5]) {
+    const V zero = splat<V>(0.0f), half = splat<V>(0.5f);
+    const V rL = WL[0], uL = WL[1], pL = WL[4];
+    const V rR = WR[0], uR = WR[1], pR = WR[4];
+    const V irL = vrcp(rL), irR = vrcp(rR);
+    const V cL = vsqrt(vmul(vmul(gamma, pL), irL));
+    const V cR = vsqrt(vmul(vmul(gamma, pR), irR));
+    const V SL = vmin(vsub(uL, cL), vsub(uR, cR));
+    const V SR = vmax(vadd(uL, cL), vadd(uR, cR));
+    const V mL = vmul(rL, vsub(SL, uL));               // < 0
+    const V mR = vmul(rR, vsub(SR, uR));               // > 0
+    const V nmR = vmul(rR, vsub(uR, SR));              // exactly -mR
+    const V num = vfma(nmR, uR, vfma(mL, uL, vsub(pR, pL)));
+    const V Sstar = vmul(num, vrcp(vadd(mL, nmR)));
+    const auto left = vge0(Sstar);
+    const V r = vsel(left, rL, rR), u = vsel(left, uL, uR), p = vsel(left, pL, pR);
+    const V t1 = vsel(left, WL[2], WR[2]), t2 = vsel(left, WL[3], WR[3]);
+    const V m = vsel(left, mL, mR), ir = vsel(left, irL, irR);
+    const V SK = vsel(left, SL, SR);
+    const V s = vsel(left, vmin(SL, zero), vmax(SR, zero));
+    const V ke = vfma(u, u, vfma(t1, t1, vmul(t2, t2)));
+    const V E = vfma(p, igm1, vmul(vmul(half, r), ke));
+    const V fac = vmul(m, vrcp(vsub(SK, Sstar)));       // rho_K (S_K - u_K) / (S_K - S*)
+    const V mu = vmul(r, u);
+    const V es = vfma(E, ir, vmul(vsub(Sstar, u), vfma(p, vrcp(m), Sstar)));
+    const V dr = vsub(fac, r);
+    F[0] = vfma(s, dr, mu);
+    F[1] = vfma(s, vsub(vmul(fac, Sstar), mu), vfma(mu, u, p));
+    F[2] = vfma(s, vmul(dr, t1), vmul(mu, t1));
+    F[3] = vfma(s, vmul(dr, t2), vmul(mu, t2));
+    F[4] = vfma(s, vsub(vmul(fac, es), E), vmul(vadd(E, p), u));
+}
+
+}  // namespace hh
