@@ -10,19 +10,12 @@
 //     the wrapped columns / rows on the same mbarrier; outflow and reflecting
 //     ghosts are read from the tile's own interior;
 //   * the conserved value of a cell, needed by the RK combine two planes
-//     later, is read back from the ring instead of from HBM;
-//   * in FP32 each thread evaluates its x face and its y face together as the
-//     two lanes of paired f32x2 arithmetic (vec2.cuh), bit-identical per lane
-//     to the scalar path; the TX + TY faces on the tile's far edges take one
-//     more paired pass on the first TX threads.
+//     later, is read back from the ring instead of from HBM.
 // The x start of every box is x0 - 4 (x0 a multiple of TX): 16-byte aligned
 // for 4- and 8-byte elements.
 #pragma once
-#include <type_traits>
-
 #include "stage_kernel.cuh"
 #include "tma.cuh"
-#include "vec2.cuh"
 
 namespace hh {
 
@@ -237,106 +230,44 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                 for (int f = 0; f < NF; ++f) Ps[f * NPF + e] = W[f];
             }
             __syncthreads();
-            if constexpr (std::is_same<T, float>::value) {
-                // lane 0: the x face left of this cell; lane 1: the y face below
-                // it.  States are loaded already rotated (slot 1 = normal
-                // velocity, slot 2 = first tangent), so one HLLC serves both.
-                F2 q[4][NF], qL[NF], qR[NF], Fn[NF];
+            // each thread: the x face left of its cell and the y face below it
+            T q[4][NF], F[NF];
 #pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
-                    const float* px = Ps + (ty + 2) * HXP + tx + s4;
-                    const float* py = Ps + (ty + s4) * HXP + tx + 2;
-                    q[s4][0] = mk2(px[0], py[0]);
-                    q[s4][1] = mk2(px[NPF], py[2 * NPF]);
-                    q[s4][2] = mk2(px[2 * NPF], py[NPF]);
-                    q[s4][3] = mk2(px[3 * NPF], py[3 * NPF]);
-                    q[s4][4] = mk2(px[4 * NPF], py[4 * NPF]);
-                }
-                plm_faces<F2>(q[0], q[1], q[2], q[3], qL, qR);
-                hllc_core<F2>(qL, qR, mk2(gamma, gamma), mk2(igm1, igm1), Fn);
-                float* fx = Fx + ty * (TX + 1) + tx;
-                float* fy = Fy + ty * TX + tx;
-                fx[0] = lo(Fn[0]);
-                fx[TY * (TX + 1)] = lo(Fn[1]);
-                fx[2 * TY * (TX + 1)] = lo(Fn[2]);
-                fx[3 * TY * (TX + 1)] = lo(Fn[3]);
-                fx[4 * TY * (TX + 1)] = lo(Fn[4]);
-                fy[0] = hi(Fn[0]);
-                fy[(TY + 1) * TX] = hi(Fn[2]);
-                fy[2 * (TY + 1) * TX] = hi(Fn[1]);
-                fy[3 * (TY + 1) * TX] = hi(Fn[3]);
-                fy[4 * (TY + 1) * TX] = hi(Fn[4]);
+            for (int s4 = 0; s4 < 4; ++s4)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + 2) * HXP + tx + s4];
+            face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Fx[(f * TY + ty) * (TX + 1) + tx] = F[f];
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + s4) * HXP + tx + 2];
+            face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + ty) * TX + tx] = F[f];
+            // the TX faces above the top row and the TY faces right of the last column
+            if (tid < TX + TY) {
                 if (tid < TX) {
-                    // lane 0: the y face above the top row at column tid;
-                    // lane 1: the x face right of the last column at row tid
-                    const int col = tid, row = tid < TY ? tid : TY - 1;
+                    const int col = tid;
 #pragma unroll
-                    for (int s4 = 0; s4 < 4; ++s4) {
-                        const float* py = Ps + (TY + s4) * HXP + col + 2;
-                        const float* px = Ps + (row + 2) * HXP + TX + s4;
-                        q[s4][0] = mk2(py[0], px[0]);
-                        q[s4][1] = mk2(py[2 * NPF], px[NPF]);
-                        q[s4][2] = mk2(py[NPF], px[2 * NPF]);
-                        q[s4][3] = mk2(py[3 * NPF], px[3 * NPF]);
-                        q[s4][4] = mk2(py[4 * NPF], px[4 * NPF]);
-                    }
-                    plm_faces<F2>(q[0], q[1], q[2], q[3], qL, qR);
-                    hllc_core<F2>(qL, qR, mk2(gamma, gamma), mk2(igm1, igm1), Fn);
-                    float* gy = Fy + TY * TX + col;
-                    gy[0] = lo(Fn[0]);
-                    gy[(TY + 1) * TX] = lo(Fn[2]);
-                    gy[2 * (TY + 1) * TX] = lo(Fn[1]);
-                    gy[3 * (TY + 1) * TX] = lo(Fn[3]);
-                    gy[4 * (TY + 1) * TX] = lo(Fn[4]);
-                    if (tid < TY) {
-                        float* gx = Fx + row * (TX + 1) + TX;
-                        gx[0] = hi(Fn[0]);
-                        gx[TY * (TX + 1)] = hi(Fn[1]);
-                        gx[2 * TY * (TX + 1)] = hi(Fn[2]);
-                        gx[3 * TY * (TX + 1)] = hi(Fn[3]);
-                        gx[4 * TY * (TX + 1)] = hi(Fn[4]);
-                    }
-                }
-            } else {
-                // each thread: the x face left of its cell and the y face below it
-                T q[4][NF], F[NF];
+                    for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4)
+                        for (int f = 0; f < NF; ++f)
+                            q[s4][f] = Ps[(f * HYP + TY + s4) * HXP + col + 2];
+                    face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + 2) * HXP + tx + s4];
-                face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
+                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + TY) * TX + col] = F[f];
+                } else {
+                    const int row = tid - TX;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) Fx[(f * TY + ty) * (TX + 1) + tx] = F[f];
+                    for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4)
+                        for (int f = 0; f < NF; ++f)
+                            q[s4][f] = Ps[(f * HYP + row + 2) * HXP + TX + s4];
+                    face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + s4) * HXP + tx + 2];
-                face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
-#pragma unroll
-                for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + ty) * TX + tx] = F[f];
-                // the TX faces above the top row and the TY faces right of the last column
-                if (tid < TX + TY) {
-                    if (tid < TX) {
-                        const int col = tid;
-#pragma unroll
-                        for (int s4 = 0; s4 < 4; ++s4)
-#pragma unroll
-                            for (int f = 0; f < NF; ++f)
-                                q[s4][f] = Ps[(f * HYP + TY + s4) * HXP + col + 2];
-                        face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
-#pragma unroll
-                        for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + TY) * TX + col] = F[f];
-                    } else {
-                        const int row = tid - TX;
-#pragma unroll
-                        for (int s4 = 0; s4 < 4; ++s4)
-#pragma unroll
-                            for (int f = 0; f < NF; ++f)
-                                q[s4][f] = Ps[(f * HYP + row + 2) * HXP + TX + s4];
-                        face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
-#pragma unroll
-                        for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + TX] = F[f];
-                    }
+                    for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + TX] = F[f];
                 }
             }
             __syncthreads();

@@ -1,10 +1,10 @@
-// Lane-generic FP32 arithmetic of the face flux: one template instantiated
-// for a scalar float and for a packed pair of floats (F2), so that a thread
-// can evaluate two faces at once with sm_100-family paired FP32 instructions
-// (add/sub/mul/fma.rn.f32x2) and still round every face exactly as the scalar
-// path does.  Paired instructions halve the issue slots of the additions,
-// multiplications and FMAs; reciprocals, square roots, min/max and selects
-// stay per lane.
+// FP32 arithmetic of the face flux, written once over a value type V with
+// small operation helpers (vadd, vfma, vminmod, ...).  Every operation is a
+// single IEEE operation with the rounding written in the source (explicit
+// fmaf, single-instruction approximate reciprocal and square root), so each
+// kernel that evaluates a face rounds it identically.  (Paired f32x2
+// arithmetic was measured: it does not round lane-for-lane like the scalar
+// instructions and did not speed the stage kernel up, so it is not used.)
 //
 // Formulas: minmod-limited PLM face states and the one-sided HLLC flux with
 // Davis wave-speed bounds (see hydro_math.cuh for the statement).
@@ -13,27 +13,6 @@
 #include <stdint.h>
 
 namespace hh {
-
-// Two FP32 values in one 64-bit register pair: .lo is lane 0, .hi lane 1.
-struct F2 {
-    unsigned long long v;
-};
-
-__device__ __forceinline__ F2 mk2(float a, float b) {
-    F2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float lo(F2 a) {
-    float x;
-    asm("{\n\t.reg .f32 u;\n\tmov.b64 {%0, u}, %1;\n\t}" : "=f"(x) : "l"(a.v));
-    return x;
-}
-__device__ __forceinline__ float hi(F2 a) {
-    float y;
-    asm("{\n\t.reg .f32 u;\n\tmov.b64 {u, %0}, %1;\n\t}" : "=f"(y) : "l"(a.v));
-    return y;
-}
 
 // ---- arithmetic, scalar ----
 __device__ __forceinline__ float vadd(float a, float b) { return a + b; }
@@ -62,44 +41,8 @@ __device__ __forceinline__ float vminmod(float a, float b) {
 __device__ __forceinline__ bool vge0(float a) { return a >= 0.0f; }
 __device__ __forceinline__ float vsel(bool c, float a, float b) { return c ? a : b; }
 
-// ---- arithmetic, packed pair ----
-struct B2 {
-    bool x, y;
-};
-__device__ __forceinline__ F2 vadd(F2 a, F2 b) {
-    F2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
-    F2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ F2 vmul(F2 a, F2 b) {
-    F2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {
-    F2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return r;
-}
-__device__ __forceinline__ F2 vmin(F2 a, F2 b) { return mk2(fminf(lo(a), lo(b)), fminf(hi(a), hi(b))); }
-__device__ __forceinline__ F2 vmax(F2 a, F2 b) { return mk2(fmaxf(lo(a), lo(b)), fmaxf(hi(a), hi(b))); }
-__device__ __forceinline__ F2 vrcp(F2 a) { return mk2(vrcp(lo(a)), vrcp(hi(a))); }
-__device__ __forceinline__ F2 vsqrt(F2 a) { return mk2(vsqrt(lo(a)), vsqrt(hi(a))); }
-__device__ __forceinline__ F2 vminmod(F2 a, F2 b) {
-    return mk2(vminmod(lo(a), lo(b)), vminmod(hi(a), hi(b)));
-}
-__device__ __forceinline__ B2 vge0(F2 a) { return B2{lo(a) >= 0.0f, hi(a) >= 0.0f}; }
-__device__ __forceinline__ F2 vsel(B2 c, F2 a, F2 b) {
-    return mk2(c.x ? lo(a) : lo(b), c.y ? hi(a) : hi(b));
-}
 template <class V> __device__ __forceinline__ V splat(float a);
 template <> __device__ __forceinline__ float splat<float>(float a) { return a; }
-template <> __device__ __forceinline__ F2 splat<F2>(float a) { return mk2(a, a); }
 
 // ---- face states: q_L = q_i + dq_i/2, q_R = q_{i+1} - dq_{i+1}/2 ----
 template <class V>
