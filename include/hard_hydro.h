@@ -130,6 +130,38 @@ int hard_hydro_advance_host(hard_hydro_t h, const void* U_host_in, void* U_host_
  * warp level up in a fixed order (deterministic).  Synchronises the stream. */
 int hard_hydro_totals(hard_hydro_t h, const void* U, double out5[5], void* stream);
 
+/* ---- batched persistent launch (many independent 1D/2D problems) ----
+ * A batch is a set of independent problems of uneven size, each a uniform
+ * mesh of nx x ny cells (nz must be 1; ny = 1 makes it 1D along x; nx >= 2)
+ * on the unit square, with its own gamma and one boundary kind on all faces.
+ * The packed state holds problem p's U[5][ny][nx] (same field order as
+ * above) at element offset hard_batch_offset(b, p); hard_batch_elements is
+ * the packed length.  One hard_hydro_step_batched call advances every problem
+ * by nsteps Heun steps, each with its own CFL step dt_p = cfl / r_p(U_p), in a
+ * single persistent launch: blocks take problems largest-first from an atomic
+ * queue head (no block ever waits on another) and run all steps of a problem
+ * with block-local reductions.  A problem advanced in a batch equals the same
+ * problem advanced alone by hard_hydro_advance (t_end = 0), bit for bit.
+ * The call allocates nothing and issues one memset and one kernel on
+ * `stream`, so it can be captured in a CUDA graph.  t_dev: device array of
+ * nprob doubles, read as each problem's start time and advanced in place.
+ * hard_batch_create returns NULL on a bad argument or allocation failure; it
+ * owns the problem table, the queue order and the packed intermediate stage.
+ * Non-physical states raise the batch's status word (hard_batch_get_error). */
+typedef struct hard_batch_s* hard_batch_t;
+hard_batch_t hard_batch_create(int nprob, const int* nx, const int* ny, const int* nz,
+                               const double* gamma, const int* bc, int dtype);
+long long hard_batch_offset(hard_batch_t b, int p);
+long long hard_batch_elements(hard_batch_t b);
+int hard_batch_tile_count(void);
+/* tile id: {1D tile width, 2D tile} = 0: {256, 32x8}, 1: {128, 32x4}, 2: {512, 64x8} */
+int hard_batch_set_tile(hard_batch_t b, int tile);
+int hard_hydro_step_batched(hard_batch_t b, void* U_packed, int nsteps, double cfl, double* t_dev,
+                            void* stream);
+/* HARD_OK or HARD_ENONPHYS (and clears it); synchronises the last stream. */
+int hard_batch_get_error(hard_batch_t b);
+void hard_batch_destroy(hard_batch_t b);
+
 /* hard_hydro_step with no device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they
  * step (code running during CUDA-graph stream capture, hosts whose device

@@ -56,6 +56,15 @@ def _declare(lib):
         "hard_hydro_totals": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
         "hard_hydro_step_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
         "hard_hydro_get_error": (ctypes.c_int, [_vp]),
+        "hard_batch_create": (_vp, [ctypes.c_int, _ip, _ip, _ip, _dp, _ip, ctypes.c_int]),
+        "hard_batch_offset": (ctypes.c_longlong, [_vp, ctypes.c_int]),
+        "hard_batch_elements": (ctypes.c_longlong, [_vp]),
+        "hard_batch_tile_count": (ctypes.c_int, []),
+        "hard_batch_set_tile": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "hard_hydro_step_batched": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double, _vp,
+                                                   _vp]),
+        "hard_batch_get_error": (ctypes.c_int, [_vp]),
+        "hard_batch_destroy": (None, [_vp]),
         "hard_hydro_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "hard_hydro_destroy": (None, [_vp]),
     }
@@ -143,6 +152,42 @@ def hard_hydro_step_noalloc(h, U_in, U_out, dt, stream):
     """hard_hydro_step without any device allocation: the intermediate stage
     lives in the library's fixed 64 MiB device array (see the C header)."""
     return lib().hard_hydro_step_noalloc(h, U_in, U_out, float(dt), stream)
+
+
+def hard_batch_create(nprob, nx, ny, nz, gamma, bc, dtype):
+    ia = lambda v: (ctypes.c_int * nprob)(*[int(x) for x in v])
+    da = (ctypes.c_double * nprob)(*[float(x) for x in gamma])
+    return lib().hard_batch_create(int(nprob), ia(nx), ia(ny), ia(nz) if nz is not None else None,
+                                   da, ia(bc), int(dtype))
+
+
+def hard_batch_offset(b, p):
+    return lib().hard_batch_offset(b, int(p))
+
+
+def hard_batch_elements(b):
+    return lib().hard_batch_elements(b)
+
+
+def hard_batch_tile_count():
+    return lib().hard_batch_tile_count()
+
+
+def hard_batch_set_tile(b, tile):
+    return lib().hard_batch_set_tile(b, int(tile))
+
+
+def hard_hydro_step_batched(b, U_packed, nsteps, cfl, t_dev, stream):
+    return lib().hard_hydro_step_batched(b, U_packed, int(nsteps), float(cfl), t_dev, stream)
+
+
+def hard_batch_get_error(b):
+    return lib().hard_batch_get_error(b)
+
+
+def hard_batch_destroy(b):
+    if b:
+        lib().hard_batch_destroy(b)
 
 
 def hard_hydro_get_error(h):
@@ -264,3 +309,78 @@ class HardHydro:
 
     def get_error(self):
         return hard_hydro_get_error(self.h)
+
+
+class HardBatch:
+    """Independent 1D/2D problems advanced together by one persistent launch.
+    Problem p is nx[p] x ny[p] cells (ny = 1: 1D) with its own gamma and
+    boundary kind; states live in one packed device tensor."""
+
+    def __init__(self, nx, ny, gamma, bc=HARD_BC_OUTFLOW, dtype=None, tile=0):
+        import torch
+        self.torch = torch
+        self.nprob = len(nx)
+        self.nx = [int(v) for v in nx]
+        self.ny = [int(v) for v in ny]
+        self.dtype = dtype or torch.float32
+        gam = [float(gamma)] * self.nprob if isinstance(gamma, (int, float)) else list(gamma)
+        bcs = [int(bc)] * self.nprob if isinstance(bc, int) else list(bc)
+        self.b = hard_batch_create(self.nprob, self.nx, self.ny, [1] * self.nprob, gam, bcs,
+                                   HARD_F64 if self.dtype == torch.float64 else HARD_F32)
+        if not self.b:
+            raise HardHydroError(HARD_EINVAL, "hard_batch_create")
+        self.offsets = [hard_batch_offset(self.b, p) for p in range(self.nprob)]
+        self.elements = hard_batch_elements(self.b)
+        check(hard_batch_set_tile(self.b, tile), "hard_batch_set_tile")
+
+    def __del__(self):
+        b, self.b = getattr(self, "b", None), None
+        if b and _lib is not None:
+            hard_batch_destroy(b)
+
+    def set_tile(self, tile):
+        check(hard_batch_set_tile(self.b, tile), "hard_batch_set_tile")
+
+    def empty(self):
+        return self.torch.zeros(self.elements, dtype=self.dtype, device="cuda")
+
+    def view(self, packed, p):
+        """Problem p's state as a (5, 1, ny, nx) view of the packed tensor."""
+        n = 5 * self.nx[p] * self.ny[p]
+        o = self.offsets[p]
+        return packed[o:o + n].view(5, 1, self.ny[p], self.nx[p])
+
+    def pack(self, states):
+        packed = self.empty()
+        for p, U in enumerate(states):
+            self.view(packed, p).copy_(self.torch.as_tensor(U, dtype=self.dtype))
+        return packed
+
+    def step(self, packed, nsteps, cfl, t=None):
+        """Advance every problem by nsteps steps in place; returns t (device, FP64)."""
+        torch = self.torch
+        if t is None:
+            t = torch.zeros(self.nprob, dtype=torch.float64, device=packed.device)
+        if not (packed.is_cuda and packed.is_contiguous() and packed.dtype == self.dtype
+                and packed.numel() == self.elements):
+            raise ValueError("packed state must be a contiguous CUDA tensor of hard_batch_elements")
+        check(hard_hydro_step_batched(self.b, packed.data_ptr(), nsteps, cfl, t.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream),
+              "hard_hydro_step_batched")
+        return t
+
+    def capture(self, packed, nsteps, cfl, t):
+        """A CUDA graph of one batched call on these buffers (replay() re-runs it)."""
+        torch = self.torch
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                check(hard_hydro_step_batched(self.b, packed.data_ptr(), nsteps, cfl, t.data_ptr(),
+                                              s.cuda_stream), "hard_hydro_step_batched")
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    def get_error(self):
+        return hard_batch_get_error(self.b)

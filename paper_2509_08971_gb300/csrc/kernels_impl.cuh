@@ -2,6 +2,7 @@
 // their launchers.  Included by exactly one translation unit per type with
 // HH_T defined (float or double) and HH_SUFFIX (f32 or f64).
 #pragma once
+#include "batched.cuh"
 #include "launch.h"
 #include "stage_kernel.cuh"
 #include "stage_tma.cuh"
@@ -261,6 +262,40 @@ cudaError_t dispatch_tile(const MeshDesc& m, int kernel, int tile, const StageCa
     }
 }
 
+template <int TX1, int TX2, int TY2>
+cudaError_t run_batched(const BatchCall& c, cudaStream_t s) {
+    constexpr size_t s1 = StageSmem<T, TX1, 1, 1>::bytes, s2 = StageSmem<T, TX2, TY2, 2>::bytes;
+    constexpr size_t smem = s1 > s2 ? s1 : s2;
+    auto kern = batched_kernel<T, TX1, TX2, TY2>;
+    static int grid = 0;
+    if (grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX1, smem);
+        if (e != cudaSuccess) return e;
+        grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    BatchArgs<T> B;
+    B.U = static_cast<T*>(c.U);
+    B.W = static_cast<T*>(c.W);
+    B.probs = c.probs;
+    B.order = c.order;
+    B.nprob = c.nprob;
+    B.nsteps = c.nsteps;
+    B.cfl = c.cfl;
+    B.t = c.t;
+    B.counter = c.counter;
+    B.status = c.status;
+    const int blocks = grid < c.nprob ? grid : c.nprob;
+    kern<<<blocks, TX1, smem, s>>>(B);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 #define HH_CAT2(a, b) a##b
@@ -307,4 +342,14 @@ cudaError_t HH_CAT(launch_totals_, HH_SUFFIX)(const MeshDesc& m, const void* U, 
     return cudaGetLastError();
 }
 
+}  // namespace hh
+
+namespace hh {
+cudaError_t HH_CAT(launch_batched_, HH_SUFFIX)(const BatchCall& c, int tile, cudaStream_t s) {
+    switch (tile) {
+        case 1: return run_batched<128, 32, 4>(c, s);
+        case 2: return run_batched<512, 64, 8>(c, s);
+        default: return run_batched<256, 32, 8>(c, s);
+    }
+}
 }  // namespace hh

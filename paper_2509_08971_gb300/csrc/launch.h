@@ -76,6 +76,35 @@ inline long long totals_blocks() { return TOTALS_BLOCKS; }
 cudaError_t launch_totals_f32(const MeshDesc& m, const void* U, double* partial, cudaStream_t s);
 cudaError_t launch_totals_f64(const MeshDesc& m, const void* U, double* partial, cudaStream_t s);
 
+// One problem of a batch (see batched.cuh).
+struct BatchProblem {
+    long long off;        // element offset of the problem's U[5][ny][nx] in the packed buffer
+    int nx, ny;           // cells (nz = 1); ny == 1 makes a 1D problem
+    int bc;               // boundary kind on all faces
+    int pad;
+    double gamma;
+};
+
+struct BatchCall {
+    void* U;
+    void* W;
+    const BatchProblem* probs;
+    const int* order;
+    int nprob;
+    int nsteps;
+    double cfl;
+    double* t;
+    int* counter;
+    int* status;
+};
+
+// Batched tile configurations: {1D tile width, 2D tile x, 2D tile y}.
+inline constexpr int BATCH_TILES[][3] = {{256, 32, 8}, {128, 32, 4}, {512, 64, 8}};
+inline constexpr int BATCH_TILE_COUNT = 3;
+
+cudaError_t launch_batched_f32(const BatchCall& c, int tile, cudaStream_t s);
+cudaError_t launch_batched_f64(const BatchCall& c, int tile, cudaStream_t s);
+
 // Read-only view of a handle (hard_hydro.cu); false for a NULL handle.
 }  // namespace hh
 struct hard_hydro_s;

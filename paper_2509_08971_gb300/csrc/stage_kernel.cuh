@@ -75,7 +75,10 @@ struct StageSmem {
 
 // Load the conserved values of kernel cell (gx, gy, gz) with the boundary map
 // applied along the active kernel axes, as primitives.
-template <typename T, int DIM, int PX, int PY>
+// NC: the state is not written during this launch, so the read-only
+// (non-coherent) cache path may serve it.  A kernel that rewrites its input
+// within the launch (the batched time loop) must read with NC = false.
+template <typename T, int DIM, int PX, int PY, bool NC>
 __device__ __forceinline__ void load_prim(const StageArgs<T>& A, int gx, int gy, int gz, T W[NF],
                                           bool& bad) {
     bool fx, fy = false, fz = false;
@@ -86,7 +89,7 @@ __device__ __forceinline__ void load_prim(const StageArgs<T>& A, int gx, int gy,
     long long c = ((long long)sz * A.n[1] + sy) * A.n[0] + sx;
     T U[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) U[f] = __ldg(A.Uc + f * A.N + c);
+    for (int f = 0; f < NF; ++f) U[f] = NC ? __ldg(A.Uc + f * A.N + c) : A.Uc[f * A.N + c];
     if (fx) U[1 + PX] = -U[1 + PX];
     if (DIM >= 2 && fy) U[1 + PY] = -U[1 + PY];
     if (DIM >= 3 && fz) U[3] = -U[3];
@@ -94,32 +97,36 @@ __device__ __forceinline__ void load_prim(const StageArgs<T>& A, int gx, int gy,
     bad |= nonphys(W);
 }
 
-template <typename T, int TX, int TY, int DIM, int PX, int PY, bool TMA>
-__global__ void __launch_bounds__(TX * TY)
-stage_kernel(const StageArgs<T> A) {
+// What a block accumulates over the cells it completes: the largest signal
+// rate, the conserved totals and the non-physical flag.
+template <typename T>
+struct TileAcc {
+    T rate_max;
+    T tot[NF];
+    bool bad;
+};
+
+// One tile of one stage: the TX x TY column at (x0, y0), z-planes [z0, z1)
+// (DIM == 3; a single plane otherwise).  Writes the completed cells of the
+// tile to A.Uo and folds them into `acc`.  All threads of the block call it.
+template <typename T, int TX, int TY, int DIM, int PX, int PY, bool NC>
+__device__ __forceinline__ void stage_tile(const StageArgs<T>& A, unsigned char* smem_raw, int x0,
+                                           int y0, int z0, int z1, TileAcc<T>& acc) {
     using S = StageSmem<T, TX, TY, DIM>;
     constexpr int NT = TX * TY;
     constexpr int HX = S::HX, HY = S::HY;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     T* Ps = reinterpret_cast<T*>(smem_raw);          // [NF][HY][HX]
     T* Fx = Ps + S::NP;                               // [NF][TY][TX+1]
     T* Fy = Fx + S::NFX;                              // [NF][TY+1][TX]
-    __shared__ double red_tot[NT / 32][NF];
-    __shared__ unsigned long long red_rate[NT / 32];
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX;
-    const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < A.n[0] && (DIM < 2 || y < A.n[1]);
-    const int z0 = DIM == 3 ? blockIdx.z * A.zchunk : 0;
-    const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.n[2]) : 1;
     const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
     const T gamma = A.gamma, gm1 = A.gm1, igm1 = A.igm1;
     bool bad = false;
-    T rate_max = T(0);
-    T tot[NF] = {T(0), T(0), T(0), T(0), T(0)};
+    T rate_max = acc.rate_max;
 
     // z stencil state of this thread's column
     T qm1[NF], dprev[NF], qLp[NF], Fzp[NF], Da[NF], Db[NF];
@@ -139,7 +146,7 @@ stage_kernel(const StageArgs<T> A) {
             for (int e = tid; e < HX * HY; e += NT) {
                 int hx = e % HX, hy = e / HX;
                 T W[NF];
-                load_prim<T, DIM, PX, PY>(A, x0 - 2 + hx, y0 - 2 + hy, j, W, bad);
+                load_prim<T, DIM, PX, PY, NC>(A, x0 - 2 + hx, y0 - 2 + hy, j, W, bad);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) Ps[(f * HY + hy) * HX + hx] = W[f];
             }
@@ -186,7 +193,7 @@ stage_kernel(const StageArgs<T> A) {
             }
         } else {
             // warm-up / look-ahead plane: only this column's primitives
-            load_prim<T, DIM, PX, PY>(A, min(x, A.n[0] - 1), min(y, A.n[1] - 1), j, qj, bad);
+            load_prim<T, DIM, PX, PY, NC>(A, min(x, A.n[0] - 1), min(y, A.n[1] - 1), j, qj, bad);
 #pragma unroll
             for (int f = 0; f < NF; ++f) Dj[f] = T(0);
         }
@@ -253,10 +260,38 @@ stage_kernel(const StageArgs<T> A) {
             }
             if (A.tot_partial) {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) tot[f] += Uo[f];
+                for (int f = 0; f < NF; ++f) acc.tot[f] += Uo[f];
             }
         }
     }
+
+    acc.rate_max = rate_max;
+    acc.bad |= bad;
+}
+
+template <typename T, int TX, int TY, int DIM, int PX, int PY, bool TMA>
+__global__ void __launch_bounds__(TX * TY)
+stage_kernel(const StageArgs<T> A) {
+    constexpr int NT = TX * TY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red_tot[NT / 32][NF];
+    __shared__ unsigned long long red_rate[NT / 32];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX;
+    const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
+    const int z0 = DIM == 3 ? blockIdx.z * A.zchunk : 0;
+    const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.n[2]) : 1;
+    TileAcc<T> acc;
+    acc.rate_max = T(0);
+    acc.bad = false;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc.tot[f] = T(0);
+    stage_tile<T, TX, TY, DIM, PX, PY, true>(A, smem_raw, x0, y0, z0, z1, acc);
+    const T rate_max = acc.rate_max;
+    const bool bad = acc.bad;
+    T tot[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) tot[f] = acc.tot[f];
 
     // ---- epilogue: block reductions ----
     const int lane = tid & 31, warp = tid >> 5;
