@@ -316,6 +316,37 @@ def main():
                "status": hh.hard_hydro_strerror(B.get_error())}
     del P, packed0, B, graph
 
+    # ---------------- adjoint cost: 2D shear layer 256^2, FP32 ----------------
+    na = 256
+    ma = hh.HardHydro((1, na, na), 1.4, hh.HARD_BC_PERIODIC, dtype=torch.float32)
+    Ua = torch.tensor(H.shear_2d(na, seed=rank, gamma=1.4), dtype=torch.float32, device=dev)
+    dta = ma.cfl_dt(Ua, CFL)
+    Ga = torch.randn_like(Ua)
+    gga = torch.zeros((), dtype=torch.float64, device=dev)
+    Va, Ha = torch.empty_like(Ua), torch.empty_like(Ua)
+    for _ in range(5):
+        ma.step(Ua, dta, out=Va)
+        ma.step_backward(Ua, Ga, dta, gga, out=Ha)
+    reps_a = 200
+
+    def timed(fn):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for _ in range(reps_a):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps_a
+
+    fwd_ms = timed(lambda: ma.step(Ua, dta, out=Va))
+    bwd_ms = timed(lambda: ma.step_backward(Ua, Ga, dta, gga, out=Ha))
+    adjoint = {"workload": "2D periodic shear layer 256^2, gamma 1.4, FP32",
+               "forward_step_ms": fwd_ms, "backward_step_ms": bwd_ms,
+               "ratio": bwd_ms / fwd_ms,
+               "backward_includes": "stage-1 recompute + stage-2 and stage-1 VJP"}
+    del ma, Ua, Ga, Va, Ha
+
     # ---------------- end to end through the C ABI, host buffers ----------------
     Uh = torch.tensor(U64, dtype=torch.float32).pin_memory()
     Uo = torch.empty_like(Uh).pin_memory()
@@ -342,6 +373,7 @@ def main():
                    "step": "CFL rate + stage 1 + stage 2 + FP64 totals"},
         "roofline": roofline,
         "batched": batched,
+        "adjoint": adjoint,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": k64,
                        "ms_per_step": ms64 / k64, "fp32_fused_speedup": value / value64},
         "e2e": e2e,

@@ -182,6 +182,18 @@ void hard_batch_destroy(hard_batch_t b);
 int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U_out, double dt,
                             void* stream);
 
+/* Adjoint of one full step with dt held constant (a vector-Jacobian product):
+ * given the cotangent gU_out of U^{n+1} = step(U_in), writes
+ * gU_in = (dU^{n+1}/dU_in)^T gU_out and adds (dU^{n+1}/dgamma)^T gU_out to the
+ * device double *g_gamma.  The intermediate stage is recomputed from U_in.
+ * Each face runs its flux backwards in the region the forward pass took;
+ * minmod and the Davis min/max pass the cotangent to the argument they
+ * selected (subgradients).  gU_in may alias gU_out.  Summation into the
+ * cotangents uses device atomics, so results agree to rounding, not bitwise,
+ * from run to run.  Device pointers, 16-byte aligned; asynchronous. */
+int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_out, void* gU_in,
+                             double dt, double* g_gamma, void* stream);
+
 /* Device status flag: returns HARD_OK or HARD_ENONPHYS and clears the flag.
  * Synchronises the handle's last stream. */
 int hard_hydro_get_error(hard_hydro_t h);

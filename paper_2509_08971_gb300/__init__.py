@@ -55,6 +55,8 @@ def _declare(lib):
                                                    ctypes.c_double, _dp, _vp]),
         "hard_hydro_totals": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
         "hard_hydro_step_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
+        "hard_hydro_step_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp,
+                                                    _vp]),
         "hard_hydro_get_error": (ctypes.c_int, [_vp]),
         "hard_batch_create": (_vp, [ctypes.c_int, _ip, _ip, _ip, _dp, _ip, ctypes.c_int]),
         "hard_batch_offset": (ctypes.c_longlong, [_vp, ctypes.c_int]),
@@ -190,6 +192,10 @@ def hard_batch_destroy(b):
         lib().hard_batch_destroy(b)
 
 
+def hard_hydro_step_backward(h, U_in, gU_out, gU_in, dt, g_gamma, stream):
+    return lib().hard_hydro_step_backward(h, U_in, gU_out, gU_in, float(dt), g_gamma, stream)
+
+
 def hard_hydro_get_error(h):
     return lib().hard_hydro_get_error(h)
 
@@ -305,6 +311,14 @@ class HardHydro:
     def totals(self, U):
         rc, out = hard_hydro_totals(self.h, self._check(U), self._stream())
         check(rc, "hard_hydro_totals")
+        return out
+
+    def step_backward(self, U, gU_out, dt, g_gamma, out=None):
+        """VJP of one step at U with fixed dt; adds d/dgamma to g_gamma (device FP64 scalar)."""
+        out = self.empty() if out is None else out
+        check(hard_hydro_step_backward(self.h, self._check(U), self._check(gU_out),
+                                       self._check(out), dt, g_gamma.data_ptr(), self._stream()),
+              "hard_hydro_step_backward")
         return out
 
     def get_error(self):

@@ -1,0 +1,332 @@
+// Adjoint (vector-Jacobian product) of one Runge-Kutta stage.
+//
+// A stage is  U_out = a U0 + b (U_c + dt L(U_c))  with L the flux difference
+// of Sec. 2.2.2 (stage 1: a = 0, b = 1; stage 2: a = b = 1/2).  Given the
+// cotangent G of U_out, the stage's VJP is
+//     dU_c  = b G + J_L(U_c)^T lambda,     lambda = b dt G
+//     dU0   = a G
+//     dgamma = (dL/dgamma)^T lambda
+// J_L^T lambda is assembled face by face.  L_i = -sum_d (F_{i+1/2} - F_{i-1/2})/dx_d,
+// so the cotangent of the face flux F_{m-1/2} between cells m-1 and m is
+//     Fbar = (lambda_m - lambda_{m-1}) / dx          (lambda of a ghost cell = 0).
+// Each face then runs its flux backwards: HLLC (the region the forward pass
+// took; Davis min/max and minmod pass the cotangent to the argument they
+// selected), the piecewise-linear face states, and lands on the primitive
+// states of its four stencil cells, mapped back through the boundary map (a
+// reflecting wall negates the normal velocity).  A per-cell pass then applies
+// the transpose of the conserved-to-primitive map and the RK combine.
+//
+// gamma enters through p = (gamma-1)(E - rho|v|^2/2) of every cell, the
+// sound speeds c = sqrt(gamma p / rho) and the face energies
+// E = p/(gamma-1) + rho|v|^2/2.
+#pragma once
+#include "hydro_math.cuh"
+#include "stage_kernel.cuh"
+
+namespace hh {
+
+template <typename T>
+struct AdjArgs {
+    const T* Uc;          // state the flux difference is taken of
+    const T* gout;        // cotangent of the stage output
+    T lam;                // lambda = lam * gout  (b * dt)
+    T* gW;                // primitive cotangent accumulator [5][N]
+    double* g_gamma;      // accumulated d/dgamma
+    long long N;
+    int n[3];             // kernel-axis extents
+    int bc_lo[3], bc_hi[3];
+    T gamma, gm1;
+    T dxk[3];             // per kernel axis: dx (FP64) or 1/dx (FP32)
+};
+
+// Which argument minmod selected: 0 none, 1 a, 2 b (the forward rule).
+template <typename T>
+__device__ __forceinline__ int minmod_sel(T a, T b) {
+    if (a > T(0) && b > T(0)) return (a <= b) ? 1 : 2;
+    if (a < T(0) && b < T(0)) return (-a <= -b) ? 1 : 2;
+    return 0;
+}
+
+// Reverse of the physical normal flux F(W) = (r u, r u^2 + p, r u v, r u w, (E+p) u),
+// E = p/(gamma-1) + r|v|^2/2, accumulated into Wb and gb.
+template <typename T>
+__device__ __forceinline__ void flux_vjp(const T W[NF], T gamma, const T Fb[NF], T Wb[NF],
+                                         T& Eb) {
+    const T r = W[0], u = W[1], v = W[2], w = W[3], p = W[4];
+    const T g1 = gamma - T(1);
+    const T E = p / g1 + T(0.5) * r * (u * u + v * v + w * w);
+    Wb[0] += Fb[0] * u + Fb[1] * u * u + Fb[2] * u * v + Fb[3] * u * w;
+    Wb[1] += Fb[0] * r + Fb[1] * T(2) * r * u + Fb[2] * r * v + Fb[3] * r * w + Fb[4] * (E + p);
+    Wb[2] += Fb[2] * r * u;
+    Wb[3] += Fb[3] * r * u;
+    Wb[4] += Fb[1] + Fb[4] * u;
+    Eb += Fb[4] * u;
+}
+
+// Reverse of E = p/(gamma-1) + r|v|^2/2.
+template <typename T>
+__device__ __forceinline__ void energy_vjp(const T W[NF], T gamma, T Eb, T Wb[NF], T& gb) {
+    const T r = W[0], u = W[1], v = W[2], w = W[3], p = W[4];
+    const T g1 = gamma - T(1);
+    Wb[0] += Eb * T(0.5) * (u * u + v * v + w * w);
+    Wb[1] += Eb * r * u;
+    Wb[2] += Eb * r * v;
+    Wb[3] += Eb * r * w;
+    Wb[4] += Eb / g1;
+    gb -= Eb * p / (g1 * g1);
+}
+
+// Reverse of c = sqrt(gamma p / r).
+template <typename T>
+__device__ __forceinline__ void sound_vjp(const T W[NF], T gamma, T c, T cb, T Wb[NF], T& gb) {
+    const T r = W[0], p = W[4];
+    const T zb = cb / (T(2) * c);            // z = gamma p / r
+    gb += zb * p / r;
+    Wb[4] += zb * gamma / r;
+    Wb[0] -= zb * gamma * p / (r * r);
+}
+
+// HLLC on rotated states (normal along slot 1): recompute the forward pass,
+// then push Fb back onto WLb, WRb (overwritten) and gb (added).
+template <typename T>
+__device__ void hllc_vjp(const T WL[NF], const T WR[NF], T gamma, const T Fb[NF], T WLb[NF],
+                         T WRb[NF], T& gb) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) WLb[f] = WRb[f] = T(0);
+    const T g1 = gamma - T(1);
+    const T rL = WL[0], uL = WL[1], pL = WL[4];
+    const T rR = WR[0], uR = WR[1], pR = WR[4];
+    const T cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+    const T aL = uL - cL, aR = uR - cR, bL = uL + cL, bR = uR + cR;
+    const bool minL = aL <= aR, maxL = bL >= bR;     // which side set S_L / S_R
+    const T SL = minL ? aL : aR;
+    const T SR = maxL ? bL : bR;
+    T ELb = T(0), ERb = T(0);
+    if (T(0) <= SL) {                                // supersonic to the right: F = F_L
+        flux_vjp(WL, gamma, Fb, WLb, ELb);
+        energy_vjp(WL, gamma, ELb, WLb, gb);
+        return;
+    }
+    if (SR <= T(0)) {                                // supersonic to the left: F = F_R
+        flux_vjp(WR, gamma, Fb, WRb, ERb);
+        energy_vjp(WR, gamma, ERb, WRb, gb);
+        return;
+    }
+    const T mL = rL * (SL - uL), mR = rR * (SR - uR);
+    const T num = pR - pL + mL * uL - mR * uR;
+    const T den = mL - mR;
+    const T Ss = num / den;
+    const bool left = Ss >= T(0);
+    const T* WK = left ? WL : WR;
+    T* WKb = left ? WLb : WRb;
+    const T rK = WK[0], uK = WK[1], vK = WK[2], wK = WK[3], pK = WK[4];
+    const T EK = pK / g1 + T(0.5) * rK * (uK * uK + vK * vK + wK * wK);
+    const T SK = left ? SL : SR;
+    const T mK = left ? mL : mR;
+    const T D = SK - Ss;
+    const T fac = mK / D;
+    const T A = Ss - uK;
+    const T q = pK / mK;
+    const T Bq = Ss + q;
+    const T es = EK / rK + A * Bq;
+    const T Us[NF] = {fac, fac * Ss, fac * vK, fac * wK, fac * es};
+    const T UK[NF] = {rK, rK * uK, rK * vK, rK * wK, EK};
+    // F = F_K + S_K (U* - U_K)
+    T EKb = T(0), SKb = T(0), Ssb = T(0), mKb = T(0);
+    flux_vjp(WK, gamma, Fb, WKb, EKb);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) SKb += Fb[f] * (Us[f] - UK[f]);
+    // U_K = (r, r u, r v, r w, E)
+    WKb[0] += -SK * (Fb[0] + Fb[1] * uK + Fb[2] * vK + Fb[3] * wK);
+    WKb[1] += -SK * Fb[1] * rK;
+    WKb[2] += -SK * Fb[2] * rK;
+    WKb[3] += -SK * Fb[3] * rK;
+    EKb += -SK * Fb[4];
+    // U* = fac (1, S*, v, w, es)
+    const T facb = SK * (Fb[0] + Fb[1] * Ss + Fb[2] * vK + Fb[3] * wK + Fb[4] * es);
+    Ssb += SK * Fb[1] * fac;
+    WKb[2] += SK * Fb[2] * fac;
+    WKb[3] += SK * Fb[3] * fac;
+    const T esb = SK * Fb[4] * fac;
+    // es = E/r + A Bq
+    EKb += esb / rK;
+    WKb[0] -= esb * EK / (rK * rK);
+    const T Ab = esb * Bq, Bqb = esb * A;
+    Ssb += Bqb;                                      // Bq = S* + q
+    WKb[4] += Bqb / mK;                              // q = p / m
+    mKb -= Bqb * pK / (mK * mK);
+    Ssb += Ab;                                       // A = S* - u
+    WKb[1] -= Ab;
+    mKb += facb / D;                                 // fac = m / D
+    const T Db = -facb * mK / (D * D);
+    SKb += Db;                                       // D = S_K - S*
+    Ssb -= Db;
+    energy_vjp(WK, gamma, EKb, WKb, gb);
+    // S* = num / den
+    const T numb = Ssb / den;
+    const T denb = -Ssb * Ss / den;
+    T mLb = denb + numb * uL + (left ? mKb : T(0));
+    T mRb = -denb - numb * uR + (left ? T(0) : mKb);
+    WRb[4] += numb;
+    WLb[4] -= numb;
+    WLb[1] += numb * mL;
+    WRb[1] -= numb * mR;
+    T SLb = left ? SKb : T(0), SRb = left ? T(0) : SKb;
+    // m_L = r_L (S_L - u_L), m_R = r_R (S_R - u_R)
+    WLb[0] += mLb * (SL - uL);
+    SLb += mLb * rL;
+    WLb[1] -= mLb * rL;
+    WRb[0] += mRb * (SR - uR);
+    SRb += mRb * rR;
+    WRb[1] -= mRb * rR;
+    // Davis bounds
+    T cLb = T(0), cRb = T(0);
+    if (minL) { WLb[1] += SLb; cLb -= SLb; } else { WRb[1] += SLb; cRb -= SLb; }
+    if (maxL) { WLb[1] += SRb; cLb += SRb; } else { WRb[1] += SRb; cRb += SRb; }
+    sound_vjp(WL, gamma, cL, cLb, WLb, gb);
+    sound_vjp(WR, gamma, cR, cRb, WRb, gb);
+}
+
+// One thread per face along kernel axis KA (physical axis PA): the reverse
+// of that face's contribution to L, scattered onto its four stencil cells.
+template <typename T, int KA, int PA>
+__global__ void __launch_bounds__(256) face_vjp_kernel(const AdjArgs<T> A) {
+    using R = Rot<PA>;
+    const int na = A.n[KA];
+    const long long others = A.N / na;
+    const long long nfaces = (long long)(na + 1) * others;
+    double gacc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nfaces;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(e % (na + 1));                 // face between cells m-1 and m
+        const long long rest = e / (na + 1);
+        int c3[3];
+        if (KA == 0) { c3[1] = (int)(rest % A.n[1]); c3[2] = (int)(rest / A.n[1]); }
+        if (KA == 1) { c3[0] = (int)(rest % A.n[0]); c3[2] = (int)(rest / A.n[0]); }
+        if (KA == 2) { c3[0] = (int)(rest % A.n[0]); c3[1] = (int)(rest / A.n[0]); }
+        long long src[4];
+        bool flip[4];
+        T q[4][NF];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int c[3] = {c3[0], c3[1], c3[2]};
+            c[KA] = bc_map(m - 2 + s, na, A.bc_lo[KA], A.bc_hi[KA], flip[s]);
+            src[s] = ((long long)c[2] * A.n[1] + c[1]) * A.n[0] + c[0];
+            T U[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) U[f] = A.Uc[f * A.N + src[s]];
+            if (flip[s]) U[R::n] = -U[R::n];
+            cons_to_prim(U, A.gm1, q[s]);
+        }
+        // face flux cotangent from the two neighbouring cells' lambda
+        T Fb[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T lr = m < na ? A.lam * A.gout[f * A.N + src[2]] : T(0);
+            const T ll = m > 0 ? A.lam * A.gout[f * A.N + src[1]] : T(0);
+            Fb[f] = sub_over_dx(T(0), ll - lr, A.dxk[KA]);   // (lambda_m - lambda_{m-1}) / dx
+        }
+        // forward face states, remembering the minmod selections
+        T qL[NF], qR[NF];
+        int s1[NF], s2[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T d0 = q[1][f] - q[0][f], d1 = q[2][f] - q[1][f], d2 = q[3][f] - q[2][f];
+            s1[f] = minmod_sel(d0, d1);
+            s2[f] = minmod_sel(d1, d2);
+            const T m1 = s1[f] == 1 ? d0 : (s1[f] == 2 ? d1 : T(0));
+            const T m2 = s2[f] == 1 ? d1 : (s2[f] == 2 ? d2 : T(0));
+            qL[f] = madd(T(0.5), m1, q[1][f]);
+            qR[f] = madd(T(-0.5), m2, q[2][f]);
+        }
+        const T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
+        const T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
+        const T Fn_b[NF] = {Fb[0], Fb[R::n], Fb[R::t1], Fb[R::t2], Fb[4]};
+        T WLb[NF], WRb[NF], gb = T(0);
+        hllc_vjp(WL, WR, A.gamma, Fn_b, WLb, WRb, gb);
+        gacc += (double)gb;
+        T qLb[NF], qRb[NF];
+        qLb[0] = WLb[0]; qLb[R::n] = WLb[1]; qLb[R::t1] = WLb[2]; qLb[R::t2] = WLb[3]; qLb[4] = WLb[4];
+        qRb[0] = WRb[0]; qRb[R::n] = WRb[1]; qRb[R::t1] = WRb[2]; qRb[R::t2] = WRb[3]; qRb[4] = WRb[4];
+        // face states backwards onto the four stencil primitives
+        T qb[4][NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            qb[0][f] = T(0); qb[1][f] = qLb[f]; qb[2][f] = qRb[f]; qb[3][f] = T(0);
+            const T s1b = T(0.5) * qLb[f], s2b = T(-0.5) * qRb[f];
+            if (s1[f] == 1) { qb[1][f] += s1b; qb[0][f] -= s1b; }
+            if (s1[f] == 2) { qb[2][f] += s1b; qb[1][f] -= s1b; }
+            if (s2[f] == 1) { qb[2][f] += s2b; qb[1][f] -= s2b; }
+            if (s2[f] == 2) { qb[3][f] += s2b; qb[2][f] -= s2b; }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (flip[s]) qb[s][R::n] = -qb[s][R::n];
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                if (qb[s][f] != T(0)) atomicAdd(A.gW + f * A.N + src[s], qb[s][f]);
+        }
+    }
+    // block sum of the explicit d/dgamma, one atomic per block
+    __shared__ double red[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(0xffffffffu, gacc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        if (s != 0.0) atomicAdd(A.g_gamma, s);
+    }
+}
+
+// Per cell: the transpose of the conserved-to-primitive map applied to the
+// accumulated primitive cotangent, plus the RK combine:
+//     out_c  (=|+=)  b G + J_prim^T gW,      out0 = a G  (when out0 != null)
+// and d/dgamma of p = (gamma-1)(E - kin): gW_p * p / (gamma - 1).
+template <typename T>
+__global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, const T* gW, const T* G,
+                                                       T b, T a, T* out_c, bool accumulate,
+                                                       T* out0, long long N, T gamma,
+                                                       double* g_gamma) {
+    double gacc = 0.0;
+    const T g1 = gamma - T(1);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        T U[NF], W[NF], Wb[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            U[f] = Uc[f * N + c];
+            Wb[f] = gW[f * N + c];
+        }
+        cons_to_prim(U, g1, W);
+        const T r = W[0], u = W[1], v = W[2], w = W[3];
+        T Ub[NF];
+        Ub[1] = Wb[1] / r - Wb[4] * g1 * u;
+        Ub[2] = Wb[2] / r - Wb[4] * g1 * v;
+        Ub[3] = Wb[3] / r - Wb[4] * g1 * w;
+        Ub[4] = Wb[4] * g1;
+        Ub[0] = Wb[0] - (Wb[1] * u + Wb[2] * v + Wb[3] * w) / r +
+                Wb[4] * g1 * T(0.5) * (u * u + v * v + w * w);
+        gacc += (double)(Wb[4] * W[4] / g1);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T gf = G[f * N + c];
+            const T val = b * gf + Ub[f];
+            out_c[f * N + c] = accumulate ? out_c[f * N + c] + val : val;
+            if (out0) out0[f * N + c] = a * gf;
+        }
+    }
+    __shared__ double red[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(0xffffffffu, gacc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        if (s != 0.0) atomicAdd(g_gamma, s);
+    }
+}
+
+}  // namespace hh

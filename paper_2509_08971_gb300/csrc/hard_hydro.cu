@@ -29,6 +29,8 @@ struct hard_hydro_s {
     unsigned char* slots = nullptr;  // rate | dt | t | status | totals[5]
     double* tot_partial = nullptr;
     long long tot_rows = 0;
+    void* adj = nullptr;             // adjoint scratch: primitive cotangent | stage-1 cotangent
+    size_t adj_bytes = 0;
     cudaStream_t last = nullptr;
 };
 
@@ -95,6 +97,9 @@ void build_mesh(hard_hydro_s* h) {
 }
 
 void free_scratch(hard_hydro_s* h) {
+    if (h->adj) cudaFree(h->adj);
+    h->adj = nullptr;
+    h->adj_bytes = 0;
     if (h->U1) cudaFree(h->U1);
     if (h->Udev) cudaFree(h->Udev);
     if (h->tot_partial) cudaFree(h->tot_partial);
@@ -450,6 +455,42 @@ int hard_hydro_totals(hard_hydro_t h, const void* U, double out5[5], void* strea
         e = cudaMemcpyAsync(out5, tot_slot(h), 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return from_cuda(e);
     return read_status(h, s);
+}
+
+int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_out, void* gU_in,
+                             double dt, double* g_gamma, void* stream) {
+    if (!h || !U_in || !gU_out || !gU_in || !g_gamma) return HARD_EINVAL;
+    if (!aligned16(U_in) || !aligned16(gU_out) || !aligned16(gU_in)) return HARD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    int rc = ensure_U1(h);
+    if (rc) return rc;
+    const size_t need = 2 * state_bytes(h);
+    if (!h->adj || h->adj_bytes < need) {
+        if (h->adj) cudaFree(h->adj);
+        h->adj = nullptr;
+        h->adj_bytes = 0;
+        rc = dev_alloc(&h->adj, need);
+        if (rc) return rc;
+        h->adj_bytes = need;
+    }
+    void* gW = h->adj;
+    void* gU1 = static_cast<unsigned char*>(h->adj) + state_bytes(h);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    // recompute the intermediate stage U1 = Un + dt L(Un)
+    const StageCall c1{1, U_in, U_in, h->U1, dt, nullptr, nullptr, nullptr, status_slot(h)};
+    cudaError_t e = stage_launch(h, c1, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    // stage 2: U^{n+1} = Un/2 + (U1 + dt L(U1))/2
+    const hh::AdjointCall a2{h->U1, gU_out, gW, gU1, false, gU_in, 0.5, 0.5, 0.5 * dt, g_gamma};
+    e = h->dtype == HARD_F64 ? hh::launch_adjoint_stage_f64(h->mesh, a2, s)
+                             : hh::launch_adjoint_stage_f32(h->mesh, a2, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    // stage 1: U1 = Un + dt L(Un)
+    const hh::AdjointCall a1{U_in, gU1, gW, gU_in, true, nullptr, 1.0, 0.0, dt, g_gamma};
+    e = h->dtype == HARD_F64 ? hh::launch_adjoint_stage_f64(h->mesh, a1, s)
+                             : hh::launch_adjoint_stage_f32(h->mesh, a1, s);
+    return from_cuda(e);
 }
 
 int hard_hydro_get_error(hard_hydro_t h) {

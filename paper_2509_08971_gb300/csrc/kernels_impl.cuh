@@ -2,6 +2,7 @@
 // their launchers.  Included by exactly one translation unit per type with
 // HH_T defined (float or double) and HH_SUFFIX (f32 or f64).
 #pragma once
+#include "adjoint.cuh"
 #include "batched.cuh"
 #include "launch.h"
 #include "stage_kernel.cuh"
@@ -296,6 +297,34 @@ cudaError_t run_batched(const BatchCall& c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+AdjArgs<T> make_adj(const MeshDesc& m, const AdjointCall& c) {
+    AdjArgs<T> A;
+    A.Uc = static_cast<const T*>(c.Uc);
+    A.gout = static_cast<const T*>(c.G);
+    A.lam = (T)c.lam;
+    A.gW = static_cast<T*>(c.gW);
+    A.g_gamma = c.g_gamma;
+    A.N = m.N;
+    for (int k = 0; k < 3; ++k) {
+        A.n[k] = m.n[k];
+        A.bc_lo[k] = m.bc_lo[k];
+        A.bc_hi[k] = m.bc_hi[k];
+        A.dxk[k] = width_param(m.dxk[k]);
+    }
+    A.gamma = (T)m.gamma;
+    A.gm1 = (T)(m.gamma - 1.0);
+    return A;
+}
+
+template <int KA, int PA>
+cudaError_t run_face_vjp(const AdjArgs<T>& A, cudaStream_t s) {
+    const long long faces = (long long)(A.n[KA] + 1) * (A.N / A.n[KA]);
+    long long blocks = (faces + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    face_vjp_kernel<T, KA, PA><<<(int)blocks, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 #define HH_CAT2(a, b) a##b
@@ -351,5 +380,34 @@ cudaError_t HH_CAT(launch_batched_, HH_SUFFIX)(const BatchCall& c, int tile, cud
         case 2: return run_batched<512, 64, 8>(c, s);
         default: return run_batched<256, 32, 8>(c, s);
     }
+}
+}  // namespace hh
+
+namespace hh {
+cudaError_t HH_CAT(launch_adjoint_stage_, HH_SUFFIX)(const MeshDesc& m, const AdjointCall& c,
+                                                     cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(c.gW, 0, sizeof(T) * 5 * (size_t)m.N, s);
+    if (e != cudaSuccess) return e;
+    const AdjArgs<T> A = make_adj(m, c);
+    if (m.dim >= 1) {
+        e = m.px == 0 ? run_face_vjp<0, 0>(A, s)
+                      : (m.px == 1 ? run_face_vjp<0, 1>(A, s) : run_face_vjp<0, 2>(A, s));
+        if (e != cudaSuccess) return e;
+    }
+    if (m.dim >= 2) {
+        e = m.py == 1 ? run_face_vjp<1, 1>(A, s) : run_face_vjp<1, 2>(A, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (m.dim >= 3) {
+        e = run_face_vjp<2, 2>(A, s);
+        if (e != cudaSuccess) return e;
+    }
+    long long blocks = (m.N + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    cell_vjp_kernel<T><<<(int)blocks, 256, 0, s>>>(
+        static_cast<const T*>(c.Uc), static_cast<const T*>(c.gW), static_cast<const T*>(c.G),
+        (T)c.b, (T)c.a, static_cast<T*>(c.out_c), c.accumulate, static_cast<T*>(c.out0), m.N,
+        (T)m.gamma, c.g_gamma);
+    return cudaGetLastError();
 }
 }  // namespace hh
