@@ -41,6 +41,38 @@ BYTES_PER_CELL_STAGE = {4: 50.0, 8: 100.0}     # algorithmic: (5+5 + 10+5)/2 val
 L2_BYTES = 129 * 2 ** 20
 
 
+def kernel_sources_digest():
+    """sha256 over the CUDA sources, to tell whether a profile still applies."""
+    import hashlib
+    root = os.path.join(ROOT, "paper_2509_08971_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(root)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(root, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per stage launch (read + write, mean of the two stages) from
+    the committed ncu summary, or None when the kernels changed since."""
+    path = os.path.join(ROOT, "profiles", "stage_tma_kernel_smooth3d_256.md")
+    try:
+        rec = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line and line.split(":", 1)[0] in ("sources-sha256",
+                                                             "traffic-bytes-per-launch"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+        if rec.get("sources-sha256") != kernel_sources_digest():
+            return None
+        return float(rec["traffic-bytes-per-launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -113,6 +145,23 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x, world, device=None):
+    """The largest of each rank's value (the job's time is its slowest rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, cells_per_rank, stages, ms):
+    """Cell-updates per second of the whole job: every rank advances its own
+    replica, so the job's work is world x the per-rank work over the max time."""
+    return world * cells_per_rank * stages / (ms * 1e-3)
 
 
 def cpu_threads():
@@ -190,12 +239,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, world, dev)
 
     n = args.n
     shape = (n, n, n)
@@ -227,8 +272,8 @@ def main():
         advance(m32, U, args.steps, tot_log)
         ev1.record(stream)
         barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1))
-    value = world * cells * 2 * args.steps / (ms * 1e-3)
+    ms = rank_max(ev0.elapsed_time(ev1))
+    value = whole_job_value(world, cells, 2 * args.steps, ms)
     status = m32.get_error()
     clocks = clk.summary()
     # kernels of this library launched in the timed region:
@@ -256,7 +301,7 @@ def main():
     alg_bytes = BYTES_PER_CELL_STAGE[4] * cells
     achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved / hbm, "traffic": profiled_traffic(), "peak_kind": peak_kind,
                 "kernel": "stage_tma_kernel<float,%d,%d> z-chunk %d (mean of stage 1 and stage 2)"
                           % tuple(tuned["info"][:3]),
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": stage_ms}
@@ -275,8 +320,8 @@ def main():
     advance(m64, V, k64, tl64)
     f1.record(stream)
     barrier()
-    ms64 = max_over_ranks(f0.elapsed_time(f1))
-    value64 = world * cells * 2 * k64 / (ms64 * 1e-3)
+    ms64 = rank_max(f0.elapsed_time(f1))
+    value64 = whole_job_value(world, cells, 2 * k64, ms64)
     del V, m64
 
     # ---------------- batched: 4096 independent 1D/2D problems ----------------
@@ -308,10 +353,10 @@ def main():
     graph.replay()
     b1.record(stream)
     barrier()
-    bms = max_over_ranks(b0.elapsed_time(b1))
+    bms = rank_max(b0.elapsed_time(b1))
     batched = {"workload": "4096 problems: half 1D n~U{64..4096}, half 2D side~U{32..256}, "
                            "two-state / four-quadrant, gamma 1.4, outflow, CFL 0.4, 50 steps",
-               "value": world * bcells * 2 * 50 / (bms * 1e-3), "unit": UNIT, "cells": bcells,
+               "value": whole_job_value(world, bcells, 2 * 50, bms), "unit": UNIT, "cells": bcells,
                "ms": bms, "tile": btile, "tile_ms_5_steps": btimes, "graph_captured": True,
                "status": hh.hard_hydro_strerror(B.get_error())}
     del P, packed0, B, graph
@@ -355,8 +400,8 @@ def main():
     t0 = time.perf_counter()
     m32.advance_host(Uh, args.steps, CFL, out=Uo)
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * cells * 2 * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = rank_max(time.perf_counter() - t0)
+    e2e = {"value": whole_job_value(world, cells, 2 * args.steps, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": Uh.numel() * 4 / args.steps,
            "d2h_bytes_per_step": Uo.numel() * 4 / args.steps,
            "call": f"hard_hydro_advance_host: one call of {args.steps} steps, pinned host "
