@@ -208,6 +208,100 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+FIELDS = ("rho", "rho_u", "rho_v", "rho_w", "E")
+
+
+def _field_errors(a, b):
+    """Relative L1 per field, sum|a-b| / sum|b| (fields that are zero in the
+    reference report the absolute L1 per cell instead)."""
+    a = np.asarray(a, dtype=np.float64).reshape(5, -1)
+    b = np.asarray(b, dtype=np.float64).reshape(5, -1)
+    out = {}
+    for f, name in enumerate(FIELDS):
+        den = np.sum(np.abs(b[f]))
+        num = np.sum(np.abs(a[f] - b[f]))
+        out[name] = float(num / den) if den > 0 else float(num / b.shape[1])
+    return out
+
+
+def precision_report():
+    """FP32 against FP64 per field and per configuration (one JSON line)."""
+    import torch
+    import hydro_inputs as H
+    import oracle
+    import paper_2509_08971_gb300 as hh
+    rep = {"report": "precision", "metric": "relative L1 per field, FP32 GPU vs FP64 reference"}
+    # configuration 1: seeded Riemann problems (400 cells, outflow, CFL 0.4, t = 0.15)
+    worst = {k: 0.0 for k in FIELDS}
+    for seed in range(8):
+        pb = H.riemann_1d(seed)
+        U = pb.U(400)
+        ref, t_ref, _ = oracle.Grid((1, 1, 400), pb.gamma, oracle.BC_OUTFLOW).run(U, 10 ** 6, 0.4, 0.15)
+        m = hh.HardHydro((1, 1, 400), pb.gamma, hh.HARD_BC_OUTFLOW)
+        Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
+        m.advance(Ud, 10 ** 4, 0.4, t_end=0.15, t=torch.zeros((), dtype=torch.float64, device="cuda"))
+        for k, v in _field_errors(Ud.cpu().numpy(), ref).items():
+            worst[k] = max(worst[k], v)
+    rep["riemann_1d_400_fp32_vs_oracle"] = worst
+    # configuration 2: smooth 3D flow, 100 steps
+    n = 64
+    U = H.smooth_3d(n, seed=0, gamma=GAMMA)
+    ref, _, _ = oracle.Grid((n, n, n), GAMMA, oracle.BC_PERIODIC).run(U, 100, CFL)
+    m = hh.HardHydro((n, n, n), GAMMA, 0)
+    Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
+    m.advance(Ud, 100, CFL)
+    rep["smooth_3d_64_fp32_vs_oracle"] = _field_errors(Ud.cpu().numpy(), ref)
+    n = 256
+    U = H.smooth_3d(n, seed=0, gamma=GAMMA)
+    m64 = hh.HardHydro((n, n, n), GAMMA, 0, dtype=torch.float64)
+    V = torch.tensor(U, dtype=torch.float64, device="cuda")
+    m64.advance(V, 100, CFL)
+    m32 = hh.HardHydro((n, n, n), GAMMA, 0)
+    Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
+    m32.advance(Ud, 100, CFL)
+    rep["smooth_3d_256_fp32_vs_fp64_gpu"] = _field_errors(Ud.cpu().numpy(), V.cpu().numpy())
+    del V, Ud, m64, m32
+    # configuration 3: spherical blast 512^3, reflecting walls, CFL 0.3
+    n = 512
+    Ub = H.blast_3d(n, seed=0, dtype=np.float32)
+    m32 = hh.HardHydro((n, n, n), 1.4, hh.HARD_BC_REFLECT)
+    Ud = torch.tensor(Ub, device="cuda")
+    t = torch.zeros((), dtype=torch.float64, device="cuda")
+    tl = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    _, _, tl = m32.advance(Ud, 200, 0.3, t=t, log_totals=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tot = tl.cpu().numpy()
+    rep["blast_512_fp32_200_steps"] = {
+        "cell_updates_per_s_per_stage": n ** 3 * 2 * 200 / (ms * 1e-3), "ms": ms,
+        "t_final": float(t), "status": hh.hard_hydro_strerror(m32.get_error()),
+        "mass_drift_rel": float(abs(tot[-1, 0] - tot[0, 0]) / tot[0, 0]),
+        "energy_drift_rel": float(abs(tot[-1, 4] - tot[0, 4]) / tot[0, 4])}
+    del Ud
+    # 20 steps in FP32 and FP64 from the same input
+    Ud = torch.tensor(Ub, device="cuda")
+    m32.advance(Ud, 20, 0.3)
+    V = torch.tensor(Ub, dtype=torch.float64, device="cuda")
+    m64 = hh.HardHydro((n, n, n), 1.4, hh.HARD_BC_REFLECT, dtype=torch.float64)
+    m64.advance(V, 20, 0.3)
+    rep["blast_512_fp32_vs_fp64_gpu_20_steps"] = _field_errors(Ud.cpu().numpy(), V.cpu().numpy())
+    del Ud, V, m64, m32
+    # configuration 5: shear layer 256^2, 200 steps
+    n = 256
+    U = H.shear_2d(n, seed=0, gamma=1.4)
+    ref, _, dts = oracle.Grid((1, n, n), 1.4, oracle.BC_PERIODIC).run(U, 200, CFL)
+    m = hh.HardHydro((1, n, n), 1.4, 0)
+    Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
+    for dt in dts:
+        Ud = m.step(Ud, dt)
+    rep["shear_2d_256_fp32_vs_oracle"] = _field_errors(Ud.cpu().numpy(), ref)
+    print(json.dumps(rep), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,8 +311,13 @@ def main():
     ap.add_argument("--f64-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_SIDE, help="mesh side (profiling runs only)")
+    ap.add_argument("--report", choices=["precision"], default=None,
+                    help="print a per-field FP32-vs-FP64 error report instead of the bench line")
     args = ap.parse_args()
     world, rank, local = dist_setup()
+    if args.report == "precision":
+        precision_report()
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return

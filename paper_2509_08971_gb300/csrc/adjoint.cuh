@@ -25,12 +25,28 @@
 
 namespace hh {
 
+// The primitive cotangent accumulator holds one 8-slot record per cell (5
+// used), so that FP32 contributions land with one 16-byte vector reduction
+// plus one scalar reduction.
+constexpr int GW_STRIDE = 8;
+
+__device__ __forceinline__ void accumulate_cell(float* rec, const float v[NF]) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(rec), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3])
+                 : "memory");
+    atomicAdd(rec + 4, v[4]);
+}
+__device__ __forceinline__ void accumulate_cell(double* rec, const double v[NF]) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) atomicAdd(rec + f, v[f]);
+}
+
 template <typename T>
 struct AdjArgs {
     const T* Uc;          // state the flux difference is taken of
     const T* gout;        // cotangent of the stage output
     T lam;                // lambda = lam * gout  (b * dt)
-    T* gW;                // primitive cotangent accumulator [5][N]
+    T* gW;                // primitive cotangent accumulator, one record of GW_STRIDE per cell
     double* g_gamma;      // accumulated d/dgamma
     long long N;
     int n[3];             // kernel-axis extents
@@ -187,85 +203,95 @@ __device__ void hllc_vjp(const T WL[NF], const T WR[NF], T gamma, const T Fb[NF]
     sound_vjp(WR, gamma, cR, cRb, WRb, gb);
 }
 
-// One thread per face along kernel axis KA (physical axis PA): the reverse
-// of that face's contribution to L, scattered onto its four stencil cells.
+// The reverse of one face's contribution to L: the face between cells m-1
+// and m along kernel axis KA (physical axis PA), at transverse coordinates
+// c3 (c3[KA] = m), scattered onto its four stencil cells.
 template <typename T, int KA, int PA>
-__global__ void __launch_bounds__(256) face_vjp_kernel(const AdjArgs<T> A) {
+__device__ __forceinline__ void face_vjp_one(const AdjArgs<T>& A, const int c3[3], double& gacc) {
     using R = Rot<PA>;
     const int na = A.n[KA];
-    const long long others = A.N / na;
-    const long long nfaces = (long long)(na + 1) * others;
+    const int m = c3[KA];
+    long long src[4];
+    bool flip[4];
+    T q[4][NF];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        int c[3] = {c3[0], c3[1], c3[2]};
+        c[KA] = bc_map(m - 2 + s, na, A.bc_lo[KA], A.bc_hi[KA], flip[s]);
+        src[s] = ((long long)c[2] * A.n[1] + c[1]) * A.n[0] + c[0];
+        T U[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) U[f] = A.Uc[f * A.N + src[s]];
+        if (flip[s]) U[R::n] = -U[R::n];
+        cons_to_prim(U, A.gm1, q[s]);
+    }
+    // face flux cotangent from the two neighbouring cells' lambda
+    T Fb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const T lr = m < na ? A.lam * A.gout[f * A.N + src[2]] : T(0);
+        const T ll = m > 0 ? A.lam * A.gout[f * A.N + src[1]] : T(0);
+        Fb[f] = sub_over_dx(T(0), ll - lr, A.dxk[KA]);   // (lambda_m - lambda_{m-1}) / dx
+    }
+    // forward face states, remembering the minmod selections
+    T qL[NF], qR[NF];
+    int s1[NF], s2[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const T d0 = q[1][f] - q[0][f], d1 = q[2][f] - q[1][f], d2 = q[3][f] - q[2][f];
+        s1[f] = minmod_sel(d0, d1);
+        s2[f] = minmod_sel(d1, d2);
+        const T m1 = s1[f] == 1 ? d0 : (s1[f] == 2 ? d1 : T(0));
+        const T m2 = s2[f] == 1 ? d1 : (s2[f] == 2 ? d2 : T(0));
+        qL[f] = madd(T(0.5), m1, q[1][f]);
+        qR[f] = madd(T(-0.5), m2, q[2][f]);
+    }
+    const T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
+    const T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
+    const T Fn_b[NF] = {Fb[0], Fb[R::n], Fb[R::t1], Fb[R::t2], Fb[4]};
+    T WLb[NF], WRb[NF], gb = T(0);
+    hllc_vjp(WL, WR, A.gamma, Fn_b, WLb, WRb, gb);
+    gacc += (double)gb;
+    T qLb[NF], qRb[NF];
+    qLb[0] = WLb[0]; qLb[R::n] = WLb[1]; qLb[R::t1] = WLb[2]; qLb[R::t2] = WLb[3]; qLb[4] = WLb[4];
+    qRb[0] = WRb[0]; qRb[R::n] = WRb[1]; qRb[R::t1] = WRb[2]; qRb[R::t2] = WRb[3]; qRb[4] = WRb[4];
+    // face states backwards onto the four stencil primitives
+    T qb[4][NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        qb[0][f] = T(0); qb[1][f] = qLb[f]; qb[2][f] = qRb[f]; qb[3][f] = T(0);
+        const T s1b = T(0.5) * qLb[f], s2b = T(-0.5) * qRb[f];
+        if (s1[f] == 1) { qb[1][f] += s1b; qb[0][f] -= s1b; }
+        if (s1[f] == 2) { qb[2][f] += s1b; qb[1][f] -= s1b; }
+        if (s2[f] == 1) { qb[2][f] += s2b; qb[1][f] -= s2b; }
+        if (s2[f] == 2) { qb[3][f] += s2b; qb[2][f] -= s2b; }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (flip[s]) qb[s][R::n] = -qb[s][R::n];
+        const bool any = qb[s][0] != T(0) || qb[s][1] != T(0) || qb[s][2] != T(0) ||
+                         qb[s][3] != T(0) || qb[s][4] != T(0);
+        if (any) accumulate_cell(A.gW + src[s] * GW_STRIDE, qb[s]);
+    }
+}
+
+// All faces of a stage in one launch.  The index space is the cell grid
+// extended by one along every active axis, x fastest (coalesced): the point
+// (i0, i1, i2) owns the x face left of cell (i0, i1, i2) when i1, i2 are in
+// range, the y face below it when i0, i2 are, and the z face when i0, i1 are.
+template <typename T, int DIM, int PX, int PY>
+__global__ void __launch_bounds__(256) faces_vjp_kernel(const AdjArgs<T> A) {
+    const int e0 = A.n[0] + 1, e1 = DIM >= 2 ? A.n[1] + 1 : 1, e2 = DIM >= 3 ? A.n[2] + 1 : 1;
+    const long long total = (long long)e0 * e1 * e2;
     double gacc = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nfaces;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)(e % (na + 1));                 // face between cells m-1 and m
-        const long long rest = e / (na + 1);
-        int c3[3];
-        if (KA == 0) { c3[1] = (int)(rest % A.n[1]); c3[2] = (int)(rest / A.n[1]); }
-        if (KA == 1) { c3[0] = (int)(rest % A.n[0]); c3[2] = (int)(rest / A.n[0]); }
-        if (KA == 2) { c3[0] = (int)(rest % A.n[0]); c3[1] = (int)(rest / A.n[0]); }
-        long long src[4];
-        bool flip[4];
-        T q[4][NF];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            int c[3] = {c3[0], c3[1], c3[2]};
-            c[KA] = bc_map(m - 2 + s, na, A.bc_lo[KA], A.bc_hi[KA], flip[s]);
-            src[s] = ((long long)c[2] * A.n[1] + c[1]) * A.n[0] + c[0];
-            T U[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) U[f] = A.Uc[f * A.N + src[s]];
-            if (flip[s]) U[R::n] = -U[R::n];
-            cons_to_prim(U, A.gm1, q[s]);
-        }
-        // face flux cotangent from the two neighbouring cells' lambda
-        T Fb[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const T lr = m < na ? A.lam * A.gout[f * A.N + src[2]] : T(0);
-            const T ll = m > 0 ? A.lam * A.gout[f * A.N + src[1]] : T(0);
-            Fb[f] = sub_over_dx(T(0), ll - lr, A.dxk[KA]);   // (lambda_m - lambda_{m-1}) / dx
-        }
-        // forward face states, remembering the minmod selections
-        T qL[NF], qR[NF];
-        int s1[NF], s2[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const T d0 = q[1][f] - q[0][f], d1 = q[2][f] - q[1][f], d2 = q[3][f] - q[2][f];
-            s1[f] = minmod_sel(d0, d1);
-            s2[f] = minmod_sel(d1, d2);
-            const T m1 = s1[f] == 1 ? d0 : (s1[f] == 2 ? d1 : T(0));
-            const T m2 = s2[f] == 1 ? d1 : (s2[f] == 2 ? d2 : T(0));
-            qL[f] = madd(T(0.5), m1, q[1][f]);
-            qR[f] = madd(T(-0.5), m2, q[2][f]);
-        }
-        const T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
-        const T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
-        const T Fn_b[NF] = {Fb[0], Fb[R::n], Fb[R::t1], Fb[R::t2], Fb[4]};
-        T WLb[NF], WRb[NF], gb = T(0);
-        hllc_vjp(WL, WR, A.gamma, Fn_b, WLb, WRb, gb);
-        gacc += (double)gb;
-        T qLb[NF], qRb[NF];
-        qLb[0] = WLb[0]; qLb[R::n] = WLb[1]; qLb[R::t1] = WLb[2]; qLb[R::t2] = WLb[3]; qLb[4] = WLb[4];
-        qRb[0] = WRb[0]; qRb[R::n] = WRb[1]; qRb[R::t1] = WRb[2]; qRb[R::t2] = WRb[3]; qRb[4] = WRb[4];
-        // face states backwards onto the four stencil primitives
-        T qb[4][NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            qb[0][f] = T(0); qb[1][f] = qLb[f]; qb[2][f] = qRb[f]; qb[3][f] = T(0);
-            const T s1b = T(0.5) * qLb[f], s2b = T(-0.5) * qRb[f];
-            if (s1[f] == 1) { qb[1][f] += s1b; qb[0][f] -= s1b; }
-            if (s1[f] == 2) { qb[2][f] += s1b; qb[1][f] -= s1b; }
-            if (s2[f] == 1) { qb[2][f] += s2b; qb[1][f] -= s2b; }
-            if (s2[f] == 2) { qb[3][f] += s2b; qb[2][f] -= s2b; }
-        }
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            if (flip[s]) qb[s][R::n] = -qb[s][R::n];
-#pragma unroll
-            for (int f = 0; f < NF; ++f)
-                if (qb[s][f] != T(0)) atomicAdd(A.gW + f * A.N + src[s], qb[s][f]);
-        }
+        const int c3[3] = {(int)(e % e0), (int)((e / e0) % e1), (int)(e / ((long long)e0 * e1))};
+        const bool in0 = c3[0] < A.n[0], in1 = DIM < 2 || c3[1] < A.n[1];
+        const bool in2 = DIM < 3 || c3[2] < A.n[2];
+        if (in1 && in2) face_vjp_one<T, 0, PX>(A, c3, gacc);
+        if (DIM >= 2 && in0 && in2) face_vjp_one<T, 1, PY>(A, c3, gacc);
+        if (DIM >= 3 && in0 && in1) face_vjp_one<T, 2, 2>(A, c3, gacc);
     }
     // block sum of the explicit d/dgamma, one atomic per block
     __shared__ double red[8];
@@ -281,14 +307,15 @@ __global__ void __launch_bounds__(256) face_vjp_kernel(const AdjArgs<T> A) {
 }
 
 // Per cell: the transpose of the conserved-to-primitive map applied to the
-// accumulated primitive cotangent, plus the RK combine:
+// accumulated primitive cotangent (which it may clear after reading), plus the
+// RK combine:
 //     out_c  (=|+=)  b G + J_prim^T gW,      out0 = a G  (when out0 != null)
 // and d/dgamma of p = (gamma-1)(E - kin): gW_p * p / (gamma - 1).
 template <typename T>
-__global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, const T* gW, const T* G,
-                                                       T b, T a, T* out_c, bool accumulate,
-                                                       T* out0, long long N, T gamma,
-                                                       double* g_gamma) {
+__global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, T* gW, const T* G, T b, T a,
+                                                       T* out_c, bool accumulate, T* out0,
+                                                       long long N, T gamma, double* g_gamma,
+                                                       bool clear_gW) {
     double gacc = 0.0;
     const T g1 = gamma - T(1);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
@@ -297,7 +324,11 @@ __global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, const T* gW,
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             U[f] = Uc[f * N + c];
-            Wb[f] = gW[f * N + c];
+            Wb[f] = gW[c * GW_STRIDE + f];
+        }
+        if (clear_gW) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) gW[c * GW_STRIDE + f] = T(0);   // ready for the next use
         }
         cons_to_prim(U, g1, W);
         const T r = W[0], u = W[1], v = W[2], w = W[3];

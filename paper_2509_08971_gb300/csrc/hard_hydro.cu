@@ -464,7 +464,11 @@ int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_ou
     if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
     int rc = ensure_U1(h);
     if (rc) return rc;
-    const size_t need = 2 * state_bytes(h);
+    // adjoint scratch: the primitive cotangent accumulator (8 slots per cell,
+    // zero between calls: zeroed here once, cleared by each cell pass) and
+    // the cotangent of the intermediate stage
+    const size_t gw_bytes = 8 * (size_t)h->mesh.N * elem_size(h);
+    const size_t need = gw_bytes + state_bytes(h);
     if (!h->adj || h->adj_bytes < need) {
         if (h->adj) cudaFree(h->adj);
         h->adj = nullptr;
@@ -472,9 +476,10 @@ int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_ou
         rc = dev_alloc(&h->adj, need);
         if (rc) return rc;
         h->adj_bytes = need;
+        if (cudaMemset(h->adj, 0, gw_bytes) != cudaSuccess) return HARD_ECUDA;
     }
     void* gW = h->adj;
-    void* gU1 = static_cast<unsigned char*>(h->adj) + state_bytes(h);
+    void* gU1 = static_cast<unsigned char*>(h->adj) + gw_bytes;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->last = s;
     // recompute the intermediate stage U1 = Un + dt L(Un)
@@ -482,12 +487,13 @@ int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_ou
     cudaError_t e = stage_launch(h, c1, s);
     if (e != cudaSuccess) return from_cuda(e);
     // stage 2: U^{n+1} = Un/2 + (U1 + dt L(U1))/2
-    const hh::AdjointCall a2{h->U1, gU_out, gW, gU1, false, gU_in, 0.5, 0.5, 0.5 * dt, g_gamma};
+    const hh::AdjointCall a2{h->U1, gU_out, gW, gU1, false, gU_in, 0.5, 0.5, 0.5 * dt, g_gamma,
+                             true};
     e = h->dtype == HARD_F64 ? hh::launch_adjoint_stage_f64(h->mesh, a2, s)
                              : hh::launch_adjoint_stage_f32(h->mesh, a2, s);
     if (e != cudaSuccess) return from_cuda(e);
     // stage 1: U1 = Un + dt L(Un)
-    const hh::AdjointCall a1{U_in, gU1, gW, gU_in, true, nullptr, 1.0, 0.0, dt, g_gamma};
+    const hh::AdjointCall a1{U_in, gU1, gW, gU_in, true, nullptr, 1.0, 0.0, dt, g_gamma, true};
     e = h->dtype == HARD_F64 ? hh::launch_adjoint_stage_f64(h->mesh, a1, s)
                              : hh::launch_adjoint_stage_f32(h->mesh, a1, s);
     return from_cuda(e);

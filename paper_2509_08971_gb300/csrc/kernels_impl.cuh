@@ -316,12 +316,13 @@ AdjArgs<T> make_adj(const MeshDesc& m, const AdjointCall& c) {
     return A;
 }
 
-template <int KA, int PA>
-cudaError_t run_face_vjp(const AdjArgs<T>& A, cudaStream_t s) {
-    const long long faces = (long long)(A.n[KA] + 1) * (A.N / A.n[KA]);
-    long long blocks = (faces + 255) / 256;
+template <int DIM, int PX, int PY>
+cudaError_t run_faces_vjp(const AdjArgs<T>& A, int dim, cudaStream_t s) {
+    long long total = (long long)(A.n[0] + 1) * (dim >= 2 ? A.n[1] + 1 : 1) *
+                      (dim >= 3 ? A.n[2] + 1 : 1);
+    long long blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    face_vjp_kernel<T, KA, PA><<<(int)blocks, 256, 0, s>>>(A);
+    faces_vjp_kernel<T, DIM, PX, PY><<<(int)blocks, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -386,28 +387,22 @@ cudaError_t HH_CAT(launch_batched_, HH_SUFFIX)(const BatchCall& c, int tile, cud
 namespace hh {
 cudaError_t HH_CAT(launch_adjoint_stage_, HH_SUFFIX)(const MeshDesc& m, const AdjointCall& c,
                                                      cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(c.gW, 0, sizeof(T) * 5 * (size_t)m.N, s);
-    if (e != cudaSuccess) return e;
     const AdjArgs<T> A = make_adj(m, c);
-    if (m.dim >= 1) {
-        e = m.px == 0 ? run_face_vjp<0, 0>(A, s)
-                      : (m.px == 1 ? run_face_vjp<0, 1>(A, s) : run_face_vjp<0, 2>(A, s));
-        if (e != cudaSuccess) return e;
-    }
-    if (m.dim >= 2) {
-        e = m.py == 1 ? run_face_vjp<1, 1>(A, s) : run_face_vjp<1, 2>(A, s);
-        if (e != cudaSuccess) return e;
-    }
-    if (m.dim >= 3) {
-        e = run_face_vjp<2, 2>(A, s);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = cudaSuccess;
+    if (m.dim == 3) e = run_faces_vjp<3, 0, 1>(A, 3, s);
+    else if (m.dim == 2)
+        e = m.px == 0 ? (m.py == 1 ? run_faces_vjp<2, 0, 1>(A, 2, s) : run_faces_vjp<2, 0, 2>(A, 2, s))
+                      : run_faces_vjp<2, 1, 2>(A, 2, s);
+    else if (m.dim == 1)
+        e = m.px == 0 ? run_faces_vjp<1, 0, 0>(A, 1, s)
+                      : (m.px == 1 ? run_faces_vjp<1, 1, 0>(A, 1, s) : run_faces_vjp<1, 2, 0>(A, 1, s));
+    if (e != cudaSuccess) return e;
     long long blocks = (m.N + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     cell_vjp_kernel<T><<<(int)blocks, 256, 0, s>>>(
-        static_cast<const T*>(c.Uc), static_cast<const T*>(c.gW), static_cast<const T*>(c.G),
-        (T)c.b, (T)c.a, static_cast<T*>(c.out_c), c.accumulate, static_cast<T*>(c.out0), m.N,
-        (T)m.gamma, c.g_gamma);
+        static_cast<const T*>(c.Uc), static_cast<T*>(c.gW), static_cast<const T*>(c.G), (T)c.b,
+        (T)c.a, static_cast<T*>(c.out_c), c.accumulate, static_cast<T*>(c.out0), m.N,
+        (T)m.gamma, c.g_gamma, c.clear_gW);
     return cudaGetLastError();
 }
 }  // namespace hh

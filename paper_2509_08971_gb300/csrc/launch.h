@@ -105,9 +105,11 @@ inline constexpr int BATCH_TILE_COUNT = 3;
 cudaError_t launch_batched_f32(const BatchCall& c, int tile, cudaStream_t s);
 cudaError_t launch_batched_f64(const BatchCall& c, int tile, cudaStream_t s);
 
-// VJP of one stage (adjoint.cuh): gW is zeroed and used as the primitive
-// cotangent accumulator; out_c (=|+=) b G + J^T(lam G) term; out0 = a G when
-// not null; d/dgamma added to *g_gamma.
+// VJP of one stage (adjoint.cuh): gW, 8 slots per cell holding zeros on
+// entry, is the primitive cotangent accumulator (cleared again on exit when
+// clear_gW);
+// out_c (=|+=) b G + J^T(lam G) term; out0 = a G when not null; d/dgamma
+// added to *g_gamma.
 struct AdjointCall {
     const void* Uc;
     const void* G;
@@ -117,6 +119,7 @@ struct AdjointCall {
     void* out0;
     double b, a, lam;
     double* g_gamma;
+    bool clear_gW;
 };
 cudaError_t launch_adjoint_stage_f32(const MeshDesc& m, const AdjointCall& c, cudaStream_t s);
 cudaError_t launch_adjoint_stage_f64(const MeshDesc& m, const AdjointCall& c, cudaStream_t s);
