@@ -4,7 +4,7 @@
 // operation order), different data movement:
 //   * one elected thread streams the haloed conserved plane of the CTA's
 //     column, box (TX+8) x (TY+4) x 5 fields, with one 4D bulk tensor load per
-//     plane into a 5-slot shared-memory ring, two planes ahead, completing on
+//     plane into a 4-slot shared-memory ring, one plane ahead, completing on
 //     one mbarrier per slot;
 //   * periodic x/y ghosts of boundary tiles arrive as narrow extra boxes of
 //     the wrapped columns / rows on the same mbarrier; outflow and reflecting
@@ -27,8 +27,8 @@ struct TmaMaps {
 
 template <typename T, int TX, int TY>
 struct TmaLayout {
-    static constexpr int D = 5;                         // ring slots
-    static constexpr int P = 2;                         // planes loaded ahead
+    static constexpr int D = 4;                         // ring slots
+    static constexpr int P = 1;                         // planes loaded ahead
     static constexpr int HXC = TX + 8, HYC = TY + 4;    // conserved box
     // every TMA destination starts on a 128-byte boundary
     static constexpr int A128 = 128 / (int)sizeof(T);
@@ -39,24 +39,28 @@ struct TmaLayout {
     static constexpr int XLO = MAIN, XHI = MAIN + XS, YLO = MAIN + 2 * XS, YHI = YLO + YS;
     static constexpr int SLOT = MAIN + 2 * XS + 2 * YS; // elements per slot
     static constexpr int HXP = TX + 4, HYP = TY + 4;    // primitive plane
-    static constexpr int NP = NF * HYP * HXP;
-    static constexpr int NFX = NF * TY * (TX + 1);
-    static constexpr int NFY = NF * (TY + 1) * TX;
+    static constexpr int NP = NF * HYP * HXP;           // one primitive plane
+    static constexpr int NFX = NF * TY * (TX + 1);      // one plane of x-face fluxes
+    static constexpr int NFY = NF * (TY + 1) * TX;      // one plane of y-face fluxes
+    // the primitive and face-flux planes are double-buffered by plane parity
     static constexpr size_t BAR_BYTES = 128;            // D mbarriers, then the ring
     static constexpr size_t RED_BYTES = (TX * TY / 32) * (NF + 1) * 8;
     static constexpr size_t data_bytes =
-        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NP + NFX + NFY) + RED_BYTES;
+        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + 2 * (NP + NFX + NFY)) + RED_BYTES;
     static constexpr size_t bytes = data_bytes + 128;   // slack to align the base by hand
     static constexpr uint32_t MAIN_BYTES = sizeof(T) * NF * HYC * HXC;
     static constexpr uint32_t XS_BYTES = sizeof(T) * NF * HYC * 4;
     static constexpr uint32_t YS_BYTES = sizeof(T) * NF * 2 * HXC;
-    static constexpr size_t RED_OFF = BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NP + NFX + NFY);
+    static constexpr size_t RED_OFF =
+        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + 2 * (NP + NFX + NFY));
     static_assert((SLOT * sizeof(T)) % 128 == 0 && (XLO * sizeof(T)) % 128 == 0 &&
                   (XHI * sizeof(T)) % 128 == 0 && (YLO * sizeof(T)) % 128 == 0 &&
                   (YHI * sizeof(T)) % 128 == 0 && BAR_BYTES % 128 == 0,
                   "every TMA destination must start on a 128-byte boundary");
     static_assert(RED_OFF % 8 == 0, "reduction scratch must be 8-byte aligned");
-    static_assert(P < D - 2, "a slot is read until two planes after it lands");
+    // A slot is read until two iterations after its own, and the load for
+    // iteration it + P is issued after the first barrier of iteration it.
+    static_assert(P <= D - 3, "ring too shallow for the prefetch distance");
 };
 
 // FP32 blocks of up to 256 threads run two per SM (register cap 128 per
@@ -73,15 +77,17 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t* bars = reinterpret_cast<uint64_t*>(base);
-    int* s_abort_p = reinterpret_cast<int*>(base + 8 * D);
+    // abort flags by plane parity: a thread one plane ahead (past barrier A of a
+    // column-only plane) must not change the flag that a slower thread reads
+    int* s_abort = reinterpret_cast<int*>(base + 8 * D);
+    static_assert(8 * D + 2 * sizeof(int) <= L::BAR_BYTES, "barrier block too small");
     T* ring = reinterpret_cast<T*>(base + L::BAR_BYTES);
-    T* Ps = ring + D * L::SLOT;                       // [NF][HYP][HXP]
-    T* Fx = Ps + L::NP;                               // [NF][TY][TX+1]
-    T* Fy = Fx + L::NFX;                              // [NF][TY+1][TX]
-    double (*red_tot)[NF] = reinterpret_cast<double (*)[NF]>(Fy + L::NFY);
+    T* Ps2 = ring + D * L::SLOT;                      // 2 x [NF][HYP][HXP]
+    T* Fx2 = Ps2 + 2 * L::NP;                         // 2 x [NF][TY][TX+1]
+    T* Fy2 = Fx2 + 2 * L::NFX;                        // 2 x [NF][TY+1][TX]
+    double (*red_tot)[NF] = reinterpret_cast<double (*)[NF]>(Fy2 + 2 * L::NFY);
     unsigned long long* red_rate =
         reinterpret_cast<unsigned long long*>(reinterpret_cast<double*>(red_tot) + (NT / 32) * NF);
-    int& s_abort = *s_abort_p;
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -125,7 +131,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     if (tid == 0) {
         for (int s = 0; s < D; ++s) mbar_init(bars + s, 1);
         mbar_fence_init();
-        s_abort = 0;
+        s_abort[0] = s_abort[1] = 0;
         prefetch_tmap(&M.main);
     }
     __syncthreads();
@@ -187,12 +193,17 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
 #pragma unroll
     for (int f = 0; f < NF; ++f) u0c[f] = u0n[f] = T(0);
 
+    // Barriers: two per plane.  Barrier A (the plane's primitives are in shared
+    // memory) also marks every thread done with iteration it-1, which frees
+    // the ring slot that the next load overwrites; the primitive and flux
+    // planes alternate by parity, so a new plane never overwrites one that a
+    // slower thread may still be reading.
     int it = 0;
     for (; it < niter; ++it) {
         const int j = jbeg + it;
-        __syncthreads();                              // iteration it-1 done with its slots
-        if (s_abort) break;
-        if (tid == 0 && it + P < niter) issue(it + P);
+        T* Ps = Ps2 + (it & 1) * L::NP;
+        T* Fx = Fx2 + (it & 1) * L::NFX;
+        T* Fy = Fy2 + (it & 1) * L::NFY;
         const int k = j - 2;                          // cell completed this iteration
         const bool upd = it >= 4 && own;
         if (A.stage == 2 && own && it >= 3 && it + 1 < niter) {
@@ -203,11 +214,11 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         }
         if (!mbar_wait(bars + (it % D), (uint32_t)((it / D) & 1))) {
             atomicOr(A.status, 4);
-            s_abort = 1;
+            s_abort[it & 1] = 1;
         }
         const T* S = slot_main(it);
         const bool xy = j >= z0 && j < z1;
-        T qj[NF], Dj[NF];
+        T qj[NF], Dj[NF], Fown_x[NF], Fown_y[NF];
         if (xy) {
             // conserved -> primitive over the haloed (TX+4) x (TY+4) plane
 #pragma unroll
@@ -229,37 +240,43 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
 #pragma unroll
                 for (int f = 0; f < NF; ++f) Ps[f * NPF + e] = W[f];
             }
-            __syncthreads();
-            // each thread: the x face left of its cell and the y face below it
+            __syncthreads();                          // barrier A
+            if (s_abort[it & 1]) break;
+            if (tid == 0 && it + P < niter) issue(it + P);
+            // this thread's own cell: shared by its x face, its y face and the z stencil
+#pragma unroll
+            for (int f = 0; f < NF; ++f) qj[f] = Ps[(f * HYP + ty + 2) * HXP + tx + 2];
+            // the x face left of the cell and the y face below it
             T q[4][NF], F[NF];
 #pragma unroll
             for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + 2) * HXP + tx + s4];
-            face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
+                for (int f = 0; f < NF; ++f)
+                    q[s4][f] = s4 == 2 ? qj[f] : Ps[(f * HYP + ty + 2) * HXP + tx + s4];
+            face_flux4<0>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, Fown_x);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) Fx[(f * TY + ty) * (TX + 1) + tx] = F[f];
+            for (int f = 0; f < NF; ++f) Fx[(f * TY + ty) * (TX + 1) + tx] = Fown_x[f];
 #pragma unroll
             for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-                for (int f = 0; f < NF; ++f) q[s4][f] = Ps[(f * HYP + ty + s4) * HXP + tx + 2];
-            face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
+                for (int f = 0; f < NF; ++f)
+                    q[s4][f] = s4 == 2 ? qj[f] : Ps[(f * HYP + ty + s4) * HXP + tx + 2];
+            face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, Fown_y);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + ty) * TX + tx] = F[f];
+            for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + ty) * TX + tx] = Fown_y[f];
             // the TX faces above the top row and the TY faces right of the last column
-            if (tid < TX + TY) {
-                if (tid < TX) {
-                    const int col = tid;
+            auto edge_face = [&](int e) {
+                if (e < TX) {
 #pragma unroll
                     for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
                         for (int f = 0; f < NF; ++f)
-                            q[s4][f] = Ps[(f * HYP + TY + s4) * HXP + col + 2];
+                            q[s4][f] = Ps[(f * HYP + TY + s4) * HXP + e + 2];
                     face_flux4<1>(q[0], q[1], q[2], q[3], gamma, gm1, igm1, F);
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + TY) * TX + col] = F[f];
-                } else {
-                    const int row = tid - TX;
+                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + TY) * TX + e] = F[f];
+                } else if (e < TX + TY) {
+                    const int row = e - TX;
 #pragma unroll
                     for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
@@ -269,13 +286,13 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
 #pragma unroll
                     for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + TX] = F[f];
                 }
-            }
-            __syncthreads();
+            };
+            if (tid < TX + TY) edge_face(tid);
+            __syncthreads();                          // barrier B: every face of the plane
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                qj[f] = Ps[(f * HYP + ty + 2) * HXP + tx + 2];
-                const T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fx[(f * TY + ty) * (TX + 1) + tx];
-                const T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fy[(f * (TY + 1) + ty) * TX + tx];
+                const T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fown_x[f];
+                const T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fown_y[f];
                 Dj[f] = sub_over_dx(T(0), a, A.dxk[0]);
                 Dj[f] = sub_over_dx(Dj[f], b, A.dxk[1]);
             }
@@ -291,6 +308,9 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             cons_to_prim(U, gm1, qj);
 #pragma unroll
             for (int f = 0; f < NF; ++f) Dj[f] = T(0);
+            __syncthreads();                          // barrier A of a column-only plane
+            if (s_abort[it & 1]) break;
+            if (tid == 0 && it + P < niter) issue(it + P);
         }
 
         // z direction: streaming stencil of this column
@@ -343,12 +363,13 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             u0c[f] = u0n[f];
         }
     }
-    if (s_abort) {
-        // a transfer never completed: wait (bounded) for the loads still in
-        // flight so none lands after this block has left, then return
-        // the failed wait was iteration it-1; loads were issued up to it-1+P
+    if (it < niter) {
+        // a transfer never completed (every thread left at the same barrier A):
+        // wait (bounded) for the loads still in flight so none lands after this
+        // block has left, then return; the failed wait was iteration it and
+        // loads were issued up to it-1+P
         if (tid == 0)
-            for (int r = it > 0 ? it - 1 : 0; r < niter && r <= it - 1 + P; ++r)
+            for (int r = it; r < niter && r <= it - 1 + P; ++r)
                 mbar_wait(bars + (r % D), (uint32_t)((r / D) & 1));
         __syncthreads();
         return;
