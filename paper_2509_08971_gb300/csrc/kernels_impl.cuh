@@ -109,11 +109,12 @@ bool encode_state_map(CUtensorMap* map, const void* base, const MeshDesc& m, int
 }
 
 // The TMA kernel needs 3 active axes, rows (and so every stride) a multiple of
-// 16 bytes, at least 4 cells along x (the periodic x strip) and a 16-byte
-// aligned base; otherwise the plain kernel runs.
+// 16 bytes, at least 4 cells along x (the periodic x strip), a 16-byte
+// aligned base and element indices of all five fields below 2^32; otherwise
+// the plain kernel runs.
 bool tma_eligible(const MeshDesc& m, const void* Uc) {
     const int per16 = 16 / (int)sizeof(T);
-    return m.dim == 3 && m.n[0] % per16 == 0 && m.n[0] >= 4 &&
+    return m.dim == 3 && m.n[0] % per16 == 0 && m.n[0] >= 4 && 5 * m.N < (1ll << 32) &&
            (reinterpret_cast<uintptr_t>(Uc) & 15u) == 0 && encode_fn() != nullptr;
 }
 
@@ -122,7 +123,7 @@ constexpr size_t SMEM_LIMIT = 232448;     // 227 KB opt-in per block
 template <int TX, int TY>
 cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall& c,
                           cudaStream_t s, bool& used) {
-    using L = TmaLayout<T, TX, TY>;
+    using L = TmaLayout<T, TX, TY, 2>;                 // the larger of the two stages
     used = false;
     if constexpr (L::bytes > SMEM_LIMIT) {
         return cudaSuccess;
@@ -130,19 +131,24 @@ cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall
         TmaMaps maps;
         if (!encode_state_map(&maps.main, c.Uc, m, TX + 8, TY + 4) ||
             !encode_state_map(&maps.xstrip, c.Uc, m, 4, TY + 4) ||
-            !encode_state_map(&maps.ystrip, c.Uc, m, TX + 8, 2))
+            !encode_state_map(&maps.ystrip, c.Uc, m, TX + 8, 2) ||
+            !encode_state_map(&maps.u0, c.stage == 2 ? c.U0 : c.Uc, m, TX, TY))
             return cudaSuccess;
         StageArgs<T> A = make_args(m, td, c);
         dim3 grid(cdiv(m.n[0], TX), cdiv(m.n[1], TY), cdiv(m.n[2], A.zchunk));
-        auto kern = stage_tma_kernel<T, TX, TY>;
+        auto kern = c.stage == 1 ? stage_tma_kernel<T, TX, TY, 1> : stage_tma_kernel<T, TX, TY, 2>;
+        constexpr size_t b1 = TmaLayout<T, TX, TY, 1>::bytes, b2 = L::bytes;
         static bool attr = false;
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)L::bytes);
+            cudaError_t e = cudaFuncSetAttribute(stage_tma_kernel<T, TX, TY, 1>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(stage_tma_kernel<T, TX, TY, 2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        kern<<<grid, TX * TY, L::bytes, s>>>(A, maps);
+        kern<<<grid, TX * TY, c.stage == 1 ? b1 : b2, s>>>(A, maps);
         used = true;
         return cudaGetLastError();
     }

@@ -20,12 +20,13 @@
 namespace hh {
 
 struct TmaMaps {
-    CUtensorMap main;    // box (TX+8, TY+4, 1, 5)
-    CUtensorMap xstrip;  // box (4, TY+4, 1, 5)
-    CUtensorMap ystrip;  // box (TX+8, 2, 1, 5)
+    CUtensorMap main;    // box (TX+8, TY+4, 1, 5) of Uc
+    CUtensorMap xstrip;  // box (4, TY+4, 1, 5) of Uc
+    CUtensorMap ystrip;  // box (TX+8, 2, 1, 5) of Uc
+    CUtensorMap u0;      // box (TX, TY, 1, 5) of U0 (stage 2)
 };
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int STAGE = 1>
 struct TmaLayout {
     static constexpr int D = 4;                         // ring slots
     static constexpr int P = 1;                         // planes loaded ahead
@@ -38,6 +39,10 @@ struct TmaLayout {
     static constexpr int YS = pad(NF * 2 * HXC);        // y strip box
     static constexpr int XLO = MAIN, XHI = MAIN + XS, YLO = MAIN + 2 * XS, YHI = YLO + YS;
     static constexpr int SLOT = MAIN + 2 * XS + 2 * YS; // elements per slot
+    // stage 2: the tile's U0 plane of the update, two slots by iteration parity
+    static constexpr int U0S = pad(NF * TY * TX);
+    static constexpr int NU0 = STAGE == 2 ? 2 : 0;
+    static constexpr uint32_t U0_BYTES = sizeof(T) * NF * TY * TX;
     static constexpr int HXP = TX + 4, HYP = TY + 4;    // primitive plane
     static constexpr int NP = NF * HYP * HXP;           // one primitive plane
     static constexpr int NFX = NF * TY * (TX + 1);      // one plane of x-face fluxes
@@ -46,13 +51,14 @@ struct TmaLayout {
     static constexpr size_t BAR_BYTES = 128;            // D mbarriers, then the ring
     static constexpr size_t RED_BYTES = (TX * TY / 32) * (NF + 1) * 8;
     static constexpr size_t data_bytes =
-        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + 2 * (NP + NFX + NFY)) + RED_BYTES;
+        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NU0 * U0S + 2 * (NP + NFX + NFY)) + RED_BYTES;
     static constexpr size_t bytes = data_bytes + 128;   // slack to align the base by hand
     static constexpr uint32_t MAIN_BYTES = sizeof(T) * NF * HYC * HXC;
     static constexpr uint32_t XS_BYTES = sizeof(T) * NF * HYC * 4;
     static constexpr uint32_t YS_BYTES = sizeof(T) * NF * 2 * HXC;
     static constexpr size_t RED_OFF =
-        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + 2 * (NP + NFX + NFY));
+        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NU0 * U0S + 2 * (NP + NFX + NFY));
+    static_assert((U0S * sizeof(T)) % 128 == 0, "U0 slots must start on 128-byte boundaries");
     static_assert((SLOT * sizeof(T)) % 128 == 0 && (XLO * sizeof(T)) % 128 == 0 &&
                   (XHI * sizeof(T)) % 128 == 0 && (YLO * sizeof(T)) % 128 == 0 &&
                   (YHI * sizeof(T)) % 128 == 0 && BAR_BYTES % 128 == 0,
@@ -65,10 +71,12 @@ struct TmaLayout {
 
 // FP32 blocks of up to 256 threads run two per SM (register cap 128 per
 // thread); FP64 rings fill an SM's shared memory with one block.
-template <typename T, int TX, int TY>
+// STAGE (1 or 2) is a template parameter: the stage-2 combine and its U0
+// stream compile away from stage 1.
+template <typename T, int TX, int TY, int STAGE>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
 stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__ TmaMaps M) {
-    using L = TmaLayout<T, TX, TY>;
+    using L = TmaLayout<T, TX, TY, STAGE>;
     constexpr int NT = TX * TY;
     constexpr int D = L::D, P = L::P;
     constexpr int HXC = L::HXC, HYC = L::HYC, HXP = L::HXP, HYP = L::HYP;
@@ -82,7 +90,8 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     int* s_abort = reinterpret_cast<int*>(base + 8 * D);
     static_assert(8 * D + 2 * sizeof(int) <= L::BAR_BYTES, "barrier block too small");
     T* ring = reinterpret_cast<T*>(base + L::BAR_BYTES);
-    T* Ps2 = ring + D * L::SLOT;                      // 2 x [NF][HYP][HXP]
+    T* u0s = ring + D * L::SLOT;                      // NU0 x [NF][TY][TX]
+    T* Ps2 = u0s + L::NU0 * L::U0S;                   // 2 x [NF][HYP][HXP]
     T* Fx2 = Ps2 + 2 * L::NP;                         // 2 x [NF][TY][TX+1]
     T* Fy2 = Fx2 + 2 * L::NFX;                        // 2 x [NF][TY+1][TX]
     double (*red_tot)[NF] = reinterpret_cast<double (*)[NF]>(Fy2 + 2 * L::NFY);
@@ -120,7 +129,10 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         uint64_t* bar = bars + (it % D);
         bool fz;
         const int jj = bc_map(jbeg + it, nz, A.bc_lo[2], A.bc_hi[2], fz);
-        mbar_arrive_expect_tx(bar, tx_bytes);
+        // stage 2, update iterations: the U0 plane of the cell completed then
+        const bool with_u0 = STAGE == 2 && it >= 4;
+        mbar_arrive_expect_tx(bar, tx_bytes + (with_u0 ? L::U0_BYTES : 0u));
+        if (with_u0) tma_load_4d(u0s + (it & 1) * L::U0S, &M.u0, x0, y0, jbeg + it - 2, 0, bar);
         tma_load_4d(s, &M.main, x0 - 4, y0 - 2, jj, 0, bar);
         if (px_lo) tma_load_4d(s + L::XLO, &M.xstrip, nx - 4, y0 - 2, jj, 0, bar);
         if (px_hi) tma_load_4d(s + L::XHI, &M.xstrip, 0, y0 - 2, jj, 0, bar);
@@ -186,12 +198,14 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                 }
             }
         }
-        cv[q] = (src < 0 ? 0xFFFF : src) | (fs << 16) | (flip << 28);
+        // interior tiles: the bare slot offset (constant field stride, no flips)
+        cv[q] = edge ? ((src < 0 ? 0xFFFF : src) | (fs << 16) | (flip << 28)) : src;
     }
 
-    T u0c[NF], u0n[NF];                               // U0 of this and of the next update
-#pragma unroll
-    for (int f = 0; f < NF; ++f) u0c[f] = u0n[f] = T(0);
+    // 32-bit element indices (the launcher guarantees 5 N < 2^32): this
+    // thread's cell in the next plane to complete, one plane per update
+    const uint32_t Nu = (uint32_t)A.N, plane = (uint32_t)ny * (uint32_t)nx;
+    uint32_t cell = (uint32_t)z0 * plane + (uint32_t)y * (uint32_t)nx + (uint32_t)x;
 
     // Barriers: two per plane.  Barrier A (the plane's primitives are in shared
     // memory) also marks every thread done with iteration it-1, which frees
@@ -204,14 +218,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         T* Ps = Ps2 + (it & 1) * L::NP;
         T* Fx = Fx2 + (it & 1) * L::NFX;
         T* Fy = Fy2 + (it & 1) * L::NFY;
-        const int k = j - 2;                          // cell completed this iteration
-        const bool upd = it >= 4 && own;
-        if (A.stage == 2 && own && it >= 3 && it + 1 < niter) {
-            // U0 of the cell completed next iteration, one plane ahead of its use
-            const long long c = ((long long)(k + 1) * ny + y) * nx + x;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) u0n[f] = A.U0[f * A.N + c];
-        }
+        const bool upd = it >= 4 && own;              // completes cell j - 2 (z0 at it = 4)
         if (!mbar_wait(bars + (it % D), (uint32_t)((it / D) & 1))) {
             atomicOr(A.status, 4);
             s_abort[it & 1] = 1;
@@ -221,24 +228,40 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         T qj[NF], Dj[NF], Fown_x[NF], Fown_y[NF];
         if (xy) {
             // conserved -> primitive over the haloed (TX+4) x (TY+4) plane
+            if (!edge) {
+                // interior tile: every plane cell is in the main box
 #pragma unroll
-            for (int q = 0; q < MAXE; ++q) {
-                const int e = tid + q * NT;
-                if (q == MAXE - 1 && e >= NPF) break;
-                T U[NF], W[NF];
-                const int off = cv[q] & 0xFFFF, fs = (cv[q] >> 16) & 0xFFF;
-                if (off != 0xFFFF) {
-                    const T* src = S + off;
+                for (int q = 0; q < MAXE; ++q) {
+                    const int e = tid + q * NT;
+                    if (q == MAXE - 1 && e >= NPF) break;
+                    T U[NF], W[NF];
+                    const T* src = S + cv[q];
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) U[f] = src[f * fs];
-                    if (cv[q] & (1 << 28)) U[1] = -U[1];
-                    if (cv[q] & (1 << 29)) U[2] = -U[2];
-                } else {
-                    U[0] = T(1); U[1] = U[2] = U[3] = T(0); U[4] = T(1);
+                    for (int f = 0; f < NF; ++f) U[f] = src[f * (HYC * HXC)];
+                    cons_to_prim(U, gm1, W);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Ps[f * NPF + e] = W[f];
                 }
-                cons_to_prim(U, gm1, W);
+            } else {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) Ps[f * NPF + e] = W[f];
+                for (int q = 0; q < MAXE; ++q) {
+                    const int e = tid + q * NT;
+                    if (q == MAXE - 1 && e >= NPF) break;
+                    T U[NF], W[NF];
+                    const int off = cv[q] & 0xFFFF, fs = (cv[q] >> 16) & 0xFFF;
+                    if (off != 0xFFFF) {
+                        const T* src = S + off;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) U[f] = src[f * fs];
+                        if (cv[q] & (1 << 28)) U[1] = -U[1];
+                        if (cv[q] & (1 << 29)) U[2] = -U[2];
+                    } else {
+                        U[0] = T(1); U[1] = U[2] = U[3] = T(0); U[4] = T(1);
+                    }
+                    cons_to_prim(U, gm1, W);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Ps[f * NPF + e] = W[f];
+                }
             }
             __syncthreads();                          // barrier A
             if (s_abort[it & 1]) break;
@@ -331,17 +354,19 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             for (int f = 0; f < NF; ++f) qLp[f] = qL[f];
         }
         if (upd) {
-            const long long c = ((long long)k * ny + y) * nx + x;
             const T* Sk = slot_main(it - 2);
             T Uo[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T Lf = sub_over_dx(Da[f], Fz[f] - Fzp[f], A.dxk[2]);
                 const T uc = Sk[(f * HYC + ty + 2) * HXC + tx + 4];
-                Uo[f] = A.stage == 1 ? madd(dt, Lf, uc)
-                                     : madd(T(0.5), u0c[f], T(0.5) * madd(dt, Lf, uc));
-                A.Uo[f * A.N + c] = Uo[f];
+                Uo[f] = STAGE == 1
+                            ? madd(dt, Lf, uc)
+                            : madd(T(0.5), u0s[(it & 1) * L::U0S + (f * TY + ty) * TX + tx],
+                                   T(0.5) * madd(dt, Lf, uc));
+                A.Uo[f * Nu + cell] = Uo[f];
             }
+            cell += plane;
             if (A.rate_slot) {
                 T W[NF];
                 cons_to_prim(Uo, gm1, W);
@@ -360,7 +385,6 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             qm1[f] = qj[f];
             Da[f] = Db[f];
             Db[f] = Dj[f];
-            u0c[f] = u0n[f];
         }
     }
     if (it < niter) {

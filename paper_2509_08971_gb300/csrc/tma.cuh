@@ -12,7 +12,7 @@ namespace hh {
 // Iteration limit of one bounded mbarrier wait.  try_wait itself suspends the
 // thread for a hardware-defined window, so this is of the order of a second of
 // wall time: only a lost transfer ever reaches it.
-constexpr long long MBAR_SPIN_LIMIT = 1ll << 20;
+constexpr int MBAR_SPIN_LIMIT = 1 << 20;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -50,7 +50,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait on a phase; false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long i = 0; i < MBAR_SPIN_LIMIT; ++i)
+    for (int i = 0; i < MBAR_SPIN_LIMIT; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
