@@ -49,23 +49,27 @@ def tune(m: HardHydro, U, kernel: int = 0, reps: int = 10, warmup: int = 2,
     U2 = torch.empty_like(U)
     dt = m.cfl_dt(U, 0.4)
     times = {}
-    for tile in range(m.tile_count()):
-        m.set_kernel(kernel, tile)
-        for _ in range(warmup):
-            m.stage(1, None, U, dt, out=U1)
-            m.stage(2, U, U1, dt, out=U2)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            m.stage(1, None, U, dt, out=U1)
-            m.stage(2, U, U1, dt, out=U2)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times[tile] = e0.elapsed_time(e1) / (2 * reps)
-        if verbose:
-            print(f"tile {tile} {m.tile_info(tile)}: {times[tile]:.4f} ms per stage")
+    # two sweeps, the faster of each tile's two timings: a host-side stall in
+    # one timed window (process start-up work, another process) cannot decide
+    for sweep in range(2):
+        for tile in range(m.tile_count()):
+            m.set_kernel(kernel, tile)
+            for _ in range(warmup):
+                m.stage(1, None, U, dt, out=U1)
+                m.stage(2, U, U1, dt, out=U2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                m.stage(1, None, U, dt, out=U1)
+                m.stage(2, U, U1, dt, out=U2)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / (2 * reps)
+            times[tile] = min(ms, times.get(tile, ms))
+            if verbose:
+                print(f"tile {tile} {m.tile_info(tile)}: {ms:.4f} ms per stage")
     best = min(times, key=times.get)
     m.set_kernel(kernel, best)
     _memory[key] = best
