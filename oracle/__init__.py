@@ -32,6 +32,7 @@ _lock = threading.Lock()
 _lib = None
 
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT = 0, 1, 2
+SCHEME_PLM_HLLC, SCHEME_WENO5Z_HLL = 0, 1
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 
@@ -51,7 +52,22 @@ def _declare(lib):
     lib.orc_minmod.argtypes = [ctypes.c_double, ctypes.c_double]
     lib.orc_hllc.restype = None
     lib.orc_hllc.argtypes = [_D, _D, ctypes.c_double, _D]
+    lib.orc_hll.restype = None
+    lib.orc_hll.argtypes = [_D, _D, ctypes.c_double, _D]
+    lib.orc_weno5z.restype = ctypes.c_double
+    lib.orc_weno5z.argtypes = [_D]
     grid = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I, ctypes.c_double]
+    sgrid = [ctypes.c_int] + grid
+    lib.orc_rhs_s.restype = ctypes.c_int
+    lib.orc_rhs_s.argtypes = sgrid + [_D, _D]
+    lib.orc_stage_s.restype = ctypes.c_int
+    lib.orc_stage_s.argtypes = sgrid + [ctypes.c_int, _D, _D, _D, ctypes.c_double]
+    lib.orc_step_s.restype = ctypes.c_int
+    lib.orc_step_s.argtypes = sgrid + [_D, _D, ctypes.c_double]
+    lib.orc_run_s.restype = ctypes.c_int
+    lib.orc_run_s.argtypes = sgrid + [_D, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
+    lib.orc_run_fixed_s.restype = ctypes.c_int
+    lib.orc_run_fixed_s.argtypes = sgrid + [_D, ctypes.c_int, _D]
     lib.orc_rhs.restype = ctypes.c_int
     lib.orc_rhs.argtypes = grid + [_D, _D]
     lib.orc_stage.restype = ctypes.c_int
@@ -115,9 +131,12 @@ def _c64(a) -> np.ndarray:
 
 class Grid:
     """Uniform Cartesian grid: ``shape=(nz, ny, nx)``, extents ``(lx, ly, lz)``,
-    boundary kinds per face ``(x-, x+, y-, y+, z-, z+)``."""
+    boundary kinds per face ``(x-, x+, y-, y+, z-, z+)``; ``scheme`` 0 is
+    PLM-minmod + HLLC, 1 is WENO5-Z + HLL (three cells per active axis at
+    least)."""
 
-    def __init__(self, shape, gamma, bc=BC_PERIODIC, extent=(1.0, 1.0, 1.0), lib=None):
+    def __init__(self, shape, gamma, bc=BC_PERIODIC, extent=(1.0, 1.0, 1.0), lib=None,
+                 scheme=SCHEME_PLM_HLLC):
         nz, ny, nx = shape
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.gamma = float(gamma)
@@ -129,14 +148,22 @@ class Grid:
         self.dxyz = np.array([self.extent[0] / self.nx, self.extent[1] / self.ny,
                               self.extent[2] / self.nz], dtype=np.float64)
         self.lib = lib if lib is not None else load()
+        self.scheme = int(scheme)
+        if self.scheme not in (SCHEME_PLM_HLLC, SCHEME_WENO5Z_HLL):
+            raise ValueError("scheme must be 0 (PLM + HLLC) or 1 (WENO5-Z + HLL)")
+        if self.scheme == SCHEME_WENO5Z_HLL and any(1 < n < 3 for n in (self.nx, self.ny, self.nz)):
+            raise ValueError("WENO5-Z needs at least three cells along every active axis")
 
     @property
     def shape(self):
         return (self.nz, self.ny, self.nx)
 
     def _g(self):
-        return (self.nx, self.ny, self.nz, _dp(self.dxyz),
+        return (self.scheme, self.nx, self.ny, self.nz, _dp(self.dxyz),
                 self.bc6.ctypes.data_as(_I), self.gamma)
+
+    def _g0(self):
+        return self._g()[1:]
 
     def _check(self, U):
         U = _c64(U)
@@ -147,38 +174,40 @@ class Grid:
     def rhs(self, U):
         U = self._check(U)
         L = np.empty_like(U)
-        self.lib.orc_rhs(*self._g(), _dp(U), _dp(L))
+        self.lib.orc_rhs_s(*self._g(), _dp(U), _dp(L))
         return L
 
     def stage(self, stage, U0, Ucur, dt):
         U0, Ucur = self._check(U0), self._check(Ucur)
         out = np.empty_like(Ucur)
-        self.lib.orc_stage(*self._g(), int(stage), _dp(U0), _dp(Ucur), _dp(out), float(dt))
+        self.lib.orc_stage_s(*self._g(), int(stage), _dp(U0), _dp(Ucur), _dp(out), float(dt))
         return out
 
     def step(self, U, dt):
         U = self._check(U)
         out = np.empty_like(U)
-        self.lib.orc_step(*self._g(), _dp(U), _dp(out), float(dt))
+        self.lib.orc_step_s(*self._g(), _dp(U), _dp(out), float(dt))
         return out
 
     def step_heun(self, U, dt):
         U = self._check(U)
         out = np.empty_like(U)
-        self.lib.orc_step_heun(*self._g(), _dp(U), _dp(out), float(dt))
+        if self.scheme != SCHEME_PLM_HLLC:
+            raise NotImplementedError("the Heun-form cross-check covers scheme 0")
+        self.lib.orc_step_heun(*self._g0(), _dp(U), _dp(out), float(dt))
         return out
 
     def max_rate(self, U):
         U = self._check(U)
-        return float(self.lib.orc_max_rate(*self._g(), _dp(U)))
+        return float(self.lib.orc_max_rate(*self._g0(), _dp(U)))
 
     def run(self, U, nsteps, cfl, t_end=0.0, t0=0.0):
         """Returns (U_final, t_final, dt_schedule)."""
         U = self._check(U).copy()
         t = np.array([t0], dtype=np.float64)
         dts = np.zeros(max(int(nsteps), 1), dtype=np.float64)
-        n = self.lib.orc_run(*self._g(), _dp(U), int(nsteps), float(cfl), float(t_end),
-                             _dp(t), _dp(dts))
+        n = self.lib.orc_run_s(*self._g(), _dp(U), int(nsteps), float(cfl), float(t_end),
+                               _dp(t), _dp(dts))
         if n < 0:
             raise FloatingPointError("non-positive or non-finite signal rate")
         return U, float(t[0]), dts[:n].copy()
@@ -186,7 +215,7 @@ class Grid:
     def run_fixed(self, U, dts):
         U = self._check(U).copy()
         dts = _c64(dts)
-        self.lib.orc_run_fixed(*self._g(), _dp(U), int(dts.size), _dp(dts))
+        self.lib.orc_run_fixed_s(*self._g(), _dp(U), int(dts.size), _dp(dts))
         return U
 
     def totals(self, U):
@@ -198,6 +227,22 @@ class Grid:
 
 def minmod(a, b, lib=None):
     return float((lib or load()).orc_minmod(float(a), float(b)))
+
+
+def weno5z(v, lib=None):
+    """WENO5-Z value at the right face of the middle of five cell averages."""
+    v = _c64(v)
+    if v.shape != (5,):
+        raise ValueError("weno5z takes five cell averages")
+    return float((lib or load()).orc_weno5z(_dp(v)))
+
+
+def hll(WL, WR, gamma, lib=None):
+    """x-normal HLL flux of two primitive states (rho, u, v, w, p)."""
+    WL, WR = _c64(WL), _c64(WR)
+    F = np.zeros(5)
+    (lib or load()).orc_hll(_dp(WL), _dp(WR), float(gamma), _dp(F))
+    return F
 
 
 def hllc(WL, WR, gamma, lib=None):

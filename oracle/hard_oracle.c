@@ -27,6 +27,10 @@
  *     (Sec. 3.1 and Sec. 3.5 use a CFL-limited step but print no formula).
  *   - Exact Riemann solver for the 1D ideal-gas Euler equations (Toro ch. 4),
  *     used to build the reference solution of the L1 metric, Eq. "l1_error".
+ *   - Second scheme (scheme = 1), the paper's own choice of Sec. 2.2.2:
+ *     WENO5-Z face states of every primitive (Borges, Carmona, Costa, Don
+ *     2008) and the HLL flux (Harten, Lax, van Leer 1983) with the same
+ *     Davis wave-speed bounds; three ghost layers per active axis.
  *
  * Storage: structure of arrays U[5][nz][ny][nx], x fastest.  Field order
  * rho, rho*u, rho*v, rho*w, E_total.  Ghost cells are not stored; they are
@@ -52,6 +56,7 @@ typedef struct {
     double dx[3];    /* cell widths                                   */
     int bc[6];       /* x-, x+, y-, y+, z-, z+                        */
     double gamma;    /* ratio of specific heats                       */
+    int scheme;      /* 0: PLM-minmod + HLLC;  1: WENO5-Z + HLL        */
 } grid_t;
 
 static size_t ncell(const grid_t* g) { return (size_t)g->n[0] * g->n[1] * g->n[2]; }
@@ -64,7 +69,8 @@ static size_t cell_index(const grid_t* g, int i, int j, int k) {
 static int axis_active(const grid_t* g, int d) { return g->n[d] > 1; }
 
 /*
- * Boundary map for one axis.  Index m in [-2, n+1] (two ghost layers) is
+ * Boundary map for one axis.  Index m in [-3, n+2] (three ghost layers; the
+ * PLM scheme uses two) is
  * mapped to an interior index; *flip is set to 1 when the normal momentum of
  * the source cell must change sign (reflecting wall).
  *   periodic: wrap around;  outflow: copy the nearest interior cell;
@@ -79,7 +85,7 @@ static int ghost_src(int m, int n, int bc_lo, int bc_hi, int* flip) {
         return r < 0 ? r + n : r;
     }
     if (bc == BC_OUTFLOW) return m < 0 ? 0 : n - 1;
-    /* reflect: ghost -1 <- 0, -2 <- 1;  ghost n <- n-1, n+1 <- n-2 */
+    /* reflect: ghost -1 <- 0, -2 <- 1, -3 <- 2;  ghost n <- n-1, n+1 <- n-2, ... */
     *flip = 1;
     return m < 0 ? -1 - m : 2 * n - 1 - m;
 }
@@ -193,6 +199,76 @@ void orc_hllc(const double* WL, const double* WR, double gamma, double* F) {
     hllc_normal(WL, WR, gamma, F);
 }
 
+/*
+ * HLL flux (Harten, Lax, van Leer 1983) for two rotated primitive states,
+ * with the Davis bounds S_L, S_R of hllc_normal:
+ *   F = F_L                                              if 0 <= S_L
+ *       (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L)   if S_L < 0 < S_R
+ *       F_R                                              if S_R <= 0
+ * (the flux of the single averaged state between the two outer waves).
+ */
+static void hll_normal(const double WL[NF], const double WR[NF], double gamma, double F[NF]) {
+    double UL[NF], FL[NF], UR[NF], FR[NF];
+    normal_flux(WL, gamma, UL, FL);
+    normal_flux(WR, gamma, UR, FR);
+    double cL = sqrt(gamma * WL[4] / WL[0]);
+    double cR = sqrt(gamma * WR[4] / WR[0]);
+    double SL = fmin(WL[1] - cL, WR[1] - cR);
+    double SR = fmax(WL[1] + cL, WR[1] + cR);
+    if (0.0 <= SL) {
+        for (int f = 0; f < NF; ++f) F[f] = FL[f];
+        return;
+    }
+    if (SR <= 0.0) {
+        for (int f = 0; f < NF; ++f) F[f] = FR[f];
+        return;
+    }
+    for (int f = 0; f < NF; ++f)
+        F[f] = (SR * FL[f] - SL * FR[f] + SL * SR * (UR[f] - UL[f])) / (SR - SL);
+}
+
+/* Exposed for unit tests: x-normal HLL on primitive states (rho,u,v,w,p). */
+void orc_hll(const double* WL, const double* WR, double gamma, double* F) {
+    hll_normal(WL, WR, gamma, F);
+}
+
+/*
+ * WENO5-Z reconstruction (Borges, Carmona, Costa, Don 2008) of the value at
+ * the right face of the middle cell of v[0..4] = v_{i-2} .. v_{i+2} (cell
+ * averages).  Three third-order candidates on the stencils {i-2,i-1,i},
+ * {i-1,i,i+1}, {i,i+1,i+2}:
+ *   p0 = ( 2 v_{i-2} - 7 v_{i-1} + 11 v_i    ) / 6
+ *   p1 = (  -v_{i-1} + 5 v_i     +  2 v_{i+1}) / 6
+ *   p2 = ( 2 v_i     + 5 v_{i+1} -    v_{i+2}) / 6
+ * Jiang-Shu smoothness indicators
+ *   b0 = 13/12 (v_{i-2} - 2 v_{i-1} + v_i)^2     + 1/4 (v_{i-2} - 4 v_{i-1} + 3 v_i)^2
+ *   b1 = 13/12 (v_{i-1} - 2 v_i + v_{i+1})^2     + 1/4 (v_{i-1} - v_{i+1})^2
+ *   b2 = 13/12 (v_i - 2 v_{i+1} + v_{i+2})^2     + 1/4 (3 v_i - 4 v_{i+1} + v_{i+2})^2
+ * global indicator tau5 = |b0 - b2| and the Z weights
+ *   a_k = d_k (1 + tau5 / (b_k + eps)),  (d0, d1, d2) = (1/10, 6/10, 3/10),
+ *   value = sum a_k p_k / sum a_k.
+ * The exponent on tau5 / (b_k + eps) is 1 (the original WENO-Z) and
+ * eps = 1e-30; the paper fixes neither.  The right state of a face is the
+ * same function of the mirrored stencil.
+ */
+#define WENO_EPS 1e-30
+double orc_weno5z(const double* v) {
+    double p0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+    double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+    double p2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+    double s0 = v[0] - 2.0 * v[1] + v[2], t0 = v[0] - 4.0 * v[1] + 3.0 * v[2];
+    double s1 = v[1] - 2.0 * v[2] + v[3], t1 = v[1] - v[3];
+    double s2 = v[2] - 2.0 * v[3] + v[4], t2 = 3.0 * v[2] - 4.0 * v[3] + v[4];
+    double b0 = 13.0 / 12.0 * s0 * s0 + 0.25 * t0 * t0;
+    double b1 = 13.0 / 12.0 * s1 * s1 + 0.25 * t1 * t1;
+    double b2 = 13.0 / 12.0 * s2 * s2 + 0.25 * t2 * t2;
+    double tau = fabs(b0 - b2);
+    double a0 = 0.1 * (1.0 + tau / (b0 + WENO_EPS));
+    double a1 = 0.6 * (1.0 + tau / (b1 + WENO_EPS));
+    double a2 = 0.3 * (1.0 + tau / (b2 + WENO_EPS));
+    return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+}
+
 /* Component order of the rotated frame for axis d: normal, tangent 1, tangent 2
  * (indices into the momentum/velocity slots 1..3). */
 static const int ROT[3][3] = {{1, 2, 3}, {2, 1, 3}, {3, 1, 2}};
@@ -205,8 +281,15 @@ static const int ROT[3][3] = {{1, 2, 3}, {2, 1, 3}, {3, 1, 2}};
  *   q_R    = q_{i+1} - dq_{i+1} / 2      (right state at i+1/2)
  * then HLLC in the frame whose normal is axis d.
  */
+static void face_flux_weno(const grid_t* g, const double* U, int d, int i, int j, int k,
+                           double F[NF]);
+
 static void face_flux(const grid_t* g, const double* U, int d, int i, int j, int k,
                       double F[NF]) {
+    if (g->scheme == 1) {
+        face_flux_weno(g, U, d, i, j, k, F);
+        return;
+    }
     double W[4][NF];                   /* cells i-1, i, i+1, i+2 along d */
     for (int s = 0; s < 4; ++s) {
         double Uc[NF];
@@ -231,14 +314,59 @@ static void face_flux(const grid_t* g, const double* U, int d, int i, int j, int
     F[4] = Fn[4];
 }
 
-static int make_grid(grid_t* g, int nx, int ny, int nz, const double* dxyz, const int* bc6,
-                     double gamma) {
-    if (nx < 1 || ny < 1 || nz < 1) return -1;
+/*
+ * Numerical flux of scheme 1 through the face between cell (i,j,k) and its
+ * +1 neighbour along axis d: WENO5-Z states of the primitives from the six
+ * cells i-2 .. i+3,
+ *   q_L = weno5z(q_{i-2}, q_{i-1}, q_i, q_{i+1}, q_{i+2})
+ *   q_R = weno5z(q_{i+3}, q_{i+2}, q_{i+1}, q_i, q_{i-1})   (mirrored)
+ * then HLL in the frame whose normal is axis d.
+ */
+static void face_flux_weno(const grid_t* g, const double* U, int d, int i, int j, int k,
+                           double F[NF]) {
+    double W[6][NF];                   /* cells i-2 .. i+3 along d */
+    for (int s = 0; s < 6; ++s) {
+        double Uc[NF];
+        fetch_cons(g, U, d, i, j, k, s - 2, Uc);
+        cons_to_prim(Uc, g->gamma, W[s]);
+    }
+    double qL[NF], qR[NF];
+    for (int f = 0; f < NF; ++f) {
+        double l[5] = {W[0][f], W[1][f], W[2][f], W[3][f], W[4][f]};
+        double r[5] = {W[5][f], W[4][f], W[3][f], W[2][f], W[1][f]};
+        qL[f] = orc_weno5z(l);
+        qR[f] = orc_weno5z(r);
+    }
+    double WLn[NF] = {qL[0], qL[ROT[d][0]], qL[ROT[d][1]], qL[ROT[d][2]], qL[4]};
+    double WRn[NF] = {qR[0], qR[ROT[d][0]], qR[ROT[d][1]], qR[ROT[d][2]], qR[4]};
+    double Fn[NF];
+    hll_normal(WLn, WRn, g->gamma, Fn);
+    F[0] = Fn[0];
+    F[ROT[d][0]] = Fn[1];
+    F[ROT[d][1]] = Fn[2];
+    F[ROT[d][2]] = Fn[3];
+    F[4] = Fn[4];
+}
+
+/* scheme 1 needs three cells along every active axis (three ghost layers
+ * mirror into the interior of a reflecting wall) */
+static int make_grid_s(grid_t* g, int scheme, int nx, int ny, int nz, const double* dxyz,
+                       const int* bc6, double gamma) {
+    if (nx < 1 || ny < 1 || nz < 1 || (scheme != 0 && scheme != 1)) return -1;
     g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
     for (int d = 0; d < 3; ++d) g->dx[d] = dxyz[d];
     for (int f = 0; f < 6; ++f) g->bc[f] = bc6[f];
     g->gamma = gamma;
+    g->scheme = scheme;
+    if (scheme == 1)
+        for (int d = 0; d < 3; ++d)
+            if (g->n[d] > 1 && g->n[d] < 3) return -1;
     return 0;
+}
+
+static int make_grid(grid_t* g, int nx, int ny, int nz, const double* dxyz, const int* bc6,
+                     double gamma) {
+    return make_grid_s(g, 0, nx, ny, nz, dxyz, bc6, gamma);
 }
 
 /*
@@ -284,12 +412,17 @@ static void rhs(const grid_t* g, const double* U, double* L) {
     }
 }
 
-int orc_rhs(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
-            const double* U, double* L) {
+int orc_rhs_s(int scheme, int nx, int ny, int nz, const double* dxyz, const int* bc6,
+              double gamma, const double* U, double* L) {
     grid_t g;
-    if (make_grid(&g, nx, ny, nz, dxyz, bc6, gamma)) return -1;
+    if (make_grid_s(&g, scheme, nx, ny, nz, dxyz, bc6, gamma)) return -1;
     rhs(&g, U, L);
     return 0;
+}
+
+int orc_rhs(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
+            const double* U, double* L) {
+    return orc_rhs_s(0, nx, ny, nz, dxyz, bc6, gamma, U, L);
 }
 
 /*
@@ -298,10 +431,11 @@ int orc_rhs(int nx, int ny, int nz, const double* dxyz, const int* bc6, double g
  *   stage 2:  U^{n+1} = Un/2 + (U1 + dt L(U1))/2
  * stage = 1 reads Ucur = Un; stage = 2 reads Ucur = U1 and U0 = Un.
  */
-int orc_stage(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
-              int stage, const double* U0, const double* Ucur, double* Uout, double dt) {
+int orc_stage_s(int scheme, int nx, int ny, int nz, const double* dxyz, const int* bc6,
+                double gamma, int stage, const double* U0, const double* Ucur, double* Uout,
+                double dt) {
     grid_t g;
-    if (make_grid(&g, nx, ny, nz, dxyz, bc6, gamma)) return -1;
+    if (make_grid_s(&g, scheme, nx, ny, nz, dxyz, bc6, gamma)) return -1;
     size_t n = NF * ncell(&g);
     double* L = (double*)malloc(sizeof(double) * n);
     rhs(&g, Ucur, L);
@@ -315,15 +449,25 @@ int orc_stage(int nx, int ny, int nz, const double* dxyz, const int* bc6, double
     return 0;
 }
 
+int orc_stage(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
+              int stage, const double* U0, const double* Ucur, double* Uout, double dt) {
+    return orc_stage_s(0, nx, ny, nz, dxyz, bc6, gamma, stage, U0, Ucur, Uout, dt);
+}
+
 /* One full step, Shu-Osher form. */
-int orc_step(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
-             const double* Un, double* Unew, double dt) {
+int orc_step_s(int scheme, int nx, int ny, int nz, const double* dxyz, const int* bc6,
+               double gamma, const double* Un, double* Unew, double dt) {
     size_t n = (size_t)NF * nx * ny * nz;
     double* U1 = (double*)malloc(sizeof(double) * n);
-    int rc = orc_stage(nx, ny, nz, dxyz, bc6, gamma, 1, Un, Un, U1, dt);
-    if (!rc) rc = orc_stage(nx, ny, nz, dxyz, bc6, gamma, 2, Un, U1, Unew, dt);
+    int rc = orc_stage_s(scheme, nx, ny, nz, dxyz, bc6, gamma, 1, Un, Un, U1, dt);
+    if (!rc) rc = orc_stage_s(scheme, nx, ny, nz, dxyz, bc6, gamma, 2, Un, U1, Unew, dt);
     free(U1);
     return rc;
+}
+
+int orc_step(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
+             const double* Un, double* Unew, double dt) {
+    return orc_step_s(0, nx, ny, nz, dxyz, bc6, gamma, Un, Unew, dt);
 }
 
 /* One full step in the Butcher form of Heun's method (cross-check only):
@@ -371,8 +515,9 @@ double orc_max_rate(int nx, int ny, int nz, const double* dxyz, const int* bc6, 
  * t reaches t_end.  *t is advanced in place; dt_log (may be NULL) receives
  * each dt.  Returns the number of steps taken, or -1 on a bad rate.
  */
-int orc_run(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
-            double* U, int nsteps, double cfl, double t_end, double* t, double* dt_log) {
+int orc_run_s(int scheme, int nx, int ny, int nz, const double* dxyz, const int* bc6,
+              double gamma, double* U, int nsteps, double cfl, double t_end, double* t,
+              double* dt_log) {
     size_t n = (size_t)NF * nx * ny * nz;
     double* Unew = (double*)malloc(sizeof(double) * n);
     int s = 0;
@@ -382,7 +527,10 @@ int orc_run(int nx, int ny, int nz, const double* dxyz, const int* bc6, double g
         if (!(r > 0.0) || !isfinite(r)) { free(Unew); return -1; }
         double dt = cfl / r;
         if (t_end > 0.0 && *t + dt > t_end) dt = t_end - *t;
-        orc_step(nx, ny, nz, dxyz, bc6, gamma, U, Unew, dt);
+        if (orc_step_s(scheme, nx, ny, nz, dxyz, bc6, gamma, U, Unew, dt)) {
+            free(Unew);
+            return -1;
+        }
         memcpy(U, Unew, sizeof(double) * n);
         *t += dt;
         if (dt_log) dt_log[s] = dt;
@@ -391,17 +539,30 @@ int orc_run(int nx, int ny, int nz, const double* dxyz, const int* bc6, double g
     return s;
 }
 
+int orc_run(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
+            double* U, int nsteps, double cfl, double t_end, double* t, double* dt_log) {
+    return orc_run_s(0, nx, ny, nz, dxyz, bc6, gamma, U, nsteps, cfl, t_end, t, dt_log);
+}
+
 /* Same loop on a recorded dt schedule (no CFL evaluation). */
-int orc_run_fixed(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
-                  double* U, int nsteps, const double* dts) {
+int orc_run_fixed_s(int scheme, int nx, int ny, int nz, const double* dxyz, const int* bc6,
+                    double gamma, double* U, int nsteps, const double* dts) {
     size_t n = (size_t)NF * nx * ny * nz;
     double* Unew = (double*)malloc(sizeof(double) * n);
     for (int s = 0; s < nsteps; ++s) {
-        orc_step(nx, ny, nz, dxyz, bc6, gamma, U, Unew, dts[s]);
+        if (orc_step_s(scheme, nx, ny, nz, dxyz, bc6, gamma, U, Unew, dts[s])) {
+            free(Unew);
+            return -1;
+        }
         memcpy(U, Unew, sizeof(double) * n);
     }
     free(Unew);
     return nsteps;
+}
+
+int orc_run_fixed(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
+                  double* U, int nsteps, const double* dts) {
+    return orc_run_fixed_s(0, nx, ny, nz, dxyz, bc6, gamma, U, nsteps, dts);
 }
 
 /* Conserved totals sum_cells U_f dV with Neumaier compensated summation. */

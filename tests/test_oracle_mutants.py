@@ -13,7 +13,8 @@ import oracle
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = [os.path.join(ROOT, "tests", f) for f in
-        ("test_oracle_hllc.py", "test_oracle_riemann.py", "test_oracle_scheme.py")]
+        ("test_oracle_hllc.py", "test_oracle_riemann.py", "test_oracle_scheme.py",
+         "test_oracle_weno.py")]
 
 # (name, original text, planted text)
 MUTANTS = [
@@ -76,6 +77,31 @@ MUTANTS = [
     ("exact shock pressure function", "*f = (p - pK) * q;", "*f = (p + pK) * q;"),
     ("Heun weights", "Unew[q] = Un[q] + dt * (0.5 * k1[q] + 0.5 * k2[q]);",
      "Unew[q] = Un[q] + dt * (0.5 * k1[q] + 0.5 * k1[q]);"),
+    # second scheme: WENO5-Z face states and the HLL flux
+    ("WENO linear weight d1", "double a1 = 0.6 * (1.0 + tau / (b1 + WENO_EPS));",
+     "double a1 = 0.5 * (1.0 + tau / (b1 + WENO_EPS));"),
+    ("WENO middle candidate stencil", "double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;",
+     "double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[4]) / 6.0;"),
+    ("WENO right candidate sign", "double p2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;",
+     "double p2 = (2.0 * v[2] + 5.0 * v[3] + v[4]) / 6.0;"),
+    ("WENO tau from the wrong indicators", "double tau = fabs(b0 - b2);",
+     "double tau = fabs(b0 - b1);"),
+    ("WENO indicator slope term", "t0 = v[0] - 4.0 * v[1] + 3.0 * v[2];",
+     "t0 = v[0] - 4.0 * v[1] + 2.0 * v[2];"),
+    ("WENO indicator curvature weight", "double b2 = 13.0 / 12.0 * s2 * s2 + 0.25 * t2 * t2;",
+     "double b2 = s2 * s2 + 0.25 * t2 * t2;"),
+    ("WENO weights not normalised", "return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);",
+     "return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1);"),
+    ("WENO right state not mirrored",
+     "double r[5] = {W[5][f], W[4][f], W[3][f], W[2][f], W[1][f]};",
+     "double r[5] = {W[1][f], W[2][f], W[3][f], W[4][f], W[5][f]};"),
+    ("WENO stencil shifted", "fetch_cons(g, U, d, i, j, k, s - 2, Uc);",
+     "fetch_cons(g, U, d, i, j, k, s - 3, Uc);"),
+    ("HLL dissipation sign",
+     "F[f] = (SR * FL[f] - SL * FR[f] + SL * SR * (UR[f] - UL[f])) / (SR - SL);",
+     "F[f] = (SR * FL[f] - SL * FR[f] - SL * SR * (UR[f] - UL[f])) / (SR - SL);"),
+    ("HLL Davis bound", "double SL = fmin(WL[1] - cL, WR[1] - cR);",
+     "double SL = fmin(WL[1] - cL, WR[1] + cR);"),
 ]
 
 
