@@ -56,6 +56,11 @@ enum { HARD_F32 = 0, HARD_F64 = 1 };
  * plain per-thread loads */
 enum { HARD_KERNEL_FUSED = 0, HARD_KERNEL_PLAIN = 1 };
 
+/* face reconstruction and flux (Sec. 2.2.2): minmod-limited PLM states with
+ * the HLLC flux (the default), or the paper's own WENO5-Z states (Borges et
+ * al. 2008) with the HLL flux, three ghost layers */
+enum { HARD_SCHEME_PLM_HLLC = 0, HARD_SCHEME_WENO5Z_HLL = 1 };
+
 enum {
     HARD_OK = 0,
     HARD_EINVAL = -1,        /* bad argument                                  */
@@ -87,6 +92,15 @@ int hard_hydro_set(hard_hydro_t h, int dtype, double lx, double ly, double lz,
 int hard_hydro_set_kernel(hard_hydro_t h, int kernel, int tile);
 int hard_hydro_tile_count(hard_hydro_t h);
 int hard_hydro_tile_info(hard_hydro_t h, int tile, int out4[4]);
+
+/* Choose the scheme of every later stage, step and advance call:
+ * HARD_SCHEME_PLM_HLLC (default) or HARD_SCHEME_WENO5Z_HLL.  The WENO5-Z
+ * scheme needs at least three cells along every active axis (else
+ * HARD_EINVAL), runs one kernel variant (the kernel and tile choice of
+ * hard_hydro_set_kernel apply to the default scheme only), and has no
+ * adjoint: hard_hydro_step_backward returns HARD_EUNSUPPORTED for it.  The
+ * CFL rate and the totals are the same for both schemes. */
+int hard_hydro_set_scheme(hard_hydro_t h, int scheme);
 
 /* One Runge-Kutta stage (Sec. 2.2.2 flux difference, Heun tableau):
  *   stage 1: Uout = Ucur + dt L(Ucur)                       (U0 ignored)

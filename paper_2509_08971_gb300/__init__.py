@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libhard_hydro.so")
 HARD_BC_PERIODIC, HARD_BC_OUTFLOW, HARD_BC_REFLECT = 0, 1, 2
 HARD_F32, HARD_F64 = 0, 1
 HARD_KERNEL_FUSED, HARD_KERNEL_PLAIN = 0, 1
+HARD_SCHEME_PLM_HLLC, HARD_SCHEME_WENO5Z_HLL = 0, 1
 HARD_OK, HARD_EINVAL, HARD_ENOMEM, HARD_ECUDA = 0, -1, -2, -3
 HARD_ENONPHYS, HARD_ETIMEOUT, HARD_EUNSUPPORTED = -4, -5, -6
 
@@ -42,6 +43,7 @@ def _declare(lib):
         "hard_hydro_set": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, _ip]),
         "hard_hydro_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+        "hard_hydro_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int]),
         "hard_hydro_tile_count": (ctypes.c_int, [_vp]),
         "hard_hydro_tile_info": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
         "hard_hydro_stage": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double,
@@ -102,6 +104,10 @@ def hard_hydro_set(h, dtype, lx, ly, lz, bc_per_face=None):
 
 def hard_hydro_set_kernel(h, kernel, tile):
     return lib().hard_hydro_set_kernel(h, int(kernel), int(tile))
+
+
+def hard_hydro_set_scheme(h, scheme):
+    return lib().hard_hydro_set_scheme(h, int(scheme))
 
 
 def hard_hydro_tile_count(h):
@@ -221,7 +227,7 @@ class HardHydro:
     """A mesh handle bound to torch tensors U of shape (5, nz, ny, nx)."""
 
     def __init__(self, shape, gamma, bc=HARD_BC_PERIODIC, dtype=None, extent=(1.0, 1.0, 1.0),
-                 kernel=HARD_KERNEL_FUSED, tile=-1):
+                 kernel=HARD_KERNEL_FUSED, tile=-1, scheme=HARD_SCHEME_PLM_HLLC):
         import torch
         self.torch = torch
         nz, ny, nx = (int(s) for s in shape)
@@ -237,6 +243,7 @@ class HardHydro:
         check(hard_hydro_set(self.h, HARD_F64 if self.dtype == torch.float64 else HARD_F32,
                              *extent, bc6), "hard_hydro_set")
         check(hard_hydro_set_kernel(self.h, kernel, tile), "hard_hydro_set_kernel")
+        check(hard_hydro_set_scheme(self.h, scheme), "hard_hydro_set_scheme")
 
     def __del__(self):
         h, self.h = getattr(self, "h", None), None
@@ -245,6 +252,9 @@ class HardHydro:
 
     def set_kernel(self, kernel, tile=-1):
         check(hard_hydro_set_kernel(self.h, kernel, tile), "hard_hydro_set_kernel")
+
+    def set_scheme(self, scheme):
+        check(hard_hydro_set_scheme(self.h, scheme), "hard_hydro_set_scheme")
 
     def tile_count(self):
         return hard_hydro_tile_count(self.h)

@@ -29,6 +29,8 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 UNITS = {
     "stage_f32.cu": ["--fmad=false"],
     "stage_f64.cu": ["--fmad=false"],
+    "weno_f32.cu": ["--fmad=false"],
+    "weno_f64.cu": ["--fmad=false"],
     "hard_hydro.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],

@@ -8,6 +8,7 @@
 
 #include "hard_hydro.h"
 #include "launch.h"
+#include "weno_launch.h"
 
 using hh::MeshDesc;
 using hh::StageCall;
@@ -20,6 +21,7 @@ struct hard_hydro_s {
     int dtype = HARD_F32;
     int kernel = HARD_KERNEL_FUSED;
     int tile = -1;
+    int scheme = HARD_SCHEME_PLM_HLLC;
     MeshDesc mesh;
     // device scratch, allocated on first use
     void* U1 = nullptr;              // intermediate stage
@@ -153,7 +155,17 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 int tile_of(const hard_hydro_s* h) { return h->tile < 0 ? 0 : h->tile; }
 
+bool weno(const hard_hydro_s* h) { return h->scheme == HARD_SCHEME_WENO5Z_HLL && h->mesh.dim > 0; }
+
+// blocks of one stage launch (rows of the totals partial array)
+long long launch_blocks(const hard_hydro_s* h) {
+    return hh::stage_blocks(h->mesh, weno(h) ? 0 : tile_of(h));
+}
+
 cudaError_t stage_launch(hard_hydro_s* h, const StageCall& c, cudaStream_t s) {
+    if (weno(h))
+        return h->dtype == HARD_F64 ? hh::launch_weno_stage_f64(h->mesh, c, s)
+                                    : hh::launch_weno_stage_f32(h->mesh, c, s);
     if (h->dtype == HARD_F64) return hh::launch_stage_f64(h->mesh, h->kernel, tile_of(h), c, s);
     return hh::launch_stage_f32(h->mesh, h->kernel, tile_of(h), c, s);
 }
@@ -282,6 +294,16 @@ int hard_hydro_set_kernel(hard_hydro_t h, int kernel, int tile) {
     return HARD_OK;
 }
 
+int hard_hydro_set_scheme(hard_hydro_t h, int scheme) {
+    if (!h) return HARD_EINVAL;
+    if (scheme != HARD_SCHEME_PLM_HLLC && scheme != HARD_SCHEME_WENO5Z_HLL) return HARD_EINVAL;
+    if (scheme == HARD_SCHEME_WENO5Z_HLL)
+        for (int a = 0; a < 3; ++a)
+            if (h->n[a] > 1 && h->n[a] < 3) return HARD_EINVAL;
+    h->scheme = scheme;
+    return HARD_OK;
+}
+
 int hard_hydro_tile_count(hard_hydro_t h) {
     if (!h) return HARD_EINVAL;
     return hh::tile_count(h->mesh.dim);
@@ -367,7 +389,7 @@ int hard_hydro_advance(hard_hydro_t h, void* U, int nsteps, double cfl, double t
     if (t_end > 0.0 && !t_dev) return HARD_EINVAL;
     int rc = ensure_U1(h);
     if (rc) return rc;
-    const long long rows = hh::stage_blocks(h->mesh, tile_of(h));
+    const long long rows = launch_blocks(h);
     if (totals_log_dev) {
         rc = ensure_partial(h, rows);
         if (rc) return rc;
@@ -461,6 +483,7 @@ int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_ou
                              double dt, double* g_gamma, void* stream) {
     if (!h || !U_in || !gU_out || !gU_in || !g_gamma) return HARD_EINVAL;
     if (!aligned16(U_in) || !aligned16(gU_out) || !aligned16(gU_in)) return HARD_EINVAL;
+    if (weno(h)) return HARD_EUNSUPPORTED;
     if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
     int rc = ensure_U1(h);
     if (rc) return rc;
@@ -530,6 +553,8 @@ void hard_hydro_destroy(hard_hydro_t h) {
 namespace hh {
 
 // Read-only view of a handle for the library's other translation units.
+int handle_scheme(const hard_hydro_s* h) { return h->scheme; }
+
 bool handle_view(hard_hydro_t h, const MeshDesc** mesh, int* dtype, int* kernel, int* tile) {
     if (!h) return false;
     *mesh = &h->mesh;

@@ -26,6 +26,7 @@
 
 #include "hard_hydro.h"
 #include "launch.h"
+#include "weno_launch.h"
 
 namespace {
 
@@ -88,12 +89,18 @@ extern "C" int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(d.status, 0, sizeof(int), s);
     if (e != cudaSuccess) return HARD_ECUDA;
+    const bool weno = hh::handle_scheme(h) == HARD_SCHEME_WENO5Z_HLL && mesh->dim > 0;
+    auto launch = [&](const hh::StageCall& c) {
+        if (weno)
+            return dtype == HARD_F64 ? hh::launch_weno_stage_f64(*mesh, c, s)
+                                     : hh::launch_weno_stage_f32(*mesh, c, s);
+        return dtype == HARD_F64 ? hh::launch_stage_f64(*mesh, kernel, tile, c, s)
+                                 : hh::launch_stage_f32(*mesh, kernel, tile, c, s);
+    };
     const hh::StageCall c1{1, U_in, U_in, d.scratch, dt, nullptr, nullptr, nullptr, d.status};
-    e = dtype == HARD_F64 ? hh::launch_stage_f64(*mesh, kernel, tile, c1, s)
-                          : hh::launch_stage_f32(*mesh, kernel, tile, c1, s);
+    e = launch(c1);
     if (e != cudaSuccess) return HARD_ECUDA;
     const hh::StageCall c2{2, U_in, d.scratch, U_out, dt, nullptr, nullptr, nullptr, d.status};
-    e = dtype == HARD_F64 ? hh::launch_stage_f64(*mesh, kernel, tile, c2, s)
-                          : hh::launch_stage_f32(*mesh, kernel, tile, c2, s);
+    e = launch(c2);
     return e == cudaSuccess ? HARD_OK : HARD_ECUDA;
 }

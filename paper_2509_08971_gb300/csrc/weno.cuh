@@ -1,0 +1,400 @@
+// Second scheme of the stage update: WENO5-Z face states of the primitives
+// and the HLL flux (Sec. 2.2.2: the paper's own reconstruction and Riemann
+// solver), three ghost layers per active axis.  Same mesh, boundary kinds,
+// RK stage combine and epilogues as the PLM-minmod + HLLC kernels.
+//
+//   WENO5-Z (Borges, Carmona, Costa, Don 2008), value at the right face of
+//   the middle cell of v0..v4 (cell averages):
+//     candidates  p0 = (2 v0 - 7 v1 + 11 v2)/6, p1 = (-v1 + 5 v2 + 2 v3)/6,
+//                 p2 = (2 v2 + 5 v3 - v4)/6
+//     indicators  b0 = 13/12 (v0 - 2v1 + v2)^2 + 1/4 (v0 - 4v1 + 3v2)^2
+//                 b1 = 13/12 (v1 - 2v2 + v3)^2 + 1/4 (v1 - v3)^2
+//                 b2 = 13/12 (v2 - 2v3 + v4)^2 + 1/4 (3v2 - 4v3 + v4)^2
+//     weights     a_k = d_k (1 + |b0 - b2| / (b_k + eps)), d = (1, 6, 3)/10,
+//                 eps = 1e-30; value = sum a_k p_k / sum a_k
+//   The right state of a face is the same function of the mirrored stencil.
+//
+//   HLL (Harten, Lax, van Leer 1983) with the Davis bounds
+//     S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R):
+//     F = F_L (0 <= S_L), F_R (S_R <= 0),
+//         (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) otherwise.
+//
+// FP64 evaluates every formula in the written order with IEEE division and
+// square root (one rounding per operation, no contraction); FP32 multiplies
+// by approximate reciprocals and square roots.
+//
+// Tiling: as stage_kernel (a TX x TY column marching its z-chunk), with a
+// (TX+6) x (TY+6) primitive plane in shared memory and, along z, each thread
+// holding its column's last six primitives in registers: plane j yields the
+// z face between cells j-3 and j-2, and cell j-3 completes.
+#pragma once
+#include "stage_kernel.cuh"
+
+namespace hh {
+
+constexpr int WENO_G = 3;                 // ghost layers
+
+// ---------------------------------------------------------------- WENO5-Z --
+__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4) {
+    const double p0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) / 6.0;
+    const double p1 = (-v1 + 5.0 * v2 + 2.0 * v3) / 6.0;
+    const double p2 = (2.0 * v2 + 5.0 * v3 - v4) / 6.0;
+    const double s0 = v0 - 2.0 * v1 + v2, t0 = v0 - 4.0 * v1 + 3.0 * v2;
+    const double s1 = v1 - 2.0 * v2 + v3, t1 = v1 - v3;
+    const double s2 = v2 - 2.0 * v3 + v4, t2 = 3.0 * v2 - 4.0 * v3 + v4;
+    const double b0 = 13.0 / 12.0 * s0 * s0 + 0.25 * t0 * t0;
+    const double b1 = 13.0 / 12.0 * s1 * s1 + 0.25 * t1 * t1;
+    const double b2 = 13.0 / 12.0 * s2 * s2 + 0.25 * t2 * t2;
+    const double tau = fabs(b0 - b2);
+    const double a0 = 0.1 * (1.0 + tau / (b0 + 1e-30));
+    const double a1 = 0.6 * (1.0 + tau / (b1 + 1e-30));
+    const double a2 = 0.3 * (1.0 + tau / (b2 + 1e-30));
+    return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+}
+__device__ __forceinline__ float weno5z(float v0, float v1, float v2, float v3, float v4) {
+    const float sixth = 1.0f / 6.0f;
+    const float p0 = (2.0f * v0 - 7.0f * v1 + 11.0f * v2) * sixth;
+    const float p1 = (-v1 + 5.0f * v2 + 2.0f * v3) * sixth;
+    const float p2 = (2.0f * v2 + 5.0f * v3 - v4) * sixth;
+    const float s0 = v0 - 2.0f * v1 + v2, t0 = v0 - 4.0f * v1 + 3.0f * v2;
+    const float s1 = v1 - 2.0f * v2 + v3, t1 = v1 - v3;
+    const float s2 = v2 - 2.0f * v3 + v4, t2 = 3.0f * v2 - 4.0f * v3 + v4;
+    const float c = 13.0f / 12.0f;
+    const float b0 = fmaf(c * s0, s0, 0.25f * t0 * t0);
+    const float b1 = fmaf(c * s1, s1, 0.25f * t1 * t1);
+    const float b2 = fmaf(c * s2, s2, 0.25f * t2 * t2);
+    const float tau = fabsf(b0 - b2);
+    const float a0 = 0.1f * fmaf(tau, vrcp(b0 + 1e-30f), 1.0f);
+    const float a1 = 0.6f * fmaf(tau, vrcp(b1 + 1e-30f), 1.0f);
+    const float a2 = 0.3f * fmaf(tau, vrcp(b2 + 1e-30f), 1.0f);
+    return fmaf(a0, p0, fmaf(a1, p1, a2 * p2)) * vrcp(a0 + a1 + a2);
+}
+
+// -------------------------------------------------------------------- HLL --
+// Rotated primitive states W = (rho, un, t1, t2, p), normal along slot 1.
+__device__ __forceinline__ void hll_normal(const double WL[NF], const double WR[NF],
+                                           double gamma, double gm1, double F[NF]) {
+    double UL[NF], FL[NF], UR[NF], FR[NF];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const double* W = s == 0 ? WL : WR;
+        double* U = s == 0 ? UL : UR;
+        double* G = s == 0 ? FL : FR;
+        const double rho = W[0], un = W[1], t1 = W[2], t2 = W[3], p = W[4];
+        const double E = p / gm1 + 0.5 * rho * (un * un + t1 * t1 + t2 * t2);
+        U[0] = rho; U[1] = rho * un; U[2] = rho * t1; U[3] = rho * t2; U[4] = E;
+        G[0] = rho * un; G[1] = rho * un * un + p; G[2] = rho * un * t1;
+        G[3] = rho * un * t2; G[4] = (E + p) * un;
+    }
+    const double cL = sqrt(gamma * WL[4] / WL[0]);
+    const double cR = sqrt(gamma * WR[4] / WR[0]);
+    const double SL = fmin(WL[1] - cL, WR[1] - cR);
+    const double SR = fmax(WL[1] + cL, WR[1] + cR);
+    if (0.0 <= SL) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) F[f] = FL[f];
+    } else if (SR <= 0.0) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) F[f] = FR[f];
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+            F[f] = (SR * FL[f] - SL * FR[f] + SL * SR * (UR[f] - UL[f])) / (SR - SL);
+    }
+}
+__device__ __forceinline__ void hll_normal(const float WL[NF], const float WR[NF], float gamma,
+                                           float igm1, float F[NF]) {
+    float UL[NF], FL[NF], UR[NF], FR[NF];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float* W = s == 0 ? WL : WR;
+        float* U = s == 0 ? UL : UR;
+        float* G = s == 0 ? FL : FR;
+        const float rho = W[0], un = W[1], t1 = W[2], t2 = W[3], p = W[4];
+        const float mu = rho * un;
+        const float E = fmaf(p, igm1, 0.5f * rho * fmaf(un, un, fmaf(t1, t1, t2 * t2)));
+        U[0] = rho; U[1] = mu; U[2] = rho * t1; U[3] = rho * t2; U[4] = E;
+        G[0] = mu; G[1] = fmaf(mu, un, p); G[2] = mu * t1; G[3] = mu * t2; G[4] = (E + p) * un;
+    }
+    const float cL = vsqrt(gamma * WL[4] * vrcp(WL[0]));
+    const float cR = vsqrt(gamma * WR[4] * vrcp(WR[0]));
+    const float SL = fminf(WL[1] - cL, WR[1] - cR);
+    const float SR = fmaxf(WL[1] + cL, WR[1] + cR);
+    // one branch-free form: the upwind cases are the clamped speeds 0 <= SL
+    // (F_L) and SR <= 0 (F_R) of the same expression
+    const float sl = fminf(SL, 0.0f), sr = fmaxf(SR, 0.0f);
+    const float inv = vrcp(sr - sl);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        F[f] = (sr * FL[f] - sl * FR[f] + sl * sr * (UR[f] - UL[f])) * inv;
+}
+
+// Face flux along physical axis AX from the six cells q0..q5 around the face
+// (the face sits between q2 and q3).
+template <int AX, typename T>
+__device__ __forceinline__ void weno_face(const T q[6][NF], T gamma, T gx, T F[NF]) {
+    using R = Rot<AX>;
+    T qL[NF], qR[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        qL[f] = weno5z(q[0][f], q[1][f], q[2][f], q[3][f], q[4][f]);
+        qR[f] = weno5z(q[5][f], q[4][f], q[3][f], q[2][f], q[1][f]);
+    }
+    const T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
+    const T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
+    T Fn[NF];
+    hll_normal(WL, WR, gamma, gx, Fn);
+    F[0] = Fn[0];
+    F[R::n] = Fn[1];
+    F[R::t1] = Fn[2];
+    F[R::t2] = Fn[3];
+    F[4] = Fn[4];
+}
+
+// Boundary map with three ghost layers: m in [-3, n+2] -> interior index
+// (flip for a reflecting wall); indices beyond them (ragged tiles) clamp to a
+// valid cell whose value feeds no used face.
+__device__ __forceinline__ int bc_map3(int m, int n, int lo, int hi, bool& flip) {
+    flip = false;
+    if (m >= 0 && m < n) return m;
+    if (m < -WENO_G || m > n + WENO_G - 1) return m < 0 ? 0 : n - 1;
+    const int bc = m < 0 ? lo : hi;
+    if (bc == 0) {
+        const int r = m % n;
+        return r < 0 ? r + n : r;
+    }
+    if (bc == 1) return m < 0 ? 0 : n - 1;
+    flip = true;
+    const int s = m < 0 ? -1 - m : 2 * n - 1 - m;
+    return s < 0 ? 0 : (s >= n ? n - 1 : s);
+}
+
+template <typename T, int DIM, int PX, int PY>
+__device__ __forceinline__ void load_prim3(const StageArgs<T>& A, int gx, int gy, int gz,
+                                           T W[NF], bool& bad) {
+    bool fx, fy = false, fz = false;
+    const int sx = bc_map3(gx, A.n[0], A.bc_lo[0], A.bc_hi[0], fx);
+    int sy = 0, sz = 0;
+    if (DIM >= 2) sy = bc_map3(gy, A.n[1], A.bc_lo[1], A.bc_hi[1], fy);
+    if (DIM >= 3) sz = bc_map3(gz, A.n[2], A.bc_lo[2], A.bc_hi[2], fz);
+    const long long c = ((long long)sz * A.n[1] + sy) * A.n[0] + sx;
+    T U[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) U[f] = __ldg(A.Uc + f * A.N + c);
+    if (fx) U[1 + PX] = -U[1 + PX];
+    if (DIM >= 2 && fy) U[1 + PY] = -U[1 + PY];
+    if (DIM >= 3 && fz) U[3] = -U[3];
+    cons_to_prim(U, A.gm1, W);
+    bad |= nonphys(W);
+}
+
+template <typename T, int TX, int TY, int DIM>
+struct WenoSmem {
+    static constexpr int HX = TX + 2 * WENO_G;
+    static constexpr int HY = DIM >= 2 ? TY + 2 * WENO_G : 1;
+    static constexpr int NP = NF * HX * HY;
+    static constexpr int NFX = NF * TY * (TX + 1);
+    static constexpr int NFY = DIM >= 2 ? NF * (TY + 1) * TX : 0;
+    static constexpr size_t bytes = sizeof(T) * (NP + NFX + NFY);
+};
+
+template <typename T, int TX, int TY, int DIM, int PX, int PY>
+__global__ void __launch_bounds__(TX * TY)
+weno_stage_kernel(const StageArgs<T> A) {
+    using S = WenoSmem<T, TX, TY, DIM>;
+    constexpr int NT = TX * TY;
+    constexpr int HX = S::HX, HY = S::HY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red_tot[NT / 32][NF];
+    __shared__ unsigned long long red_rate[NT / 32];
+    T* Ps = reinterpret_cast<T*>(smem_raw);          // [NF][HY][HX]
+    T* Fx = Ps + S::NP;                               // [NF][TY][TX+1]
+    T* Fy = Fx + S::NFX;                              // [NF][TY+1][TX]
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX;
+    const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
+    const int z0 = DIM == 3 ? blockIdx.z * A.zchunk : 0;
+    const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.n[2]) : 1;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own = x < A.n[0] && (DIM < 2 || y < A.n[1]);
+    const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
+    const T gamma = A.gamma;
+    // the HLL energy closure: 1/(gamma-1) in FP32, gamma-1 (a divisor) in FP64
+    const T gx = sizeof(T) == 4 ? A.igm1 : A.gm1;
+    bool bad = false;
+    T rate_max = T(0);
+    T tot[NF] = {T(0), T(0), T(0), T(0), T(0)};
+
+    // z stencil of this thread's column: primitives of the last six planes,
+    // the previous z-face flux and the x/y flux differences of three planes
+    T w[6][NF], Fzp[NF], Da[NF], Db[NF], Dc[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        Fzp[f] = Da[f] = Db[f] = Dc[f] = T(0);
+#pragma unroll
+        for (int s = 0; s < 6; ++s) w[s][f] = T(0);
+    }
+
+    const int jbeg = DIM == 3 ? z0 - WENO_G : 0;
+    const int jend = DIM == 3 ? z1 + WENO_G : 1;
+    for (int j = jbeg; j < jend; ++j) {
+        const bool xy = DIM < 3 || (j >= z0 && j < z1);
+        T qj[NF], Dj[NF];
+        if (xy) {
+            __syncthreads();                       // previous plane fully consumed
+            for (int e = tid; e < HX * HY; e += NT) {
+                const int hx = e % HX, hy = e / HX;
+                T W[NF];
+                load_prim3<T, DIM, PX, PY>(A, x0 - WENO_G + hx, y0 - (DIM >= 2 ? WENO_G : 0) + hy,
+                                           j, W, bad);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) Ps[(f * HY + hy) * HX + hx] = W[f];
+            }
+            __syncthreads();
+            // x faces: (TX+1) per row; face fx sits left of tile cell fx
+            for (int e = tid; e < (TX + 1) * TY; e += NT) {
+                const int fx = e % (TX + 1), row = e / (TX + 1);
+                const int hy = DIM >= 2 ? row + WENO_G : 0;
+                T q[6][NF];
+#pragma unroll
+                for (int s = 0; s < 6; ++s)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HY + hy) * HX + fx + s];
+                T F[NF];
+                weno_face<PX>(q, gamma, gx, F);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + fx] = F[f];
+            }
+            if (DIM >= 2) {
+                for (int e = tid; e < TX * (TY + 1); e += NT) {
+                    const int col = e % TX, fy = e / TX;
+                    T q[6][NF];
+#pragma unroll
+                    for (int s = 0; s < 6; ++s)
+#pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            q[s][f] = Ps[(f * HY + fy + s) * HX + col + WENO_G];
+                    T F[NF];
+                    weno_face<PY>(q, gamma, gx, F);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + fy) * TX + col] = F[f];
+                }
+            }
+            __syncthreads();
+            const int hyc = DIM >= 2 ? ty + WENO_G : 0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                qj[f] = Ps[(f * HY + hyc) * HX + tx + WENO_G];
+                const T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fx[(f * TY + ty) * (TX + 1) + tx];
+                Dj[f] = sub_over_dx(T(0), a, A.dxk[0]);
+                if (DIM >= 2) {
+                    const T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fy[(f * (TY + 1) + ty) * TX + tx];
+                    Dj[f] = sub_over_dx(Dj[f], b, A.dxk[1]);
+                }
+            }
+        } else {
+            // warm-up / look-ahead plane: only this column's primitives
+            load_prim3<T, DIM, PX, PY>(A, min(x, A.n[0] - 1), min(y, A.n[1] - 1), j, qj, bad);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Dj[f] = T(0);
+        }
+
+        int k;                 // cell completed in this iteration (-1: none)
+        T L[NF];
+        if (DIM == 3) {
+            const int cnt = j - jbeg;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+#pragma unroll
+                for (int s = 0; s < 5; ++s) w[s][f] = w[s + 1][f];
+                w[5][f] = qj[f];
+            }
+            T Fz[NF];
+            if (cnt >= 5) weno_face<2>(w, gamma, gx, Fz);    // face between j-3 and j-2
+            k = cnt >= 6 ? j - WENO_G : -1;
+            if (k >= 0) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) L[f] = sub_over_dx(Da[f], Fz[f] - Fzp[f], A.dxk[2]);
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (cnt >= 5) Fzp[f] = Fz[f];
+                Da[f] = Db[f];
+                Db[f] = Dc[f];
+                Dc[f] = Dj[f];
+            }
+        } else {
+            k = 0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) L[f] = Dj[f];
+        }
+
+        if (k >= 0 && own) {
+            const long long c = ((long long)k * A.n[1] + y) * A.n[0] + x;
+            T Uo[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T uc = A.Uc[f * A.N + c];
+                if (A.stage == 1) {
+                    Uo[f] = madd(dt, L[f], uc);
+                } else {
+                    const T u0 = A.U0[f * A.N + c];
+                    Uo[f] = madd(T(0.5), u0, T(0.5) * madd(dt, L[f], uc));
+                }
+                A.Uo[f * A.N + c] = Uo[f];
+            }
+            if (A.rate_slot) {
+                T W[NF];
+                cons_to_prim(Uo, A.gm1, W);
+                const T r = cell_rate(W, gamma, A.act, A.rdx);
+                rate_max = (r > rate_max || r != r) ? r : rate_max;
+            }
+            if (A.tot_partial) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) tot[f] += Uo[f];
+            }
+        }
+    }
+
+    // ---- epilogue: block reductions ----
+    const int lane = tid & 31, warp = tid >> 5;
+    if (A.rate_slot) {
+        unsigned long long b = rate_bits(rate_max);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+            b = v > b ? v : b;
+        }
+        if (lane == 0) red_rate[warp] = b;
+    }
+    if (A.tot_partial) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            double v = (double)tot[f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red_tot[warp][f] = v;
+        }
+    }
+    const int any_bad = __syncthreads_or(bad);
+    if (tid == 0) {
+        if (any_bad) atomicOr(A.status, 1);
+        if (A.rate_slot) {
+            unsigned long long b = 0;
+            for (int wi = 0; wi < NT / 32; ++wi) b = red_rate[wi] > b ? red_rate[wi] : b;
+            atomicMax(A.rate_slot, b);
+        }
+        if (A.tot_partial) {
+            const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            for (int f = 0; f < NF; ++f) {
+                double s = 0.0;
+                for (int wi = 0; wi < NT / 32; ++wi) s += red_tot[wi][f];
+                A.tot_partial[blk * NF + f] = s;
+            }
+        }
+    }
+}
+
+}  // namespace hh

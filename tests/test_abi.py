@@ -54,6 +54,13 @@ def test_host_only_calls_without_gpu(libpath):
     assert rc == 0 and info[3] == info[0] * info[1]
     assert hh.hard_hydro_set(h, hh.HARD_F64, 2.0, 1.0, 1.0, None) == hh.HARD_OK
     assert hh.hard_hydro_create(4, 4, 4, 0.5, 0) is None
+    # the second scheme needs three cells along every active axis
+    assert hh.hard_hydro_set_scheme(h, hh.HARD_SCHEME_WENO5Z_HLL) == hh.HARD_OK
+    assert hh.hard_hydro_set_scheme(h, 7) == hh.HARD_EINVAL
+    assert hh.hard_hydro_set_scheme(h, hh.HARD_SCHEME_PLM_HLLC) == hh.HARD_OK
+    h2 = hh.hard_hydro_create(16, 2, 1, 1.4, 0)
+    assert hh.hard_hydro_set_scheme(h2, hh.HARD_SCHEME_WENO5Z_HLL) == hh.HARD_EINVAL
+    hh.hard_hydro_destroy(h2)
     hh.hard_hydro_destroy(h)
 
 
