@@ -263,3 +263,68 @@ def batch_problem_U(spec: BatchSpec, q: int):
     rho, u, v, p = (arr[sel, c] for c in range(4))
     U = prim_to_cons((rho, u, v, np.zeros_like(rho), p), gamma)
     return U.reshape(5, 1, ny, nx)
+
+
+# --------------------------------------------------------------------------
+# Radiative heating / cooling (Sec. 3.2), CGS units
+# --------------------------------------------------------------------------
+
+C_LIGHT = 2.99792458e10              # cm / s
+K_BOLTZMANN = 1.380649e-16           # erg / K
+M_U = 1.66053906660e-24              # g (atomic mass unit)
+SIGMA_SB = 5.670374419e-5            # erg / (cm^2 s K^4)
+A_RAD = 4.0 * SIGMA_SB / C_LIGHT     # radiation constant a = 4 sigma / c
+
+
+@dataclass
+class HeatingCooling:
+    """Sec. 3.2: rho = 1e-7 g/cm^3, mu = 0.6, kappa = 0.4 cm^2/g, a uniform
+    radiation field at T_r = 3.4e6 K and a fluid at T_f = 11 K (heating) or
+    1.1e9 K (cooling).  gamma = 5/3 (monatomic ideal gas; the paper does not
+    print it)."""
+    T_fluid: float
+    rho: float = 1e-7
+    mu: float = 0.6
+    kappa: float = 0.4
+    T_rad: float = 3.4e6
+    gamma: float = 5.0 / 3.0
+
+    @property
+    def cv(self):
+        """Specific heat per unit mass, k_B / ((gamma - 1) mu m_u)."""
+        return K_BOLTZMANN / ((self.gamma - 1.0) * self.mu * M_U)
+
+    @property
+    def params(self):
+        """(c, kappa, a, c_v) of the exchange."""
+        return (C_LIGHT, self.kappa, A_RAD, self.cv)
+
+    def state(self, shape=(1, 1, 1), seed=None, spread=0.0):
+        """Fluid at rest (U, 5 x shape) and radiation energy density Er (shape).
+        With a seed, rho, T_f and T_r vary cell by cell by a log-uniform
+        factor in [1/(1+spread), 1+spread] and the fluid moves at up to
+        1e5 cm/s."""
+        shape = tuple(shape)
+        rho = np.full(shape, self.rho)
+        Tf = np.full(shape, self.T_fluid)
+        Tr = np.full(shape, self.T_rad)
+        vel = np.zeros((3,) + shape)
+        if seed is not None:
+            g = _rng(seed)
+            s = math.log1p(spread)
+            rho = rho * np.exp(g.uniform(-s, s, shape))
+            Tf = Tf * np.exp(g.uniform(-s, s, shape))
+            Tr = Tr * np.exp(g.uniform(-s, s, shape))
+            vel = g.uniform(-1e5, 1e5, (3,) + shape)
+        e = rho * self.cv * Tf
+        U = np.stack([rho, rho * vel[0], rho * vel[1], rho * vel[2],
+                      e + 0.5 * rho * np.sum(vel * vel, axis=0)])
+        return U, A_RAD * Tr ** 4
+
+
+def heating():
+    return HeatingCooling(T_fluid=11.0)
+
+
+def cooling():
+    return HeatingCooling(T_fluid=1.1e9)

@@ -56,6 +56,8 @@ def _declare(lib):
     lib.orc_hll.argtypes = [_D, _D, ctypes.c_double, _D]
     lib.orc_weno5z.restype = ctypes.c_double
     lib.orc_weno5z.argtypes = [_D]
+    lib.orc_rad_exchange.restype = ctypes.c_int
+    lib.orc_rad_exchange.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
     grid = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I, ctypes.c_double]
     sgrid = [ctypes.c_int] + grid
     lib.orc_rhs_s.restype = ctypes.c_int
@@ -235,6 +237,20 @@ def weno5z(v, lib=None):
     if v.shape != (5,):
         raise ValueError("weno5z takes five cell averages")
     return float((lib or load()).orc_weno5z(_dp(v)))
+
+
+def rad_exchange(U, Er, dt, c, kappa, a_rad, cv, lib=None):
+    """One backward-Euler step of the radiative heating / cooling exchange on
+    the conserved state U (5, ...) and the radiation energy density Er (...).
+    Returns (U', Er', largest Newton step count)."""
+    U = _c64(U).copy()
+    Er = _c64(Er).copy()
+    n = Er.size
+    if U.shape[0] != 5 or U[0].size != n:
+        raise ValueError("U must be (5, ...) with Er of the cell shape")
+    prm = np.array([c, kappa, a_rad, cv], dtype=np.float64)
+    it = (lib or load()).orc_rad_exchange(int(n), _dp(prm), float(dt), _dp(U), _dp(Er))
+    return U, Er, int(it)
 
 
 def hll(WL, WR, gamma, lib=None):

@@ -27,6 +27,8 @@
  *     (Sec. 3.1 and Sec. 3.5 use a CFL-limited step but print no formula).
  *   - Exact Riemann solver for the 1D ideal-gas Euler equations (Toro ch. 4),
  *     used to build the reference solution of the L1 metric, Eq. "l1_error".
+ *   - Radiative heating / cooling, Eq. "heating-cooling": a pointwise
+ *     backward-Euler exchange of fluid and radiation energy (orc_rad_exchange).
  *   - Second scheme (scheme = 1), the paper's own choice of Sec. 2.2.2:
  *     WENO5-Z face states of every primitive (Borges, Carmona, Costa, Don
  *     2008) and the HLL flux (Harten, Lax, van Leer 1983) with the same
@@ -596,6 +598,64 @@ int orc_get_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Radiative heating / cooling (the q-dot source, Sec. 2.2.1 and Sec. 3.2).   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The heating rate of Eq. "heating-cooling", qdot = c kappa rho (E - a T^4),
+ * adds to the fluid energy and takes from the radiation energy density E
+ * (the sources of Eq. "conservative form" with no radiation flux and no
+ * fluid velocity coupling), so e + E is conserved pointwise.  The fluid
+ * temperature is T = e / (rho c_v), c_v the specific heat per mass (for the
+ * ideal gas c_v = k_B / ((gamma - 1) mu m_u)).
+ *
+ * One backward-Euler step of length dt:
+ *   e' = e + dt k (E_tot - e' - a (e' / (rho c_v))^4),   k = c kappa rho,
+ *   E' = E_tot - e',   E_tot = e + E,
+ * solved for e' by Newton's method on
+ *   f(x) = x - e - dt k (E_tot - x - a (x / (rho c_v))^4),
+ * which is increasing and convex for x > 0, so Newton started right of the
+ * root decreases monotonically onto it.  The start
+ *   x0 = min(e + dt k max(E_tot - e - a T(e)^4, 0), E_tot)
+ * has f(x0) >= 0 (the root lies in (0, E_tot): E' = E_tot - e' >= 0).  Iteration stops when the step is at most 1e-15 x (at most
+ * 200 steps).  The fluid's kinetic energy is left as it is: the update
+ * changes U[4] by e' - e and E by e - e'.
+ * prm = {c, kappa, a, c_v}.  Returns the largest Newton step count.
+ */
+int orc_rad_exchange(int ncell, const double* prm, double dt, double* U, double* Er) {
+    const double c = prm[0], kappa = prm[1], arad = prm[2], cv = prm[3];
+    int worst = 0;
+    size_t N = (size_t)ncell;
+    for (size_t q = 0; q < N; ++q) {
+        double rho = U[q];
+        double m1 = U[N + q], m2 = U[2 * N + q], m3 = U[3 * N + q];
+        double kin = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / rho;
+        double e = U[4 * N + q] - kin;
+        double Etot = e + Er[q];
+        double k = c * kappa * rho;
+        double rcv = rho * cv;
+        double Te = e / rcv;
+        double R0 = Etot - e - arad * (Te * Te) * (Te * Te);
+        double x = e + dt * k * (R0 > 0.0 ? R0 : 0.0);
+        if (x > Etot) x = Etot;                    /* the root lies below E_tot */
+        int it = 0;
+        for (; it < 200; ++it) {
+            double T = x / rcv;
+            double aT4 = arad * (T * T) * (T * T);
+            double f = x - e - dt * k * (Etot - x - aT4);
+            double df = 1.0 + dt * k * (1.0 + 4.0 * aT4 / x);
+            double dx = f / df;
+            x = x - dx;
+            if (fabs(dx) <= 1e-15 * x) { ++it; break; }
+        }
+        if (it > worst) worst = it;
+        U[4 * N + q] = x + kin;
+        Er[q] = Er[q] + (e - x);
+    }
+    return worst;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -14,7 +14,7 @@ import oracle
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = [os.path.join(ROOT, "tests", f) for f in
         ("test_oracle_hllc.py", "test_oracle_riemann.py", "test_oracle_scheme.py",
-         "test_oracle_weno.py")]
+         "test_oracle_weno.py", "test_oracle_rad.py")]
 
 # (name, original text, planted text)
 MUTANTS = [
@@ -102,6 +102,14 @@ MUTANTS = [
      "F[f] = (SR * FL[f] - SL * FR[f] - SL * SR * (UR[f] - UL[f])) / (SR - SL);"),
     ("HLL Davis bound", "double SL = fmin(WL[1] - cL, WR[1] - cR);",
      "double SL = fmin(WL[1] - cL, WR[1] + cR);"),
+    # radiative heating / cooling exchange
+    ("exchange source sign", "double f = x - e - dt * k * (Etot - x - aT4);",
+     "double f = x - e + dt * k * (Etot - x - aT4);"),
+    ("exchange T^4 as T^3", "double aT4 = arad * (T * T) * (T * T);",
+     "double aT4 = arad * (T * T) * T;"),
+    ("exchange rate without density", "double k = c * kappa * rho;", "double k = c * kappa;"),
+    ("radiation energy update sign", "Er[q] = Er[q] + (e - x);", "Er[q] = Er[q] - (e - x);"),
+    ("exchange ignores kinetic energy", "U[4 * N + q] = x + kin;", "U[4 * N + q] = x;"),
 ]
 
 
