@@ -410,6 +410,72 @@ def main():
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": stage_ms}
     del U1, U2
 
+    # ---------------- second scheme: WENO5-Z + HLL, FP32 ----------------
+    mw = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32,
+                      scheme=hh.HARD_SCHEME_WENO5Z_HLL)
+    Uw = torch.tensor(U64, dtype=torch.float32, device=dev)
+    kw = max(2, args.steps // 4)
+    advance(mw, Uw, 3, tot_log)
+    barrier()
+    e0.record(stream)
+    advance(mw, Uw, kw, tot_log)
+    e1.record(stream)
+    barrier()
+    msw = rank_max(e0.elapsed_time(e1))
+    W1, W2 = torch.empty_like(Uw), torch.empty_like(Uw)
+    dtw = mw.cfl_dt(Uw, CFL)
+    for _ in range(2):
+        mw.stage(1, None, Uw, dtw, out=W1)
+        mw.stage(2, Uw, W1, dtw, out=W2)
+    barrier()
+    e0.record(stream)
+    for _ in range(10):
+        mw.stage(1, None, Uw, dtw, out=W1)
+        mw.stage(2, Uw, W1, dtw, out=W2)
+    e1.record(stream)
+    barrier()
+    wstage_ms = e0.elapsed_time(e1) / 20
+    w_achieved = alg_bytes / (wstage_ms * 1e-3) / 1e9
+    weno = {"workload": WORKLOAD.replace("CFL 0.4", "CFL 0.4, WENO5-Z + HLL"),
+            "value": whole_job_value(world, cells, 2 * kw, msw), "unit": UNIT, "steps": kw,
+            "ms_per_step": msw / kw, "status": hh.hard_hydro_strerror(mw.get_error()),
+            "roofline": {"bound": "hbm", "achieved": w_achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": w_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "weno_stage_kernel<float,32,8,3> z-chunk 32 "
+                                   "(mean of stage 1 and stage 2)",
+                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": wstage_ms}}
+    del mw, Uw, W1, W2
+
+    # ---------------- radiative heating / cooling exchange, FP32 ----------------
+    pbr = H.cooling()
+    Ur, Err = pbr.state(shape, seed=rank, spread=0.5)
+    mr = hh.HardHydro(shape, pbr.gamma, hh.HARD_BC_PERIODIC, dtype=torch.float32)
+    Urd = torch.tensor(Ur, dtype=torch.float32, device=dev)
+    Erd = torch.tensor(Err, dtype=torch.float32, device=dev)
+    del Ur, Err
+    dt_rad = 1e-12                                  # every launch solves a fresh implicit step
+    for _ in range(3):
+        mr.rad_exchange(Urd, Erd, dt_rad, *pbr.params)
+    barrier()
+    e0.record(stream)
+    for _ in range(20):
+        mr.rad_exchange(Urd, Erd, dt_rad, *pbr.params)
+    e1.record(stream)
+    barrier()
+    rad_ms = e0.elapsed_time(e1) / 20
+    rad_bytes = 8 * 4 * cells                       # reads rho, 3 momenta, E_total, E; writes 2
+    rad_achieved = rad_bytes / (rad_ms * 1e-3) / 1e9
+    rad = {"workload": "256^3 radiative heating/cooling exchange (Sec. 3.2 cooling case, "
+                       "seeded +-50% spread in rho, T_f, T_r; moving fluid), FP32, dt 1e-12 s, "
+                       "state 403 MB > L2",
+           "value": whole_job_value(world, cells, 1, rank_max(rad_ms)), "unit": UNIT,
+           "launch_ms": rad_ms, "status": hh.hard_hydro_strerror(mr.get_error()),
+           "roofline": {"bound": "hbm", "achieved": rad_achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": rad_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                        "kernel": "rad_exchange_kernel<float>",
+                        "algorithmic_bytes_per_launch": rad_bytes}}
+    del mr, Urd, Erd
+
     # ---------------- FP64 plain ----------------
     m64 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float64,
                        kernel=hh.HARD_KERNEL_PLAIN)
@@ -526,6 +592,8 @@ def main():
                    "tile": {"chosen": tuned["info"], "ms_per_stage": tuned["ms"]},
                    "step": "CFL rate + stage 1 + stage 2 + FP64 totals"},
         "roofline": roofline,
+        "weno5z_hll": weno,
+        "rad_exchange": rad,
         "batched": batched,
         "adjoint": adjoint,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": k64,

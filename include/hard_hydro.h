@@ -196,6 +196,22 @@ void hard_batch_destroy(hard_batch_t b);
 int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U_out, double dt,
                             void* stream);
 
+/* Radiative heating / cooling (Eq. "heating-cooling"): one backward-Euler
+ * step of length dt > 0 of the pointwise exchange
+ *   de/dt = c kappa rho (E - a T^4),  dE/dt = -(same),  T = e / (rho c_v),
+ * between the fluid's internal energy density e = E_total - rho |v|^2 / 2 and
+ * the radiation energy density E (e + E is conserved; rho and the momenta are
+ * not touched).  U is the handle's state [5][nz][ny][nx]; Er the radiation
+ * energy density [nz][ny][nx]; both device buffers of the handle's element
+ * type, 16-byte aligned, caller-owned, updated in place.  prm = {c, kappa, a,
+ * c_v} (host array, all > 0, consistent units).  Each cell solves its implicit
+ * update by Newton's method to 1e-15 (FP64) / 4e-7 (FP32) relative.  A cell
+ * with rho <= 0, e <= 0 or E < 0 (or no convergence) is left unchanged and
+ * raises the non-physical flag, read by hard_hydro_get_error.  Asynchronous
+ * on `stream`; allocates nothing beyond the handle's status slot. */
+int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const double prm[4],
+                            void* stream);
+
 /* Adjoint of one full step with dt held constant (a vector-Jacobian product):
  * given the cotangent gU_out of U^{n+1} = step(U_in), writes
  * gU_in = (dU^{n+1}/dU_in)^T gU_out and adds (dU^{n+1}/dgamma)^T gU_out to the

@@ -619,8 +619,12 @@ int orc_get_threads(void) {
  *   f(x) = x - e - dt k (E_tot - x - a (x / (rho c_v))^4),
  * which is increasing and convex for x > 0, so Newton started right of the
  * root decreases monotonically onto it.  The start
- *   x0 = min(e + dt k max(E_tot - e - a T(e)^4, 0), E_tot)
- * has f(x0) >= 0 (the root lies in (0, E_tot): E' = E_tot - e' >= 0).  Iteration stops when the step is at most 1e-15 x (at most
+ *   x0 = min(e + dt k max(E_tot - e - a T(e)^4, 0), E_tot, x_q),
+ *   x_q = rho c_v ((e + dt k E_tot) / (dt k a))^(1/4),
+ * has f(x0) >= 0: each of the three has (the root lies in (0, E_tot), since
+ * E' = E_tot - e' >= 0, and f(x) >= (1 + dt k) x + dt k a T(x)^4 - e - dt k E_tot,
+ * which is >= 0 at x_q).  x_q is the close start when the T^4 term dominates
+ * (stiff cooling).  Iteration stops when the step is at most 1e-15 x (at most
  * 200 steps).  The fluid's kinetic energy is left as it is: the update
  * changes U[4] by e' - e and E by e - e'.
  * prm = {c, kappa, a, c_v}.  Returns the largest Newton step count.
@@ -641,6 +645,8 @@ int orc_rad_exchange(int ncell, const double* prm, double dt, double* U, double*
         double R0 = Etot - e - arad * (Te * Te) * (Te * Te);
         double x = e + dt * k * (R0 > 0.0 ? R0 : 0.0);
         if (x > Etot) x = Etot;                    /* the root lies below E_tot */
+        double xq = rcv * sqrt(sqrt((e + dt * k * Etot) / (dt * k * arad)));
+        if (xq < x) x = xq;
         int it = 0;
         for (; it < 200; ++it) {
             double T = x / rcv;

@@ -44,6 +44,8 @@ def _declare(lib):
                                           ctypes.c_double, _ip]),
         "hard_hydro_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
         "hard_hydro_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "hard_hydro_rad_exchange": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double,
+                                                   ctypes.POINTER(ctypes.c_double), _vp]),
         "hard_hydro_tile_count": (ctypes.c_int, [_vp]),
         "hard_hydro_tile_info": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
         "hard_hydro_stage": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double,
@@ -108,6 +110,11 @@ def hard_hydro_set_kernel(h, kernel, tile):
 
 def hard_hydro_set_scheme(h, scheme):
     return lib().hard_hydro_set_scheme(h, int(scheme))
+
+
+def hard_hydro_rad_exchange(h, U, Er, dt, prm, stream):
+    arr = (ctypes.c_double * 4)(*[float(v) for v in prm])
+    return lib().hard_hydro_rad_exchange(h, U, Er, float(dt), arr, stream)
 
 
 def hard_hydro_tile_count(h):
@@ -255,6 +262,17 @@ class HardHydro:
 
     def set_scheme(self, scheme):
         check(hard_hydro_set_scheme(self.h, scheme), "hard_hydro_set_scheme")
+
+    def rad_exchange(self, U, Er, dt, c, kappa, a_rad, cv):
+        """In place on U (its E_total field) and Er: one backward-Euler step of
+        the radiative heating / cooling exchange."""
+        if not (Er.is_cuda and Er.is_contiguous() and Er.dtype == self.dtype
+                and tuple(Er.shape) == self.shape):
+            raise ValueError(f"Er must be a contiguous {self.dtype} CUDA tensor of shape {self.shape}")
+        check(hard_hydro_rad_exchange(self.h, self._check(U), Er.data_ptr(), dt,
+                                      (c, kappa, a_rad, cv), self._stream()),
+              "hard_hydro_rad_exchange")
+        return U, Er
 
     def tile_count(self):
         return hard_hydro_tile_count(self.h)

@@ -31,6 +31,7 @@ UNITS = {
     "stage_f64.cu": ["--fmad=false"],
     "weno_f32.cu": ["--fmad=false"],
     "weno_f64.cu": ["--fmad=false"],
+    "rad.cu": ["--fmad=false"],
     "hard_hydro.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],

@@ -8,6 +8,7 @@
 
 #include "hard_hydro.h"
 #include "launch.h"
+#include "rad_launch.h"
 #include "weno_launch.h"
 
 using hh::MeshDesc;
@@ -477,6 +478,19 @@ int hard_hydro_totals(hard_hydro_t h, const void* U, double out5[5], void* strea
         e = cudaMemcpyAsync(out5, tot_slot(h), 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return from_cuda(e);
     return read_status(h, s);
+}
+
+int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const double prm[4],
+                            void* stream) {
+    if (!h || !U || !Er || !prm || !aligned16(U) || !aligned16(Er)) return HARD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    for (int i = 0; i < 4; ++i)
+        if (!(prm[i] > 0.0) || !std::isfinite(prm[i])) return HARD_EINVAL;
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    return from_cuda(hh::launch_rad_exchange(h->mesh, h->dtype, U, Er, dt, prm, status_slot(h), s));
 }
 
 int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_out, void* gU_in,
