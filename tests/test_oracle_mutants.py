@@ -127,6 +127,46 @@ def _run_mutant(args):
     return name, r.returncode
 
 
+# mistakes planted in the flux-limited diffusion oracle (oracle/fld.py)
+FLD_MUTANTS = [
+    ("limiter denominator", "(2.0 + R) / (6.0 + 3.0 * R + R * R)",
+     "(2.0 + R) / (6.0 + 2.0 * R + R * R)"),
+    ("face coefficient from one side", "w = 0.5 * (D + Dn) * dt / (dxyz[d] * dxyz[d])",
+     "w = 0.5 * (D + D) * dt / (dxyz[d] * dxyz[d])"),
+    ("face weight not over dx^2", "w = 0.5 * (D + Dn) * dt / (dxyz[d] * dxyz[d])",
+     "w = 0.5 * (D + Dn) * dt / dxyz[d]"),
+    ("gradient without the factor 2", "/ (2.0 * dxyz[d])", "/ dxyz[d]"),
+    ("coefficient without rho", "return c * flux_limiter(R) / (kappa * rho)",
+     "return c * flux_limiter(R) / kappa"),
+    ("R without kappa", "R = np.sqrt(grad2) / (rho * kappa * E)", "R = np.sqrt(grad2) / (rho * E)"),
+    ("off-diagonal sign", "vals += [-w.ravel(), -w.ravel()]", "vals += [w.ravel(), w.ravel()]"),
+]
+
+
+def _run_fld_mutant(args):
+    idx, (name, old, new), tmp = args
+    src = open(os.path.join(ROOT, "oracle", "fld.py")).read()
+    assert old in src, f"mutation site of '{name}' not found"
+    path = os.path.join(tmp, f"fld_m{idx}.py")
+    with open(path, "w") as fh:
+        fh.write(src.replace(old, new, 1))
+    env = dict(os.environ, HARD_FLD_PATH=path)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_fld.py"),
+                        "-x", "-q", "-p", "no:cacheprovider"],
+                       env=env, capture_output=True, text=True, cwd=ROOT)
+    return name, r.returncode
+
+
+def test_every_planted_fld_mistake_is_caught(tmp_path):
+    if os.environ.get("HARD_FLD_PATH"):
+        pytest.skip("already running against a planted copy")
+    jobs = [(i, m, str(tmp_path)) for i, m in enumerate(FLD_MUTANTS)]
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(_run_fld_mutant, jobs))
+    survivors = [name for name, rc in results if rc == 0]
+    assert not survivors, f"pins did not catch: {survivors}"
+
+
 def test_every_planted_mistake_is_caught(tmp_path):
     if os.environ.get("HARD_ORACLE_LIB"):
         pytest.skip("already running against a planted copy")
