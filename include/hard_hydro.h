@@ -212,6 +212,28 @@ int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U_out, doubl
 int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const double prm[4],
                             void* stream);
 
+/* Flux-limited radiation diffusion (Sec. 2.2.1-2.2.2): one backward-Euler
+ * step of dE/dt = div(D grad E), D = c lambda(R) / (kappa rho) with the
+ * Levermore limiter lambda = (2 + R)/(6 + 3R + R^2), R = |grad E|/(rho kappa E),
+ * D frozen at the old E, on the handle's mesh (face coefficient: the mean of
+ * its two cells; periodic faces wrap, outflow and reflecting faces carry no
+ * flux).  The linear system is solved by geometric-multigrid V-cycles
+ * (red-black Gauss-Seidel, cell-centred coarsening of every even axis of
+ * length >= 4) until the 2-norm of the residual is at most rtol times that of
+ * the right-hand side, or max_cycles >= 1 cycles ran; rtol <= 0 runs exactly
+ * max_cycles cycles without synchronising.  U: the handle's state (its
+ * density field is read); Er: the radiation energy density [nz][ny][nx],
+ * updated in place.  Both device buffers of the handle's element type,
+ * 16-byte aligned, caller-owned.  c, kappa > 0 in consistent units.
+ * *cycles_out and *resid_out (may be NULL) receive the cycles run and the last
+ * relative residual (-1 when rtol <= 0).  The handle allocates its multigrid
+ * levels on first use (freed by hard_hydro_set of another element type and by
+ * hard_hydro_destroy).  With rtol > 0 the call synchronises `stream` once per
+ * cycle.  A mesh with no active axis returns HARD_EUNSUPPORTED. */
+int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, double c,
+                        double kappa, double rtol, int max_cycles, int* cycles_out,
+                        double* resid_out, void* stream);
+
 /* Adjoint of one full step with dt held constant (a vector-Jacobian product):
  * given the cotangent gU_out of U^{n+1} = step(U_in), writes
  * gU_in = (dU^{n+1}/dU_in)^T gU_out and adds (dU^{n+1}/dgamma)^T gU_out to the

@@ -46,6 +46,10 @@ def _declare(lib):
         "hard_hydro_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int]),
         "hard_hydro_rad_exchange": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double,
                                                    ctypes.POINTER(ctypes.c_double), _vp]),
+        "hard_hydro_fld_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_double), _vp]),
         "hard_hydro_tile_count": (ctypes.c_int, [_vp]),
         "hard_hydro_tile_info": (ctypes.c_int, [_vp, ctypes.c_int, _ip]),
         "hard_hydro_stage": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double,
@@ -110,6 +114,15 @@ def hard_hydro_set_kernel(h, kernel, tile):
 
 def hard_hydro_set_scheme(h, scheme):
     return lib().hard_hydro_set_scheme(h, int(scheme))
+
+
+def hard_hydro_fld_step(h, U, Er, dt, c, kappa, rtol, max_cycles, stream):
+    """Returns (rc, cycles, relative residual)."""
+    cyc = ctypes.c_int(0)
+    res = ctypes.c_double(-1.0)
+    rc = lib().hard_hydro_fld_step(h, U, Er, float(dt), float(c), float(kappa), float(rtol),
+                                   int(max_cycles), ctypes.byref(cyc), ctypes.byref(res), stream)
+    return rc, cyc.value, res.value
 
 
 def hard_hydro_rad_exchange(h, U, Er, dt, prm, stream):
@@ -262,6 +275,17 @@ class HardHydro:
 
     def set_scheme(self, scheme):
         check(hard_hydro_set_scheme(self.h, scheme), "hard_hydro_set_scheme")
+
+    def fld_step(self, U, Er, dt, c, kappa, rtol=1e-8, max_cycles=50):
+        """In place on Er: one implicit flux-limited diffusion step.  Returns
+        (cycles, relative residual)."""
+        if not (Er.is_cuda and Er.is_contiguous() and Er.dtype == self.dtype
+                and tuple(Er.shape) == self.shape):
+            raise ValueError(f"Er must be a contiguous {self.dtype} CUDA tensor of shape {self.shape}")
+        rc, cyc, res = hard_hydro_fld_step(self.h, self._check(U), Er.data_ptr(), dt, c, kappa,
+                                           rtol, max_cycles, self._stream())
+        check(rc, "hard_hydro_fld_step")
+        return cyc, res
 
     def rad_exchange(self, U, Er, dt, c, kappa, a_rad, cv):
         """In place on U (its E_total field) and Er: one backward-Euler step of

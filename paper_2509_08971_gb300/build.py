@@ -32,6 +32,7 @@ UNITS = {
     "weno_f32.cu": ["--fmad=false"],
     "weno_f64.cu": ["--fmad=false"],
     "rad.cu": ["--fmad=false"],
+    "fld.cu": [],
     "hard_hydro.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],

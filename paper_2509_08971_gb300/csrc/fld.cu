@@ -1,0 +1,394 @@
+// Flux-limited radiation diffusion (Sec. 2.2.1-2.2.2): one backward-Euler
+// step of dE/dt = div(D grad E) with D = c lambda(R) / (kappa rho) frozen at
+// the old state,
+//   lambda = (2 + R) / (6 + 3R + R^2),  R = |grad E| / (rho kappa E),
+// on the cell-centred mesh: the linear system (Eq. "linear_equation")
+//   E' (1 + sum_f w_f) - sum_f w_f E'_nb = E,   w_f = dt (D_i + D_nb) / (2 dx^2),
+// over the faces f of each cell (periodic faces wrap; outflow and reflecting
+// faces carry no flux), solved by geometric multigrid V-cycles (the paper's
+// GMG, Sec. 2.2.2):
+//   * levels: every active axis of even length >= 4 halves (cell-centred
+//     coarsening, 2 children per coarsened axis), D of a coarse cell is the
+//     mean of its children, dx doubles on coarsened axes (re-discretised
+//     coarse operators);
+//   * smoother: red-black Gauss-Seidel, two sweeps before and after the
+//     coarse correction, 50 on the coarsest level;
+//   * restriction: the mean of the children's residuals; prolongation:
+//     the coarse correction added to every child (piecewise constant).
+// grad E of R: central differences, the edge cell repeated at a non-periodic
+// boundary.  Everything is bandwidth-bound stencil work over the levels.
+#include <cmath>
+#include <new>
+
+#include "fld_launch.h"
+#include "hard_hydro.h"
+
+namespace hh {
+
+constexpr int FLD_MAX_LEVELS = 16;
+constexpr int FLD_PRE = 2, FLD_POST = 2, FLD_COARSE = 50;
+
+struct FldLevel {
+    int n[3];
+    double dx[3];
+    long long N;
+    bool coarsened[3];       // this level's axes halved into the next level
+    void* x;                 // solution / correction (level 0: the caller's Er)
+    void* b;                 // right-hand side
+    void* r;                 // residual
+    void* D;                 // cell coefficient
+};
+
+struct FldHierarchy {
+    int dtype;
+    int nl;
+    int n0[3];
+    int bc_lo[3], bc_hi[3];
+    FldLevel L[FLD_MAX_LEVELS];
+    double* norms;           // device: sum r^2, sum b^2
+};
+
+namespace {
+
+template <typename T>
+struct LvlArgs {
+    T* x;
+    const T* b;
+    T* r;
+    const T* D;
+    int n[3];
+    T idx2[3];               // 1 / dx^2 per axis (0: inactive)
+    bool per[3];
+    long long N;
+    T dt;
+};
+
+__device__ __forceinline__ void cell_ijk(long long q, const int n[3], int& i, int& j, int& k) {
+    i = (int)(q % n[0]);
+    const long long t = q / n[0];
+    j = (int)(t % n[1]);
+    k = (int)(t / n[1]);
+}
+
+// neighbour index along one axis (-1: no face there)
+__device__ __forceinline__ int nb_index(int i, int n, int step, bool per) {
+    const int m = i + step;
+    if (m >= 0 && m < n) return m;
+    return per ? (m + n) % n : -1;
+}
+
+// the cell's stencil: diagonal 1 + sum w and sum w x_nb
+template <typename T>
+__device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k, long long q,
+                                        T& diag, T& off) {
+    const int c[3] = {i, j, k};
+    const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+    const T Dc = a.D[q];
+    diag = T(1);
+    off = T(0);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (a.n[ax] <= 1) continue;
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            const int m = nb_index(c[ax], a.n[ax], s, a.per[ax]);
+            if (m < 0) continue;
+            const long long qn = q + (long long)(m - c[ax]) * stride[ax];
+            const T w = a.dt * (T(0.5) * (Dc + a.D[qn])) * a.idx2[ax];
+            diag += w;
+            off += w * a.x[qn];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) smooth_kernel(const LvlArgs<T> a, int color) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.N;
+         q += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_ijk(q, a.n, i, j, k);
+        if (((i + j + k) & 1) != color) continue;
+        T diag, off;
+        stencil(a, i, j, k, q, diag, off);
+        a.x[q] = (a.b[q] + off) / diag;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) residual_kernel(const LvlArgs<T> a, double* norms) {
+    double rr = 0.0, bb = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.N;
+         q += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_ijk(q, a.n, i, j, k);
+        T diag, off;
+        stencil(a, i, j, k, q, diag, off);
+        const T r = a.b[q] - (diag * a.x[q] - off);
+        a.r[q] = r;
+        rr += (double)r * (double)r;
+        bb += (double)a.b[q] * (double)a.b[q];
+    }
+    if (norms) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rr += __shfl_xor_sync(0xffffffffu, rr, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(norms, rr);
+            atomicAdd(norms + 1, bb);
+        }
+    }
+}
+
+// coarse[I] = mean of the children fine[...] (restriction of r, and of D)
+template <typename T>
+__global__ void __launch_bounds__(256) restrict_kernel(const T* fine, T* coarse, int nf0, int nf1,
+                                                       int nc0, int nc1, int nc2, int h0, int h1,
+                                                       int h2, long long Nc) {
+    const T inv = T(1) / T(h0 * h1 * h2);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Nc;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(q % nc0);
+        const long long t = q / nc0;
+        const int J = (int)(t % nc1), K = (int)(t / nc1);
+        T s = T(0);
+        for (int c = 0; c < h2; ++c)
+            for (int b = 0; b < h1; ++b)
+                for (int a = 0; a < h0; ++a)
+                    s += fine[((long long)(K * h2 + c) * nf1 + (J * h1 + b)) * nf0 + (I * h0 + a)];
+        coarse[q] = s * inv;
+        (void)nc2;
+    }
+}
+
+// fine[i] += coarse[parent(i)]
+template <typename T>
+__global__ void __launch_bounds__(256) prolong_kernel(T* fine, const T* coarse, int nf0, int nf1,
+                                                      int nc0, int nc1, int h0, int h1, int h2,
+                                                      long long Nf) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Nf;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % nf0);
+        const long long t = q / nf0;
+        const int j = (int)(t % nf1), k = (int)(t / nf1);
+        fine[q] += coarse[((long long)(k / h2) * nc1 + j / h1) * nc0 + i / h0];
+    }
+}
+
+// D = c lambda(R) / (kappa rho), R = |grad E| / (rho kappa E), on level 0
+template <typename T>
+__global__ void __launch_bounds__(256) coeff_kernel(const T* U, const T* E, T* D, LvlArgs<T> a,
+                                                    T c, T kappa, T dx0, T dx1, T dx2) {
+    const T dxa[3] = {dx0, dx1, dx2};
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.N;
+         q += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_ijk(q, a.n, i, j, k);
+        const int cc[3] = {i, j, k};
+        const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+        T grad2 = T(0);
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            if (a.n[ax] <= 1) continue;
+            int up = cc[ax] + 1, dn = cc[ax] - 1;
+            if (a.per[ax]) {
+                up = (up + a.n[ax]) % a.n[ax];
+                dn = (dn + a.n[ax]) % a.n[ax];
+            } else {
+                up = up > a.n[ax] - 1 ? a.n[ax] - 1 : up;
+                dn = dn < 0 ? 0 : dn;
+            }
+            const T g = (E[q + (long long)(up - cc[ax]) * stride[ax]] -
+                         E[q + (long long)(dn - cc[ax]) * stride[ax]]) / (T(2) * dxa[ax]);
+            grad2 += g * g;
+        }
+        const T rho = U[q];
+        const T R = sqrt(grad2) / (rho * kappa * E[q]);
+        const T lam = (T(2) + R) / (T(6) + T(3) * R + R * R);
+        D[q] = c * lam / (kappa * rho);
+    }
+}
+
+int grid_for(long long N) {
+    long long b = (N + 255) / 256;
+    return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+template <typename T>
+LvlArgs<T> level_args(const FldHierarchy* H, int l, double dt) {
+    const FldLevel& L = H->L[l];
+    LvlArgs<T> a;
+    a.x = static_cast<T*>(L.x);
+    a.b = static_cast<const T*>(L.b);
+    a.r = static_cast<T*>(L.r);
+    a.D = static_cast<const T*>(L.D);
+    for (int ax = 0; ax < 3; ++ax) {
+        a.n[ax] = L.n[ax];
+        a.idx2[ax] = L.n[ax] > 1 ? (T)(1.0 / (L.dx[ax] * L.dx[ax])) : T(0);
+        a.per[ax] = H->bc_lo[ax] == 0 && H->bc_hi[ax] == 0;
+    }
+    a.N = L.N;
+    a.dt = (T)dt;
+    return a;
+}
+
+template <typename T>
+cudaError_t smooth(const FldHierarchy* H, int l, double dt, int sweeps, cudaStream_t s) {
+    const LvlArgs<T> a = level_args<T>(H, l, dt);
+    for (int it = 0; it < sweeps; ++it)
+        for (int color = 0; color < 2; ++color) smooth_kernel<T><<<grid_for(a.N), 256, 0, s>>>(a, color);
+    return cudaGetLastError();
+}
+
+template <typename T>
+void restrict_to(const FldHierarchy* H, int l, const void* fine, void* coarse, cudaStream_t s) {
+    const FldLevel& F = H->L[l];
+    const FldLevel& C = H->L[l + 1];
+    restrict_kernel<T><<<grid_for(C.N), 256, 0, s>>>(
+        static_cast<const T*>(fine), static_cast<T*>(coarse), F.n[0], F.n[1], C.n[0], C.n[1],
+        C.n[2], F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1, C.N);
+}
+
+template <typename T>
+cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er, double dt,
+                    double c, double kappa, double rtol, int max_cycles, int* cycles,
+                    double* rel_resid, cudaStream_t s) {
+    FldLevel& L0 = H->L[0];
+    L0.x = Er;
+    cudaError_t e = cudaMemcpyAsync(L0.b, Er, sizeof(T) * L0.N, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    {
+        const LvlArgs<T> a = level_args<T>(H, 0, dt);
+        coeff_kernel<T><<<grid_for(L0.N), 256, 0, s>>>(
+            static_cast<const T*>(U), static_cast<const T*>(L0.b), static_cast<T*>(L0.D), a,
+            (T)c, (T)kappa, (T)m.dxk[0], (T)m.dxk[1], (T)m.dxk[2]);
+    }
+    for (int l = 0; l + 1 < H->nl; ++l) restrict_to<T>(H, l, H->L[l].D, H->L[l + 1].D, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    int done = 0;
+    double rel = -1.0;
+    for (int cyc = 0; cyc < max_cycles; ++cyc) {
+        // down: smooth, residual, restrict
+        for (int l = 0; l + 1 < H->nl; ++l) {
+            if ((e = smooth<T>(H, l, dt, FLD_PRE, s)) != cudaSuccess) return e;
+            residual_kernel<T><<<grid_for(H->L[l].N), 256, 0, s>>>(level_args<T>(H, l, dt), nullptr);
+            restrict_to<T>(H, l, H->L[l].r, H->L[l + 1].b, s);
+            e = cudaMemsetAsync(H->L[l + 1].x, 0, sizeof(T) * H->L[l + 1].N, s);
+            if (e != cudaSuccess) return e;
+        }
+        if ((e = smooth<T>(H, H->nl - 1, dt, FLD_COARSE, s)) != cudaSuccess) return e;
+        // up: prolong the correction, smooth
+        for (int l = H->nl - 2; l >= 0; --l) {
+            const FldLevel& F = H->L[l];
+            const FldLevel& C = H->L[l + 1];
+            prolong_kernel<T><<<grid_for(F.N), 256, 0, s>>>(
+                static_cast<T*>(F.x), static_cast<const T*>(C.x), F.n[0], F.n[1], C.n[0], C.n[1],
+                F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1, F.N);
+            if ((e = smooth<T>(H, l, dt, FLD_POST, s)) != cudaSuccess) return e;
+        }
+        done = cyc + 1;
+        if (rtol > 0.0) {
+            if ((e = cudaMemsetAsync(H->norms, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
+            residual_kernel<T><<<grid_for(L0.N), 256, 0, s>>>(level_args<T>(H, 0, dt), H->norms);
+            double nr[2];
+            if ((e = cudaMemcpyAsync(nr, H->norms, sizeof(nr), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            rel = nr[1] > 0.0 ? std::sqrt(nr[0] / nr[1]) : 0.0;
+            if (!(rel > rtol)) break;             // converged (or NaN: stop and report it)
+        }
+    }
+    if (cycles) *cycles = done;
+    if (rel_resid) *rel_resid = rel;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+FldHierarchy* fld_create(const MeshDesc& m, int dtype) {
+    FldHierarchy* H = new (std::nothrow) FldHierarchy();
+    if (!H) return nullptr;
+    H->dtype = dtype;
+    const size_t es = dtype == HARD_F64 ? 8 : 4;
+    for (int a = 0; a < 3; ++a) {
+        H->n0[a] = m.n[a];
+        H->bc_lo[a] = m.bc_lo[a];
+        H->bc_hi[a] = m.bc_hi[a];
+    }
+    int n[3] = {m.n[0], m.n[1], m.n[2]};
+    double dx[3] = {m.dxk[0], m.dxk[1], m.dxk[2]};
+    int nl = 0;
+    bool ok = true;
+    while (nl < FLD_MAX_LEVELS) {
+        FldLevel& L = H->L[nl];
+        L.N = (long long)n[0] * n[1] * n[2];
+        for (int a = 0; a < 3; ++a) {
+            L.n[a] = n[a];
+            L.dx[a] = dx[a];
+        }
+        L.x = nullptr;
+        if (nl > 0 && cudaMalloc(&L.x, es * L.N) != cudaSuccess) ok = false;
+        if (cudaMalloc(&L.b, es * L.N) != cudaSuccess) ok = false;
+        if (cudaMalloc(&L.r, es * L.N) != cudaSuccess) ok = false;
+        if (cudaMalloc(&L.D, es * L.N) != cudaSuccess) ok = false;
+        ++nl;
+        if (!ok) break;
+        bool any = false;
+        for (int a = 0; a < 3; ++a) {
+            L.coarsened[a] = n[a] >= 4 && n[a] % 2 == 0;
+            any |= L.coarsened[a];
+        }
+        if (!any || L.N <= 64) {
+            for (int a = 0; a < 3; ++a) L.coarsened[a] = false;
+            break;
+        }
+        for (int a = 0; a < 3; ++a)
+            if (L.coarsened[a]) {
+                n[a] /= 2;
+                dx[a] *= 2.0;
+            }
+    }
+    H->nl = nl;
+    if (ok && cudaMalloc(&H->norms, 2 * sizeof(double)) != cudaSuccess) ok = false;
+    if (!ok) {
+        fld_destroy(H);
+        cudaGetLastError();
+        return nullptr;
+    }
+    return H;
+}
+
+void fld_destroy(FldHierarchy* H) {
+    if (!H) return;
+    for (int l = 0; l < H->nl; ++l) {
+        if (l > 0) cudaFree(H->L[l].x);
+        cudaFree(H->L[l].b);
+        cudaFree(H->L[l].r);
+        cudaFree(H->L[l].D);
+    }
+    cudaFree(H->norms);
+    delete H;
+}
+
+bool fld_matches(const FldHierarchy* H, const MeshDesc& m, int dtype) {
+    if (!H || H->dtype != dtype) return false;
+    for (int a = 0; a < 3; ++a)
+        if (H->n0[a] != m.n[a] || H->bc_lo[a] != m.bc_lo[a] || H->bc_hi[a] != m.bc_hi[a] ||
+            H->L[0].dx[a] != m.dxk[a])
+            return false;
+    return true;
+}
+
+int fld_levels(const FldHierarchy* H) { return H ? H->nl : 0; }
+
+cudaError_t fld_solve(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er, double dt,
+                      double c, double kappa, double rtol, int max_cycles, int* cycles,
+                      double* rel_resid, cudaStream_t s) {
+    return H->dtype == HARD_F64
+               ? solve_t<double>(H, m, U, Er, dt, c, kappa, rtol, max_cycles, cycles, rel_resid, s)
+               : solve_t<float>(H, m, U, Er, dt, c, kappa, rtol, max_cycles, cycles, rel_resid, s);
+}
+
+}  // namespace hh

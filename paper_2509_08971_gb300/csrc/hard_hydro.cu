@@ -8,6 +8,7 @@
 
 #include "hard_hydro.h"
 #include "launch.h"
+#include "fld_launch.h"
 #include "rad_launch.h"
 #include "weno_launch.h"
 
@@ -34,6 +35,7 @@ struct hard_hydro_s {
     long long tot_rows = 0;
     void* adj = nullptr;             // adjoint scratch: primitive cotangent | stage-1 cotangent
     size_t adj_bytes = 0;
+    hh::FldHierarchy* fld = nullptr; // radiation diffusion multigrid levels, on first use
     cudaStream_t last = nullptr;
 };
 
@@ -100,6 +102,8 @@ void build_mesh(hard_hydro_s* h) {
 }
 
 void free_scratch(hard_hydro_s* h) {
+    hh::fld_destroy(h->fld);
+    h->fld = nullptr;
     if (h->adj) cudaFree(h->adj);
     h->adj = nullptr;
     h->adj_bytes = 0;
@@ -491,6 +495,30 @@ int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->last = s;
     return from_cuda(hh::launch_rad_exchange(h->mesh, h->dtype, U, Er, dt, prm, status_slot(h), s));
+}
+
+int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, double c,
+                        double kappa, double rtol, int max_cycles, int* cycles_out,
+                        double* resid_out, void* stream) {
+    if (!h || !U || !Er || !aligned16(U) || !aligned16(Er)) return HARD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(c > 0.0) || !std::isfinite(c) ||
+        !(kappa > 0.0) || !std::isfinite(kappa) || max_cycles < 1 || !std::isfinite(rtol))
+        return HARD_EINVAL;
+    if (h->mesh.dim == 0) return HARD_EUNSUPPORTED;          // nothing to diffuse along
+    if (!hh::fld_matches(h->fld, h->mesh, h->dtype)) {
+        hh::fld_destroy(h->fld);
+        h->fld = hh::fld_create(h->mesh, h->dtype);
+        if (!h->fld) return HARD_ENOMEM;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    int cyc = 0;
+    double rel = -1.0;
+    const cudaError_t e = hh::fld_solve(h->fld, h->mesh, U, Er, dt, c, kappa, rtol, max_cycles,
+                                        &cyc, &rel, s);
+    if (cycles_out) *cycles_out = cyc;
+    if (resid_out) *resid_out = rel;
+    return from_cuda(e);
 }
 
 int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_out, void* gU_in,

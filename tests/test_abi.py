@@ -62,6 +62,9 @@ def test_host_only_calls_without_gpu(libpath):
     assert hh.hard_hydro_rad_exchange(h, None, None, 1e-3, (1, 1, 1, 1), None) == hh.HARD_EINVAL
     assert hh.hard_hydro_rad_exchange(h, 16, 32, 1e-3, (1, 0, 1, 1), None) == hh.HARD_EINVAL
     assert hh.hard_hydro_rad_exchange(h, 16, 32, -1.0, (1, 1, 1, 1), None) == hh.HARD_EINVAL
+    assert hh.hard_hydro_fld_step(h, None, None, 1.0, 1.0, 1.0, 1e-6, 10, None)[0] == hh.HARD_EINVAL
+    assert hh.hard_hydro_fld_step(h, 16, 32, 1.0, 1.0, -1.0, 1e-6, 10, None)[0] == hh.HARD_EINVAL
+    assert hh.hard_hydro_fld_step(h, 16, 32, 1.0, 1.0, 1.0, 1e-6, 0, None)[0] == hh.HARD_EINVAL
     h2 = hh.hard_hydro_create(16, 2, 1, 1.4, 0)
     assert hh.hard_hydro_set_scheme(h2, hh.HARD_SCHEME_WENO5Z_HLL) == hh.HARD_EINVAL
     hh.hard_hydro_destroy(h2)
