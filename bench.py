@@ -476,6 +476,39 @@ def main():
                         "algorithmic_bytes_per_launch": rad_bytes}}
     del mr, Urd, Erd
 
+    # ---------------- flux-limited radiation diffusion (multigrid), FP32 ----------------
+    mf = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32)
+    gf = np.random.default_rng(100 + rank)
+    Uf = torch.zeros((5,) + shape, dtype=torch.float32, device=dev)
+    Uf[0] = torch.tensor(1.0 + 0.5 * gf.random(shape), dtype=torch.float32, device=dev)
+    Ef0 = torch.tensor(1.0 + 0.5 * gf.random(shape), dtype=torch.float32, device=dev)
+    Ef = Ef0.clone()
+    dt_fld = 100.0 * (1.0 / n) ** 2 * 3             # diffusion number ~ 100 (c = kappa = 1)
+    mf.fld_step(Uf, Ef, dt_fld, 1.0, 1.0, rtol=1e-5, max_cycles=40)      # builds the levels
+    Ef.copy_(Ef0)
+    barrier()
+    e0.record(stream)
+    cyc_f, res_f = mf.fld_step(Uf, Ef, dt_fld, 1.0, 1.0, rtol=1e-5, max_cycles=40)
+    e1.record(stream)
+    barrier()
+    fld_ms = e0.elapsed_time(e1)
+    # bytes per V-cycle: per level, two pre- and two post-smoothing red-black
+    # sweeps (24 B/cell each: x read twice, b and D, x written), the fused
+    # residual-restriction (13), prolongation (12): 121 B/cell, x 8/7 over
+    # the levels
+    fld_bytes = 121.0 * 8.0 / 7.0 * cells * cyc_f
+    fld_achieved = fld_bytes / (fld_ms * 1e-3) / 1e9
+    fld = {"workload": f"{n}^3 periodic implicit flux-limited diffusion step, c = kappa = 1, "
+                       "rho, E ~ 1 + 0.5 U[0,1) (seeded), diffusion number ~100, "
+                       "V-cycles to a 1e-5 relative residual, FP32",
+           "value": whole_job_value(world, cells, cyc_f, rank_max(fld_ms)),
+           "unit": "cell-V-cycles/s", "cycles": cyc_f, "rel_residual": res_f, "ms": fld_ms,
+           "roofline": {"bound": "hbm", "achieved": fld_achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": fld_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                        "kernel": "V-cycle (smooth/residual/restrict/prolong kernels)",
+                        "algorithmic_bytes_per_cycle": fld_bytes / max(cyc_f, 1)}}
+    del mf, Uf, Ef, Ef0
+
     # ---------------- FP64 plain ----------------
     m64 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float64,
                        kernel=hh.HARD_KERNEL_PLAIN)
@@ -594,6 +627,7 @@ def main():
         "roofline": roofline,
         "weno5z_hll": weno,
         "rad_exchange": rad,
+        "fld_multigrid": fld,
         "batched": batched,
         "adjoint": adjoint,
         "fp64_plain": {"value": value64, "unit": UNIT, "steps": k64,

@@ -229,7 +229,8 @@ int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const 
  * relative residual (-1 when rtol <= 0).  The handle allocates its multigrid
  * levels on first use (freed by hard_hydro_set of another element type and by
  * hard_hydro_destroy).  With rtol > 0 the call synchronises `stream` once per
- * cycle.  A mesh with no active axis returns HARD_EUNSUPPORTED. */
+ * cycle.  A mesh with no active axis or with 2^31 cells or more returns
+ * HARD_EUNSUPPORTED. */
 int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, double c,
                         double kappa, double rtol, int max_cycles, int* cycles_out,
                         double* resid_out, void* stream);

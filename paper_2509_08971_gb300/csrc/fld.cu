@@ -27,6 +27,7 @@ namespace hh {
 
 constexpr int FLD_MAX_LEVELS = 16;
 constexpr int FLD_PRE = 2, FLD_POST = 2, FLD_COARSE = 50;
+constexpr int FLD_COARSE_SMEM = 1024;       // coarsest levels up to this size: one block, in smem
 
 struct FldLevel {
     int n[3];
@@ -70,30 +71,31 @@ __device__ __forceinline__ void cell_ijk(long long q, const int n[3], int& i, in
     k = (int)(t / n[1]);
 }
 
-// neighbour index along one axis (-1: no face there)
-__device__ __forceinline__ int nb_index(int i, int n, int step, bool per) {
-    const int m = i + step;
-    if (m >= 0 && m < n) return m;
-    return per ? (m + n) % n : -1;
-}
-
-// the cell's stencil: diagonal 1 + sum w and sum w x_nb
+// the cell's stencil: diagonal 1 + sum w and sum w x_nb (32-bit cell
+// indices: a level has fewer than 2^31 cells)
 template <typename T>
-__device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k, long long q,
-                                        T& diag, T& off) {
+__device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k, int q, T& diag,
+                                        T& off) {
     const int c[3] = {i, j, k};
-    const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+    const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
     const T Dc = a.D[q];
     diag = T(1);
     off = T(0);
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        if (a.n[ax] <= 1) continue;
+        const int n = a.n[ax];
+        if (n <= 1) continue;
 #pragma unroll
         for (int s = -1; s <= 1; s += 2) {
-            const int m = nb_index(c[ax], a.n[ax], s, a.per[ax]);
-            if (m < 0) continue;
-            const long long qn = q + (long long)(m - c[ax]) * stride[ax];
+            const int m = c[ax] + s;
+            int qn;
+            if (m >= 0 && m < n) {
+                qn = q + s * stride[ax];
+            } else if (a.per[ax]) {
+                qn = q + (m < 0 ? (n - 1) : -(n - 1)) * stride[ax];    // across the wrap
+            } else {
+                continue;                                               // a wall: no flux
+            }
             const T w = a.dt * (T(0.5) * (Dc + a.D[qn])) * a.idx2[ax];
             diag += w;
             off += w * a.x[qn];
@@ -101,44 +103,120 @@ __device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k
     }
 }
 
+// Launch shape of the level kernels: x along threads (and blockIdx.x), one
+// row j per blockIdx.y, one plane k per blockIdx.z: no index division.
 template <typename T>
-__global__ void __launch_bounds__(256) smooth_kernel(const LvlArgs<T> a, int color) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.N;
-         q += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(q, a.n, i, j, k);
-        if (((i + j + k) & 1) != color) continue;
-        T diag, off;
-        stencil(a, i, j, k, q, diag, off);
-        a.x[q] = (a.b[q] + off) / diag;
-    }
+__global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int color) {
+    const int j = blockIdx.y, k = blockIdx.z;
+    // the cells of this colour in the row: i = 2p + ((j + k + color) & 1)
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+    if (i >= a.n[0]) return;
+    const int q = (k * a.n[1] + j) * a.n[0] + i;
+    T diag, off;
+    stencil(a, i, j, k, q, diag, off);
+    a.x[q] = (a.b[q] + off) / diag;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) residual_kernel(const LvlArgs<T> a, double* norms) {
+__global__ void __launch_bounds__(128) residual_kernel(const LvlArgs<T> a) {
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n[0]) return;
+    const int q = (k * a.n[1] + j) * a.n[0] + i;
+    T diag, off;
+    stencil(a, i, j, k, q, diag, off);
+    a.r[q] = a.b[q] - (diag * a.x[q] - off);
+}
+
+// Residual of level l restricted to level l+1 in one pass: one thread per
+// coarse cell computes its children's residuals and writes their mean to the
+// coarse right-hand side, and zeroes the coarse correction.
+template <typename T>
+__global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T> a, T* bc, T* xc,
+                                                                int nc0, int nc1, int h0, int h1,
+                                                                int h2) {
+    const int J = blockIdx.y, K = blockIdx.z;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc0) return;
+    T sum = T(0);
+    for (int cz = 0; cz < h2; ++cz)
+        for (int cy = 0; cy < h1; ++cy)
+            for (int cx = 0; cx < h0; ++cx) {
+                const int i = I * h0 + cx, j = J * h1 + cy, k = K * h2 + cz;
+                const int q = (k * a.n[1] + j) * a.n[0] + i;
+                T diag, off;
+                stencil(a, i, j, k, q, diag, off);
+                sum += a.b[q] - (diag * a.x[q] - off);
+            }
+    const int Q = (K * nc1 + J) * nc0 + I;
+    bc[Q] = sum / T(h0 * h1 * h2);
+    xc[Q] = T(0);
+}
+
+// sum r^2 and sum b^2 into norms[0..1]: grid-stride, one atomic per block
+template <typename T>
+__global__ void __launch_bounds__(256) norms_kernel(const T* r, const T* b, long long N,
+                                                    double* norms) {
+    __shared__ double sr[8], sb[8];
     double rr = 0.0, bb = 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.N;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(q, a.n, i, j, k);
-        T diag, off;
-        stencil(a, i, j, k, q, diag, off);
-        const T r = a.b[q] - (diag * a.x[q] - off);
-        a.r[q] = r;
-        rr += (double)r * (double)r;
-        bb += (double)a.b[q] * (double)a.b[q];
+        rr += (double)r[q] * (double)r[q];
+        bb += (double)b[q] * (double)b[q];
     }
-    if (norms) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rr += __shfl_xor_sync(0xffffffffu, rr, o);
-            bb += __shfl_xor_sync(0xffffffffu, bb, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(norms, rr);
-            atomicAdd(norms + 1, bb);
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        bb += __shfl_xor_sync(0xffffffffu, bb, o);
     }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sr[w] = rr;
+        sb[w] = bb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, tb = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            tr += sr[k];
+            tb += sb[k];
+        }
+        atomicAdd(norms, tr);
+        atomicAdd(norms + 1, tb);
+    }
+}
+
+// The coarsest level: `sweeps` red-black Gauss-Seidel sweeps by one block
+// (the level has at most a few thousand cells), so one launch instead of
+// 2 x sweeps.
+template <typename T>
+__global__ void __launch_bounds__(1024) coarse_solve_kernel(const LvlArgs<T> a, int sweeps) {
+    // the level fits in shared memory (at most FLD_COARSE_SMEM cells)
+    __shared__ T sx[FLD_COARSE_SMEM], sb[FLD_COARSE_SMEM], sD[FLD_COARSE_SMEM];
+    const int N = (int)a.N;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        sx[q] = a.x[q];
+        sb[q] = a.b[q];
+        sD[q] = a.D[q];
+    }
+    __syncthreads();
+    LvlArgs<T> s = a;
+    s.x = sx;
+    s.b = sb;
+    s.D = sD;
+    for (int it = 0; it < sweeps; ++it)
+        for (int color = 0; color < 2; ++color) {
+            for (int q = threadIdx.x; q < N; q += blockDim.x) {
+                const int i = q % a.n[0], t = q / a.n[0];
+                const int j = t % a.n[1], k = t / a.n[1];
+                if (((i + j + k) & 1) != color) continue;
+                T diag, off;
+                stencil(s, i, j, k, q, diag, off);
+                sx[q] = (sb[q] + off) / diag;
+            }
+            __syncthreads();
+        }
+    for (int q = threadIdx.x; q < N; q += blockDim.x) a.x[q] = sx[q];
 }
 
 // coarse[I] = mean of the children fine[...] (restriction of r, and of D)
@@ -164,16 +242,13 @@ __global__ void __launch_bounds__(256) restrict_kernel(const T* fine, T* coarse,
 
 // fine[i] += coarse[parent(i)]
 template <typename T>
-__global__ void __launch_bounds__(256) prolong_kernel(T* fine, const T* coarse, int nf0, int nf1,
-                                                      int nc0, int nc1, int h0, int h1, int h2,
-                                                      long long Nf) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Nf;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(q % nf0);
-        const long long t = q / nf0;
-        const int j = (int)(t % nf1), k = (int)(t / nf1);
-        fine[q] += coarse[((long long)(k / h2) * nc1 + j / h1) * nc0 + i / h0];
-    }
+__global__ void __launch_bounds__(128) prolong_kernel(T* fine, const T* coarse, int nf0, int nf1,
+                                                      int nc0, int nc1, int h0, int h1, int h2) {
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf0) return;
+    const long long q = ((long long)k * nf1 + j) * nf0 + i;
+    fine[q] += coarse[((long long)(k / h2) * nc1 + j / h1) * nc0 + i / h0];
 }
 
 // D = c lambda(R) / (kappa rho), R = |grad E| / (rho kappa E), on level 0
@@ -215,6 +290,12 @@ int grid_for(long long N) {
     return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
 }
 
+// one thread per x cell (or per x pair), a row per blockIdx.y, a plane per blockIdx.z
+dim3 rows_grid(const FldLevel& L, int per_thread) {
+    const int nx = (L.n[0] + per_thread - 1) / per_thread;
+    return dim3((unsigned)((nx + 127) / 128), (unsigned)L.n[1], (unsigned)L.n[2]);
+}
+
 template <typename T>
 LvlArgs<T> level_args(const FldHierarchy* H, int l, double dt) {
     const FldLevel& L = H->L[l];
@@ -236,8 +317,9 @@ LvlArgs<T> level_args(const FldHierarchy* H, int l, double dt) {
 template <typename T>
 cudaError_t smooth(const FldHierarchy* H, int l, double dt, int sweeps, cudaStream_t s) {
     const LvlArgs<T> a = level_args<T>(H, l, dt);
+    const dim3 g = rows_grid(H->L[l], 2);
     for (int it = 0; it < sweeps; ++it)
-        for (int color = 0; color < 2; ++color) smooth_kernel<T><<<grid_for(a.N), 256, 0, s>>>(a, color);
+        for (int color = 0; color < 2; ++color) smooth_kernel<T><<<g, 128, 0, s>>>(a, color);
     return cudaGetLastError();
 }
 
@@ -273,25 +355,36 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
         // down: smooth, residual, restrict
         for (int l = 0; l + 1 < H->nl; ++l) {
             if ((e = smooth<T>(H, l, dt, FLD_PRE, s)) != cudaSuccess) return e;
-            residual_kernel<T><<<grid_for(H->L[l].N), 256, 0, s>>>(level_args<T>(H, l, dt), nullptr);
-            restrict_to<T>(H, l, H->L[l].r, H->L[l + 1].b, s);
-            e = cudaMemsetAsync(H->L[l + 1].x, 0, sizeof(T) * H->L[l + 1].N, s);
-            if (e != cudaSuccess) return e;
+            const FldLevel& F = H->L[l];
+            const FldLevel& C = H->L[l + 1];
+            residual_restrict_kernel<T><<<rows_grid(C, 1), 128, 0, s>>>(
+                level_args<T>(H, l, dt), static_cast<T*>(C.b), static_cast<T*>(C.x), C.n[0],
+                C.n[1], F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
         }
-        if ((e = smooth<T>(H, H->nl - 1, dt, FLD_COARSE, s)) != cudaSuccess) return e;
+        {
+            const LvlArgs<T> a = level_args<T>(H, H->nl - 1, dt);
+            if (a.N <= FLD_COARSE_SMEM) {
+                coarse_solve_kernel<T><<<1, 1024, 0, s>>>(a, FLD_COARSE);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            } else if ((e = smooth<T>(H, H->nl - 1, dt, FLD_COARSE, s)) != cudaSuccess) {
+                return e;
+            }
+        }
         // up: prolong the correction, smooth
         for (int l = H->nl - 2; l >= 0; --l) {
             const FldLevel& F = H->L[l];
             const FldLevel& C = H->L[l + 1];
-            prolong_kernel<T><<<grid_for(F.N), 256, 0, s>>>(
+            prolong_kernel<T><<<rows_grid(F, 1), 128, 0, s>>>(
                 static_cast<T*>(F.x), static_cast<const T*>(C.x), F.n[0], F.n[1], C.n[0], C.n[1],
-                F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1, F.N);
+                F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
             if ((e = smooth<T>(H, l, dt, FLD_POST, s)) != cudaSuccess) return e;
         }
         done = cyc + 1;
         if (rtol > 0.0) {
             if ((e = cudaMemsetAsync(H->norms, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
-            residual_kernel<T><<<grid_for(L0.N), 256, 0, s>>>(level_args<T>(H, 0, dt), H->norms);
+            residual_kernel<T><<<rows_grid(L0, 1), 128, 0, s>>>(level_args<T>(H, 0, dt));
+            norms_kernel<T><<<grid_for(L0.N) < 152 * 4 ? grid_for(L0.N) : 152 * 4, 256, 0, s>>>(
+                static_cast<const T*>(L0.r), static_cast<const T*>(L0.b), L0.N, H->norms);
             double nr[2];
             if ((e = cudaMemcpyAsync(nr, H->norms, sizeof(nr), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
                 return e;
@@ -321,6 +414,10 @@ FldHierarchy* fld_create(const MeshDesc& m, int dtype) {
     double dx[3] = {m.dxk[0], m.dxk[1], m.dxk[2]};
     int nl = 0;
     bool ok = true;
+    if ((long long)n[0] * n[1] * n[2] >= (1ll << 31)) {      // 32-bit cell indices
+        delete H;
+        return nullptr;
+    }
     while (nl < FLD_MAX_LEVELS) {
         FldLevel& L = H->L[nl];
         L.N = (long long)n[0] * n[1] * n[2];

@@ -505,6 +505,7 @@ int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, doub
         !(kappa > 0.0) || !std::isfinite(kappa) || max_cycles < 1 || !std::isfinite(rtol))
         return HARD_EINVAL;
     if (h->mesh.dim == 0) return HARD_EUNSUPPORTED;          // nothing to diffuse along
+    if (h->mesh.N >= (1ll << 31)) return HARD_EUNSUPPORTED;  // 32-bit cell indices
     if (!hh::fld_matches(h->fld, h->mesh, h->dtype)) {
         hh::fld_destroy(h->fld);
         h->fld = hh::fld_create(h->mesh, h->dtype);
