@@ -60,6 +60,12 @@ def _declare(lib):
     lib.orc_rad_exchange.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
     grid = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I, ctypes.c_double]
     sgrid = [ctypes.c_int] + grid
+    lib.orc_advect_E_step.restype = ctypes.c_int
+    lib.orc_advect_E_step.argtypes = grid + [_D, _D, ctypes.c_double]
+    lib.orc_rusanov_E.restype = ctypes.c_double
+    lib.orc_rusanov_E.argtypes = [ctypes.c_double] * 4
+    lib.orc_rhs_E.restype = ctypes.c_int
+    lib.orc_rhs_E.argtypes = grid + [_D, _D, _D]
     lib.orc_rhs_s.restype = ctypes.c_int
     lib.orc_rhs_s.argtypes = sgrid + [_D, _D]
     lib.orc_stage_s.restype = ctypes.c_int
@@ -220,6 +226,25 @@ class Grid:
         self.lib.orc_run_fixed_s(*self._g(), _dp(U), int(dts.size), _dp(dts))
         return U
 
+    def advect_E(self, U, E, dt):
+        """One Heun step of the radiation energy advection (WENO5-Z states,
+        Rusanov flux) with U's velocity field held fixed; returns E'."""
+        U = self._check(U)
+        E = _c64(E).copy()
+        if E.shape != (self.nz, self.ny, self.nx):
+            raise ValueError("E must have the cell shape")
+        if self.lib.orc_advect_E_step(*self._g0(), _dp(U), _dp(E), float(dt)):
+            raise ValueError("the advection needs three cells along every active axis")
+        return E
+
+    def rhs_E(self, U, E):
+        U = self._check(U)
+        E = _c64(E)
+        L = np.empty_like(E)
+        if self.lib.orc_rhs_E(*self._g0(), _dp(U), _dp(E), _dp(L)):
+            raise ValueError("the advection needs three cells along every active axis")
+        return L
+
     def totals(self, U):
         U = self._check(U)
         out = np.zeros(5, dtype=np.float64)
@@ -251,6 +276,11 @@ def rad_exchange(U, Er, dt, c, kappa, a_rad, cv, lib=None):
     prm = np.array([c, kappa, a_rad, cv], dtype=np.float64)
     it = (lib or load()).orc_rad_exchange(int(n), _dp(prm), float(dt), _dp(U), _dp(Er))
     return U, Er, int(it)
+
+
+def rusanov_E(EL, ER, uL, uR, lib=None):
+    """Rusanov flux of E u from the face states."""
+    return float((lib or load()).orc_rusanov_E(float(EL), float(ER), float(uL), float(uR)))
 
 
 def hll(WL, WR, gamma, lib=None):

@@ -27,6 +27,8 @@
  *     (Sec. 3.1 and Sec. 3.5 use a CFL-limited step but print no formula).
  *   - Exact Riemann solver for the 1D ideal-gas Euler equations (Toro ch. 4),
  *     used to build the reference solution of the L1 metric, Eq. "l1_error".
+ *   - Radiation energy advection, d_j(E v^j) of Eq. "radiation": WENO5-Z
+ *     states and the Rusanov flux, Heun in time with U held fixed.
  *   - Radiative heating / cooling, Eq. "heating-cooling": a pointwise
  *     backward-Euler exchange of fluid and radiation energy (orc_rad_exchange).
  *   - Second scheme (scheme = 1), the paper's own choice of Sec. 2.2.2:
@@ -598,6 +600,98 @@ int orc_get_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Radiation energy advection (the d_j(E v^j) term of Eq. "radiation").       */
+/* ------------------------------------------------------------------------ */
+
+/* The Rusanov flux of E u from face states (E_L, u_L), (E_R, u_R). */
+double orc_rusanov_E(double EL, double ER, double uL, double uR) {
+    double a = fmax(fabs(uL), fabs(uR));
+    return 0.5 * (EL * uL + ER * uR) - 0.5 * a * (ER - EL);
+}
+
+/* E of cell (i,j,k) displaced by m cells along axis d (the ghost map of
+ * fetch_cons; E is a scalar, so a reflecting wall does not flip it). */
+static double fetch_scalar(const grid_t* g, const double* E, int d, int i, int j, int k, int m) {
+    int idx[3] = {i, j, k};
+    int flip = 0;
+    idx[d] = ghost_src(idx[d] + m, g->n[d], g->bc[2 * d], g->bc[2 * d + 1], &flip);
+    return E[cell_index(g, idx[0], idx[1], idx[2])];
+}
+
+/*
+ * Rusanov (local Lax-Friedrichs) flux of E v through the face between cell
+ * (i,j,k) and its +1 neighbour along d (Sec. 2.2.2: WENO5-Z states of every
+ * variable, Rusanov for the radiation energy density): WENO5-Z states E_L,
+ * E_R of E and u_L, u_R of the normal velocity (a primitive of U) from the
+ * six cells i-2 .. i+3, then
+ *   F = (E_L u_L + E_R u_R) / 2 - a (E_R - E_L) / 2,  a = max(|u_L|, |u_R|).
+ */
+static double rusanov_E(const grid_t* g, const double* U, const double* E, int d, int i, int j,
+                        int k) {
+    double e[6], u[6];
+    for (int s = 0; s < 6; ++s) {
+        double Uc[NF], W[NF];
+        fetch_cons(g, U, d, i, j, k, s - 2, Uc);
+        cons_to_prim(Uc, g->gamma, W);
+        u[s] = W[1 + d];
+        e[s] = fetch_scalar(g, E, d, i, j, k, s - 2);
+    }
+    double el[5] = {e[0], e[1], e[2], e[3], e[4]}, er[5] = {e[5], e[4], e[3], e[2], e[1]};
+    double ul[5] = {u[0], u[1], u[2], u[3], u[4]}, ur[5] = {u[5], u[4], u[3], u[2], u[1]};
+    return orc_rusanov_E(orc_weno5z(el), orc_weno5z(er), orc_weno5z(ul), orc_weno5z(ur));
+}
+
+/* L_E(E; U) = - sum_{d active} (F_{i+1/2} - F_{i-1/2}) / dx_d. */
+static void rhs_E(const grid_t* g, const double* U, const double* E, double* L) {
+    size_t N = ncell(g);
+    memset(L, 0, sizeof(double) * N);
+    for (int d = 0; d < 3; ++d) {
+        if (!axis_active(g, d)) continue;
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int lo[3] = {i, j, k};
+                    lo[d] -= 1;
+                    double Fhi = rusanov_E(g, U, E, d, i, j, k);
+                    double Flo = rusanov_E(g, U, E, d, lo[0], lo[1], lo[2]);
+                    L[cell_index(g, i, j, k)] -= (Fhi - Flo) / g->dx[d];
+                }
+    }
+}
+
+/*
+ * One Heun step (Shu-Osher form, the Butcher tableau of Sec. 2.2.2) of the
+ * radiation energy advection with the velocity field of U held fixed:
+ *   E1 = E + dt L_E(E),  E' = E/2 + (E1 + dt L_E(E1))/2.
+ * Needs three cells along every active axis.  Updates E in place.
+ */
+int orc_advect_E_step(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
+                      const double* U, double* E, double dt) {
+    grid_t g;
+    if (make_grid_s(&g, 1, nx, ny, nz, dxyz, bc6, gamma)) return -1;
+    size_t N = ncell(&g);
+    double* L = (double*)malloc(sizeof(double) * N);
+    double* E1 = (double*)malloc(sizeof(double) * N);
+    rhs_E(&g, U, E, L);
+    for (size_t q = 0; q < N; ++q) E1[q] = E[q] + dt * L[q];
+    rhs_E(&g, U, E1, L);
+    for (size_t q = 0; q < N; ++q) E[q] = 0.5 * E[q] + 0.5 * (E1[q] + dt * L[q]);
+    free(L);
+    free(E1);
+    return 0;
+}
+
+/* Exposed for unit tests: the flux-difference operator L_E alone. */
+int orc_rhs_E(int nx, int ny, int nz, const double* dxyz, const int* bc6, double gamma,
+              const double* U, const double* E, double* L) {
+    grid_t g;
+    if (make_grid_s(&g, 1, nx, ny, nz, dxyz, bc6, gamma)) return -1;
+    rhs_E(&g, U, E, L);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

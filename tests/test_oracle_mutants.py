@@ -14,7 +14,7 @@ import oracle
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = [os.path.join(ROOT, "tests", f) for f in
         ("test_oracle_hllc.py", "test_oracle_riemann.py", "test_oracle_scheme.py",
-         "test_oracle_weno.py", "test_oracle_rad.py")]
+         "test_oracle_weno.py", "test_oracle_rad.py", "test_oracle_advect.py")]
 
 # (name, original text, planted text)
 MUTANTS = [
@@ -110,6 +110,13 @@ MUTANTS = [
     ("exchange rate without density", "double k = c * kappa * rho;", "double k = c * kappa;"),
     ("radiation energy update sign", "Er[q] = Er[q] + (e - x);", "Er[q] = Er[q] - (e - x);"),
     ("exchange ignores kinetic energy", "U[4 * N + q] = x + kin;", "U[4 * N + q] = x;"),
+    # radiation energy advection
+    ("Rusanov dissipation sign", "return 0.5 * (EL * uL + ER * uR) - 0.5 * a * (ER - EL);",
+     "return 0.5 * (EL * uL + ER * uR) + 0.5 * a * (ER - EL);"),
+    ("Rusanov speed from one side", "double a = fmax(fabs(uL), fabs(uR));", "double a = fabs(uL);"),
+    ("advection velocity from the wrong axis", "u[s] = W[1 + d];", "u[s] = W[1];"),
+    ("advected E states not mirrored",
+     "er[5] = {e[5], e[4], e[3], e[2], e[1]};", "er[5] = {e[1], e[2], e[3], e[4], e[5]};"),
 ]
 
 
