@@ -476,6 +476,33 @@ def main():
                         "algorithmic_bytes_per_launch": rad_bytes}}
     del mr, Urd, Erd
 
+    # ---------------- radiation energy advection (WENO5-Z + Rusanov), FP32 ----------------
+    Ea = torch.tensor(1.0 + 0.5 * np.random.default_rng(200 + rank).random(shape),
+                      dtype=torch.float32, device=dev)
+    dt_adv = m32.cfl_dt(U, CFL)
+    for _ in range(2):
+        m32.advect_E(U, Ea, dt_adv)
+    barrier()
+    e0.record(stream)
+    for _ in range(5):
+        m32.advect_E(U, Ea, dt_adv)
+    e1.record(stream)
+    barrier()
+    adv_ms = e0.elapsed_time(e1) / 5
+    # per Heun step: two stages, each reading E, rho and the three momenta and
+    # writing E (24 B/cell), the second also reading E^n (4 B/cell)
+    adv_bytes = (24.0 + 28.0) * cells
+    adv_achieved = adv_bytes / (adv_ms * 1e-3) / 1e9
+    advect = {"workload": f"{n}^3 periodic radiation energy advection by the smooth-flow velocity "
+                          "field, E ~ 1 + 0.5 U[0,1) (seeded), Heun step, FP32",
+              "value": whole_job_value(world, cells, 2, rank_max(adv_ms)), "unit": UNIT,
+              "ms_per_step": adv_ms,
+              "roofline": {"bound": "hbm", "achieved": adv_achieved, "peak": hbm, "unit": "GB/s",
+                           "frac": adv_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                           "kernel": "weno_advect_kernel<float,32,8,3> (mean of the two stages)",
+                           "algorithmic_bytes_per_step": adv_bytes}}
+    del Ea
+
     # ---------------- flux-limited radiation diffusion (multigrid), FP32 ----------------
     mf = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32)
     gf = np.random.default_rng(100 + rank)
@@ -627,6 +654,7 @@ def main():
         "roofline": roofline,
         "weno5z_hll": weno,
         "rad_exchange": rad,
+        "radiation_advection": advect,
         "fld_multigrid": fld,
         "batched": batched,
         "adjoint": adjoint,

@@ -212,6 +212,20 @@ int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U_out, doubl
 int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const double prm[4],
                             void* stream);
 
+/* Radiation energy advection (the d_j(E v^j) term of Eq. "radiation",
+ * Sec. 2.2.2): one Heun step (the two stages of hard_hydro_step) of
+ * dE/dt + div(E v) = 0 with the fluid velocity of U held fixed: WENO5-Z face
+ * states of E and of the normal velocity, the Rusanov flux
+ * (E_L u_L + E_R u_R)/2 - max(|u_L|, |u_R|)(E_R - E_L)/2, the handle's mesh
+ * and boundary kinds (E mirrors without a sign change at a reflecting wall).
+ * U: the handle's state (read); Er: the radiation energy density
+ * [nz][ny][nx], updated in place.  Device buffers of the handle's element
+ * type, 16-byte aligned, caller-owned; the intermediate stage uses the
+ * handle's scratch.  Every active axis needs at least three cells
+ * (HARD_EINVAL otherwise).  The caller chooses dt (a CFL limit is
+ * max |v_d| dt / dx_d <= 1 summed over the axes).  Asynchronous. */
+int hard_hydro_advect_E(hard_hydro_t h, const void* U, void* Er, double dt, void* stream);
+
 /* Flux-limited radiation diffusion (Sec. 2.2.1-2.2.2): one backward-Euler
  * step of dE/dt = div(D grad E), D = c lambda(R) / (kappa rho) with the
  * Levermore limiter lambda = (2 + R)/(6 + 3R + R^2), R = |grad E|/(rho kappa E),

@@ -46,6 +46,7 @@ def _declare(lib):
         "hard_hydro_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int]),
         "hard_hydro_rad_exchange": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double,
                                                    ctypes.POINTER(ctypes.c_double), _vp]),
+        "hard_hydro_advect_E": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
         "hard_hydro_fld_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int),
@@ -114,6 +115,10 @@ def hard_hydro_set_kernel(h, kernel, tile):
 
 def hard_hydro_set_scheme(h, scheme):
     return lib().hard_hydro_set_scheme(h, int(scheme))
+
+
+def hard_hydro_advect_E(h, U, Er, dt, stream):
+    return lib().hard_hydro_advect_E(h, U, Er, float(dt), stream)
 
 
 def hard_hydro_fld_step(h, U, Er, dt, c, kappa, rtol, max_cycles, stream):
@@ -275,6 +280,15 @@ class HardHydro:
 
     def set_scheme(self, scheme):
         check(hard_hydro_set_scheme(self.h, scheme), "hard_hydro_set_scheme")
+
+    def advect_E(self, U, Er, dt):
+        """In place on Er: one Heun step of the radiation energy advection."""
+        if not (Er.is_cuda and Er.is_contiguous() and Er.dtype == self.dtype
+                and tuple(Er.shape) == self.shape):
+            raise ValueError(f"Er must be a contiguous {self.dtype} CUDA tensor of shape {self.shape}")
+        check(hard_hydro_advect_E(self.h, self._check(U), Er.data_ptr(), dt, self._stream()),
+              "hard_hydro_advect_E")
+        return Er
 
     def fld_step(self, U, Er, dt, c, kappa, rtol=1e-8, max_cycles=50):
         """In place on Er: one implicit flux-limited diffusion step.  Returns

@@ -497,6 +497,23 @@ int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const 
     return from_cuda(hh::launch_rad_exchange(h->mesh, h->dtype, U, Er, dt, prm, status_slot(h), s));
 }
 
+int hard_hydro_advect_E(hard_hydro_t h, const void* U, void* Er, double dt, void* stream) {
+    if (!h || !U || !Er || !aligned16(U) || !aligned16(Er)) return HARD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (h->n[a] > 1 && h->n[a] < 3) return HARD_EINVAL;
+    if (h->mesh.dim == 0) return HARD_OK;                     // nothing moves
+    int rc = ensure_U1(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    const bool f64 = h->dtype == HARD_F64;
+    auto stage = f64 ? hh::launch_advect_E_stage_f64 : hh::launch_advect_E_stage_f32;
+    cudaError_t e = stage(h->mesh, 1, U, nullptr, Er, h->U1, dt, s);   // U1 holds E1
+    if (e == cudaSuccess) e = stage(h->mesh, 2, U, Er, h->U1, Er, dt, s);
+    return from_cuda(e);
+}
+
 int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, double c,
                         double kappa, double rtol, int max_cycles, int* cycles_out,
                         double* resid_out, void* stream) {

@@ -398,3 +398,175 @@ weno_stage_kernel(const StageArgs<T> A) {
 }
 
 }  // namespace hh
+
+namespace hh {
+
+// ----------------------------------------------------- radiation energy --
+// Advection of the radiation energy density E by the fluid velocity (the
+// d_j(E v^j) term of Eq. "radiation"), Sec. 2.2.2: WENO5-Z face states of E
+// and of the normal velocity, the Rusanov flux
+//   F = (E_L u_L + E_R u_R)/2 - max(|u_L|, |u_R|) (E_R - E_L)/2,
+// and the Heun stage combine, with the fluid state U held fixed.  Same tiling
+// as weno_stage_kernel, with a four-field plane (E and the three velocity
+// components along the kernel axes) and a two-field z window (E, w).
+
+template <typename T>
+struct AdvectArgs {
+    const T* U;          // fluid state [5][N] (velocities)
+    const T* E0;         // stage 2: E^n
+    const T* Ec;         // E the flux difference is taken of
+    T* Eo;               // output
+    long long N;
+    int n[3];
+    int bc_lo[3], bc_hi[3];
+    T dxk[3];            // per kernel axis: dx (FP64) or 1/dx (FP32)
+    double dt;
+    int stage;
+    int zchunk;
+};
+
+__device__ __forceinline__ double rusanov_e(double EL, double ER, double uL, double uR) {
+    const double a = fmax(fabs(uL), fabs(uR));
+    return 0.5 * (EL * uL + ER * uR) - 0.5 * a * (ER - EL);
+}
+__device__ __forceinline__ float rusanov_e(float EL, float ER, float uL, float uR) {
+    const float a = fmaxf(fabsf(uL), fabsf(uR));
+    return 0.5f * (EL * uL + ER * uR) - 0.5f * a * (ER - EL);
+}
+
+// E and the velocity along kernel axes (x', y', z') = physical (PX, PY, 2)
+// of kernel cell (gx, gy, gz) through the three-layer boundary map
+template <typename T, int DIM, int PX, int PY>
+__device__ __forceinline__ void load_ev(const AdvectArgs<T>& A, int gx, int gy, int gz, T out[4]) {
+    bool fx, fy = false, fz = false;
+    const int sx = bc_map3(gx, A.n[0], A.bc_lo[0], A.bc_hi[0], fx);
+    int sy = 0, sz = 0;
+    if (DIM >= 2) sy = bc_map3(gy, A.n[1], A.bc_lo[1], A.bc_hi[1], fy);
+    if (DIM >= 3) sz = bc_map3(gz, A.n[2], A.bc_lo[2], A.bc_hi[2], fz);
+    const long long c = ((long long)sz * A.n[1] + sy) * A.n[0] + sx;
+    const T rho = __ldg(A.U + c);
+    T m[3] = {__ldg(A.U + A.N + c), __ldg(A.U + 2 * A.N + c), __ldg(A.U + 3 * A.N + c)};
+    if (fx) m[PX] = -m[PX];
+    if (DIM >= 2 && fy) m[PY] = -m[PY];
+    if (DIM >= 3 && fz) m[2] = -m[2];
+    out[0] = __ldg(A.Ec + c);
+    out[1] = m[PX] / rho;
+    out[2] = DIM >= 2 ? m[PY] / rho : T(0);
+    out[3] = DIM >= 3 ? m[2] / rho : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T advect_face(const T e[6], const T u[6]) {
+    const T EL = weno5z(e[0], e[1], e[2], e[3], e[4]);
+    const T ER = weno5z(e[5], e[4], e[3], e[2], e[1]);
+    const T uL = weno5z(u[0], u[1], u[2], u[3], u[4]);
+    const T uR = weno5z(u[5], u[4], u[3], u[2], u[1]);
+    return rusanov_e(EL, ER, uL, uR);
+}
+
+template <typename T, int TX, int TY, int DIM, int PX, int PY>
+__global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T> A) {
+    constexpr int NT = TX * TY;
+    constexpr int HX = TX + 2 * WENO_G, HY = DIM >= 2 ? TY + 2 * WENO_G : 1;
+    constexpr int NPF = HX * HY;
+    __shared__ T Ps[4 * NPF];                        // E, u', v', w' planes
+    __shared__ T Fx[TY * (TX + 1)];
+    __shared__ T Fy[DIM >= 2 ? (TY + 1) * TX : 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX;
+    const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
+    const int z0 = DIM == 3 ? blockIdx.z * A.zchunk : 0;
+    const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.n[2]) : 1;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own = x < A.n[0] && (DIM < 2 || y < A.n[1]);
+    const T dt = (T)A.dt;
+
+    T we[6], ww[6], Fzp = T(0), Da = T(0), Db = T(0), Dc = T(0);
+#pragma unroll
+    for (int s = 0; s < 6; ++s) we[s] = ww[s] = T(0);
+
+    const int jbeg = DIM == 3 ? z0 - WENO_G : 0;
+    const int jend = DIM == 3 ? z1 + WENO_G : 1;
+    for (int j = jbeg; j < jend; ++j) {
+        const bool xy = DIM < 3 || (j >= z0 && j < z1);
+        T ej, wj, Dj;
+        if (xy) {
+            __syncthreads();
+            for (int e = tid; e < NPF; e += NT) {
+                const int hx = e % HX, hy = e / HX;
+                T v[4];
+                load_ev<T, DIM, PX, PY>(A, x0 - WENO_G + hx, y0 - (DIM >= 2 ? WENO_G : 0) + hy, j, v);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) Ps[f * NPF + e] = v[f];
+            }
+            __syncthreads();
+            for (int e = tid; e < (TX + 1) * TY; e += NT) {
+                const int fx = e % (TX + 1), row = e / (TX + 1);
+                const int hy = DIM >= 2 ? row + WENO_G : 0;
+                T ee[6], uu[6];
+#pragma unroll
+                for (int s = 0; s < 6; ++s) {
+                    ee[s] = Ps[0 * NPF + hy * HX + fx + s];
+                    uu[s] = Ps[1 * NPF + hy * HX + fx + s];
+                }
+                Fx[row * (TX + 1) + fx] = advect_face(ee, uu);
+            }
+            if (DIM >= 2) {
+                for (int e = tid; e < TX * (TY + 1); e += NT) {
+                    const int col = e % TX, fy = e / TX;
+                    T ee[6], vv[6];
+#pragma unroll
+                    for (int s = 0; s < 6; ++s) {
+                        ee[s] = Ps[0 * NPF + (fy + s) * HX + col + WENO_G];
+                        vv[s] = Ps[2 * NPF + (fy + s) * HX + col + WENO_G];
+                    }
+                    Fy[fy * TX + col] = advect_face(ee, vv);
+                }
+            }
+            __syncthreads();
+            const int hyc = DIM >= 2 ? ty + WENO_G : 0;
+            ej = Ps[0 * NPF + hyc * HX + tx + WENO_G];
+            wj = Ps[3 * NPF + hyc * HX + tx + WENO_G];
+            Dj = sub_over_dx(T(0), Fx[ty * (TX + 1) + tx + 1] - Fx[ty * (TX + 1) + tx], A.dxk[0]);
+            if (DIM >= 2)
+                Dj = sub_over_dx(Dj, Fy[(ty + 1) * TX + tx] - Fy[ty * TX + tx], A.dxk[1]);
+        } else {
+            T v[4];
+            load_ev<T, DIM, PX, PY>(A, min(x, A.n[0] - 1), min(y, A.n[1] - 1), j, v);
+            ej = v[0];
+            wj = v[3];
+            Dj = T(0);
+        }
+        int k;
+        T L;
+        if (DIM == 3) {
+            const int cnt = j - jbeg;
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                we[s] = we[s + 1];
+                ww[s] = ww[s + 1];
+            }
+            we[5] = ej;
+            ww[5] = wj;
+            T Fz = T(0);
+            if (cnt >= 5) Fz = advect_face(we, ww);
+            k = cnt >= 6 ? j - WENO_G : -1;
+            L = sub_over_dx(Da, Fz - Fzp, A.dxk[2]);
+            if (cnt >= 5) Fzp = Fz;
+            Da = Db;
+            Db = Dc;
+            Dc = Dj;
+        } else {
+            k = 0;
+            L = Dj;
+        }
+        if (k >= 0 && own) {
+            const long long c = ((long long)k * A.n[1] + y) * A.n[0] + x;
+            const T ec = A.Ec[c];
+            A.Eo[c] = A.stage == 1 ? madd(dt, L, ec) : madd(T(0.5), A.E0[c], T(0.5) * madd(dt, L, ec));
+        }
+    }
+}
+
+}  // namespace hh

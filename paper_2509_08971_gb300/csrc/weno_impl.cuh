@@ -66,7 +66,49 @@ cudaError_t run_weno(const MeshDesc& m, const StageCall& c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int TX, int TY, int DIM, int PX, int PY>
+cudaError_t run_advect(const MeshDesc& m, const AdvectArgs<T>& A, cudaStream_t s) {
+    const dim3 grid(wcdiv(m.n[0], TX), DIM >= 2 ? wcdiv(m.n[1], TY) : 1,
+                    DIM == 3 ? wcdiv(m.n[2], A.zchunk) : 1);
+    weno_advect_kernel<T, TX, TY, DIM, PX, PY><<<grid, TX * TY, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t HH_WCAT(launch_advect_E_stage_, HH_SUFFIX)(const MeshDesc& m, int stage, const void* U,
+                                                       const void* E0, const void* Ec, void* Eo,
+                                                       double dt, cudaStream_t s) {
+    for (int a = 0; a < 3; ++a)
+        if (m.n[a] > 1 && m.n[a] < WENO_G) return cudaErrorInvalidValue;
+    AdvectArgs<T> A{};
+    A.U = static_cast<const T*>(U);
+    A.E0 = static_cast<const T*>(E0);
+    A.Ec = static_cast<const T*>(Ec);
+    A.Eo = static_cast<T*>(Eo);
+    A.N = m.N;
+    for (int a = 0; a < 3; ++a) {
+        A.n[a] = m.n[a];
+        A.bc_lo[a] = m.bc_lo[a];
+        A.bc_hi[a] = m.bc_hi[a];
+        A.dxk[a] = width_param_w(m.dxk[a]);
+    }
+    A.dt = dt;
+    A.stage = stage;
+    A.zchunk = tile_desc(3, 0).zc;
+    if (m.dim == 3) return run_advect<32, 8, 3, 0, 1>(m, A, s);
+    if (m.dim == 2) {
+        if (m.px == 0 && m.py == 1) return run_advect<32, 8, 2, 0, 1>(m, A, s);
+        if (m.px == 0 && m.py == 2) return run_advect<32, 8, 2, 0, 2>(m, A, s);
+        return run_advect<32, 8, 2, 1, 2>(m, A, s);
+    }
+    if (m.dim == 1) {
+        if (m.px == 0) return run_advect<128, 1, 1, 0, 0>(m, A, s);
+        if (m.px == 1) return run_advect<128, 1, 1, 1, 0>(m, A, s);
+        return run_advect<128, 1, 1, 2, 0>(m, A, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t HH_WCAT(launch_weno_stage_, HH_SUFFIX)(const MeshDesc& m, const StageCall& c,
                                                    cudaStream_t s) {

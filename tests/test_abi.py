@@ -65,7 +65,10 @@ def test_host_only_calls_without_gpu(libpath):
     assert hh.hard_hydro_fld_step(h, None, None, 1.0, 1.0, 1.0, 1e-6, 10, None)[0] == hh.HARD_EINVAL
     assert hh.hard_hydro_fld_step(h, 16, 32, 1.0, 1.0, -1.0, 1e-6, 10, None)[0] == hh.HARD_EINVAL
     assert hh.hard_hydro_fld_step(h, 16, 32, 1.0, 1.0, 1.0, 1e-6, 0, None)[0] == hh.HARD_EINVAL
+    assert hh.hard_hydro_advect_E(h, None, None, 1.0, None) == hh.HARD_EINVAL
+    assert hh.hard_hydro_advect_E(h, 16, 32, 0.0, None) == hh.HARD_EINVAL
     h2 = hh.hard_hydro_create(16, 2, 1, 1.4, 0)
+    assert hh.hard_hydro_advect_E(h2, 16, 32, 1.0, None) == hh.HARD_EINVAL    # 2 cells along y
     assert hh.hard_hydro_set_scheme(h2, hh.HARD_SCHEME_WENO5Z_HLL) == hh.HARD_EINVAL
     hh.hard_hydro_destroy(h2)
     hh.hard_hydro_destroy(h)
