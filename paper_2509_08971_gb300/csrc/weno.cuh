@@ -151,6 +151,62 @@ __device__ __forceinline__ void weno_face(const T q[6][NF], T gamma, T gx, T F[N
     F[4] = Fn[4];
 }
 
+// Both face values of the middle cell of v0..v4: `right` at its right face
+// (weno5z(v0, .., v4)) and `left` at its left face (weno5z of the mirrored
+// stencil v4, .., v0).  The mirrored stencil has the indicators (b2, b1, b0)
+// and the same tau5, so in FP32 one pass shares the three ratios
+// tau5 / (b_k + eps): candidate k of the left value takes the linear weight
+// d_k with the ratio of b_{2-k}.
+// FP64 (the parity path) evaluates the two values exactly as weno5z of the
+// stencil and of its mirror, so that they round like the oracle's.
+__device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, double v3, double v4,
+                                            double& right, double& left) {
+    right = weno5z(v0, v1, v2, v3, v4);
+    left = weno5z(v4, v3, v2, v1, v0);
+}
+__device__ __forceinline__ void weno5z_pair(float v0, float v1, float v2, float v3, float v4,
+                                            float& right, float& left) {
+    const float sixth = 1.0f / 6.0f, c = 13.0f / 12.0f;
+    const float s0 = v0 - 2.0f * v1 + v2, t0 = v0 - 4.0f * v1 + 3.0f * v2;
+    const float s1 = v1 - 2.0f * v2 + v3, t1 = v1 - v3;
+    const float s2 = v2 - 2.0f * v3 + v4, t2 = 3.0f * v2 - 4.0f * v3 + v4;
+    const float b0 = fmaf(c * s0, s0, 0.25f * t0 * t0);
+    const float b1 = fmaf(c * s1, s1, 0.25f * t1 * t1);
+    const float b2 = fmaf(c * s2, s2, 0.25f * t2 * t2);
+    const float tau = fabsf(b0 - b2);
+    const float r0 = tau * vrcp(b0 + 1e-30f), r1 = tau * vrcp(b1 + 1e-30f),
+                r2 = tau * vrcp(b2 + 1e-30f);
+    {
+        const float p0 = (2.0f * v0 - 7.0f * v1 + 11.0f * v2) * sixth;
+        const float p1 = (-v1 + 5.0f * v2 + 2.0f * v3) * sixth;
+        const float p2 = (2.0f * v2 + 5.0f * v3 - v4) * sixth;
+        const float a0 = fmaf(0.1f, r0, 0.1f), a1 = fmaf(0.6f, r1, 0.6f), a2 = fmaf(0.3f, r2, 0.3f);
+        right = fmaf(a0, p0, fmaf(a1, p1, a2 * p2)) * vrcp(a0 + a1 + a2);
+    }
+    {
+        const float p0 = (2.0f * v4 - 7.0f * v3 + 11.0f * v2) * sixth;
+        const float p1 = (-v3 + 5.0f * v2 + 2.0f * v1) * sixth;
+        const float p2 = (2.0f * v2 + 5.0f * v1 - v0) * sixth;
+        const float a0 = fmaf(0.1f, r2, 0.1f), a1 = fmaf(0.6f, r1, 0.6f), a2 = fmaf(0.3f, r0, 0.3f);
+        left = fmaf(a0, p0, fmaf(a1, p1, a2 * p2)) * vrcp(a0 + a1 + a2);
+    }
+}
+
+// HLL flux along physical axis AX from the face states (primitives).
+template <int AX, typename T>
+__device__ __forceinline__ void hll_face(const T qL[NF], const T qR[NF], T gamma, T gx, T F[NF]) {
+    using R = Rot<AX>;
+    const T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
+    const T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
+    T Fn[NF];
+    hll_normal(WL, WR, gamma, gx, Fn);
+    F[0] = Fn[0];
+    F[R::n] = Fn[1];
+    F[R::t1] = Fn[2];
+    F[R::t2] = Fn[3];
+    F[4] = Fn[4];
+}
+
 // Boundary map with three ghost layers: m in [-3, n+2] -> interior index
 // (flip for a reflecting wall); indices beyond them (ragged tiles) clamp to a
 // valid cell whose value feeds no used face.
@@ -193,9 +249,10 @@ struct WenoSmem {
     static constexpr int HX = TX + 2 * WENO_G;
     static constexpr int HY = DIM >= 2 ? TY + 2 * WENO_G : 1;
     static constexpr int NP = NF * HX * HY;
-    static constexpr int NFX = NF * TY * (TX + 1);
-    static constexpr int NFY = DIM >= 2 ? NF * (TY + 1) * TX : 0;
-    static constexpr size_t bytes = sizeof(T) * (NP + NFX + NFY);
+    static constexpr int NFX = NF * TY * (TX + 1);                 // one x-face array
+    static constexpr int NFY = DIM >= 2 ? NF * (TY + 1) * TX : 0;  // one y-face array
+    // primitive plane; face states (left, right) and fluxes of the x and y faces
+    static constexpr size_t bytes = sizeof(T) * (NP + 3 * NFX + 3 * NFY);
 };
 
 template <typename T, int TX, int TY, int DIM, int PX, int PY>
@@ -209,7 +266,11 @@ weno_stage_kernel(const StageArgs<T> A) {
     __shared__ unsigned long long red_rate[NT / 32];
     T* Ps = reinterpret_cast<T*>(smem_raw);          // [NF][HY][HX]
     T* Fx = Ps + S::NP;                               // [NF][TY][TX+1]
-    T* Fy = Fx + S::NFX;                              // [NF][TY+1][TX]
+    T* QLx = Fx + S::NFX;                             // left states of the x faces
+    T* QRx = QLx + S::NFX;                            // right states
+    T* Fy = QRx + S::NFX;                             // [NF][TY+1][TX]
+    T* QLy = Fy + S::NFY;
+    T* QRy = QLy + S::NFY;
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -227,14 +288,15 @@ weno_stage_kernel(const StageArgs<T> A) {
     T rate_max = T(0);
     T tot[NF] = {T(0), T(0), T(0), T(0), T(0)};
 
-    // z stencil of this thread's column: primitives of the last six planes,
-    // the previous z-face flux and the x/y flux differences of three planes
-    T w[6][NF], Fzp[NF], Da[NF], Db[NF], Dc[NF];
+    // z stencil of this thread's column: primitives of the last five planes,
+    // the pending left state of the next z face, the previous z-face flux and
+    // the x/y flux differences of three planes
+    T w[5][NF], qLz[NF], Fzp[NF], Da[NF], Db[NF], Dc[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        Fzp[f] = Da[f] = Db[f] = Dc[f] = T(0);
+        qLz[f] = Fzp[f] = Da[f] = Db[f] = Dc[f] = T(0);
 #pragma unroll
-        for (int s = 0; s < 6; ++s) w[s][f] = T(0);
+        for (int s = 0; s < 5; ++s) w[s][f] = T(0);
     }
 
     const int jbeg = DIM == 3 ? z0 - WENO_G : 0;
@@ -253,33 +315,59 @@ weno_stage_kernel(const StageArgs<T> A) {
                 for (int f = 0; f < NF; ++f) Ps[(f * HY + hy) * HX + hx] = W[f];
             }
             __syncthreads();
-            // x faces: (TX+1) per row; face fx sits left of tile cell fx
-            for (int e = tid; e < (TX + 1) * TY; e += NT) {
-                const int fx = e % (TX + 1), row = e / (TX + 1);
-                const int hy = DIM >= 2 ? row + WENO_G : 0;
-                T q[6][NF];
+            // each cell's two face values per axis (halo cells -1 and TX / TY
+            // included): x face fx (left of tile cell fx) takes its left state
+            // from cell fx-1 and its right state from cell fx
+            constexpr int NRX = (TX + 2) * TY, NRY = DIM >= 2 ? TX * (TY + 2) : 0;
+            for (int e = tid; e < NRX + NRY; e += NT) {
+                if (e < NRX) {
+                    const int cx = e % (TX + 2) - 1, row = e / (TX + 2);
+                    const int hy = DIM >= 2 ? row + WENO_G : 0;
 #pragma unroll
-                for (int s = 0; s < 6; ++s)
+                    for (int f = 0; f < NF; ++f) {
+                        const T* v = Ps + (f * HY + hy) * HX + cx + WENO_G;
+                        T rv, lv;
+                        weno5z_pair(v[-2], v[-1], v[0], v[1], v[2], rv, lv);
+                        if (cx + 1 <= TX) QLx[(f * TY + row) * (TX + 1) + cx + 1] = rv;
+                        if (cx >= 0) QRx[(f * TY + row) * (TX + 1) + cx] = lv;
+                    }
+                } else {
+                    const int e2 = e - NRX;
+                    const int col = e2 % TX, cy = e2 / TX - 1;
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) q[s][f] = Ps[(f * HY + hy) * HX + fx + s];
-                T F[NF];
-                weno_face<PX>(q, gamma, gx, F);
-#pragma unroll
-                for (int f = 0; f < NF; ++f) Fx[(f * TY + row) * (TX + 1) + fx] = F[f];
+                    for (int f = 0; f < NF; ++f) {
+                        const T* v = Ps + (f * HY + cy + WENO_G) * HX + col + WENO_G;
+                        T rv, lv;
+                        weno5z_pair(v[-2 * HX], v[-HX], v[0], v[HX], v[2 * HX], rv, lv);
+                        if (cy + 1 <= TY) QLy[(f * (TY + 1) + cy + 1) * TX + col] = rv;
+                        if (cy >= 0) QRy[(f * (TY + 1) + cy) * TX + col] = lv;
+                    }
+                }
             }
-            if (DIM >= 2) {
-                for (int e = tid; e < TX * (TY + 1); e += NT) {
-                    const int col = e % TX, fy = e / TX;
-                    T q[6][NF];
+            __syncthreads();
+            // the HLL flux of every x and y face of the plane
+            constexpr int NX = (TX + 1) * TY, NY = DIM >= 2 ? TX * (TY + 1) : 0;
+            for (int e = tid; e < NX + NY; e += NT) {
+                T qL[NF], qR[NF], F[NF];
+                if (e < NX) {
 #pragma unroll
-                    for (int s = 0; s < 6; ++s)
+                    for (int f = 0; f < NF; ++f) {
+                        qL[f] = QLx[f * NX + e];
+                        qR[f] = QRx[f * NX + e];
+                    }
+                    hll_face<PX>(qL, qR, gamma, gx, F);
 #pragma unroll
-                        for (int f = 0; f < NF; ++f)
-                            q[s][f] = Ps[(f * HY + fy + s) * HX + col + WENO_G];
-                    T F[NF];
-                    weno_face<PY>(q, gamma, gx, F);
+                    for (int f = 0; f < NF; ++f) Fx[f * NX + e] = F[f];
+                } else {
+                    const int e2 = e - NX;
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) Fy[(f * (TY + 1) + fy) * TX + col] = F[f];
+                    for (int f = 0; f < NF; ++f) {
+                        qL[f] = QLy[f * NY + e2];
+                        qR[f] = QRy[f * NY + e2];
+                    }
+                    hll_face<PY>(qL, qR, gamma, gx, F);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Fy[f * NY + e2] = F[f];
                 }
             }
             __syncthreads();
@@ -308,11 +396,20 @@ weno_stage_kernel(const StageArgs<T> A) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
 #pragma unroll
-                for (int s = 0; s < 5; ++s) w[s][f] = w[s + 1][f];
-                w[5][f] = qj[f];
+                for (int s = 0; s < 4; ++s) w[s][f] = w[s + 1][f];
+                w[4][f] = qj[f];
             }
+            // cell j-2 (planes j-4 .. j): its lower face value closes the face
+            // between j-3 and j-2; its upper value waits for the next plane
             T Fz[NF];
-            if (cnt >= 5) weno_face<2>(w, gamma, gx, Fz);    // face between j-3 and j-2
+            if (cnt >= 4) {
+                T qR[NF], up[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) weno5z_pair(w[0][f], w[1][f], w[2][f], w[3][f], w[4][f], up[f], qR[f]);
+                if (cnt >= 5) hll_face<2>(qLz, qR, gamma, gx, Fz);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) qLz[f] = up[f];
+            }
             k = cnt >= 6 ? j - WENO_G : -1;
             if (k >= 0) {
 #pragma unroll
