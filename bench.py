@@ -144,6 +144,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class nvtx_range:
+    """Names a region of launches for profilers (ncu --nvtx --nvtx-include
+    "<name>/"); a no-op where torch has no NVTX support."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        try:
+            import torch
+            torch.cuda.nvtx.range_push(self.name)
+            self.on = True
+        except Exception:
+            self.on = False
+        return self
+
+    def __exit__(self, *exc):
+        if self.on:
+            import torch
+            torch.cuda.nvtx.range_pop()
+        return False
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -371,10 +394,11 @@ def main():
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(dev.index)
     with ClockSampler(gpu_id) as clk:
         barrier()
-        ev0.record(stream)
-        advance(m32, U, args.steps, tot_log)
-        ev1.record(stream)
-        barrier()
+        with nvtx_range("whole_mesh_steps"):
+            ev0.record(stream)
+            advance(m32, U, args.steps, tot_log)
+            ev1.record(stream)
+            barrier()
     ms = rank_max(ev0.elapsed_time(ev1))
     value = whole_job_value(world, cells, 2 * args.steps, ms)
     status = m32.get_error()
@@ -382,6 +406,22 @@ def main():
     # kernels of this library launched in the timed region:
     # 1 signal rate + per step (finalize dt, stage 1, stage 2, finalize totals)
     launches = 1 + 4 * args.steps
+
+    # ---------------- the same step, stages blocked through L2 (z slabs) ----------------
+    slab = 2 * tuned["info"][2]                       # two z-chunks of the tuned tile per slab
+    m32.set_schedule(slab)
+    advance(m32, U, max(args.warmup, 3), tot_log)
+    barrier()
+    with nvtx_range("slab_steps"):
+        ev0.record(stream)
+        advance(m32, U, args.steps, tot_log)
+        ev1.record(stream)
+        barrier()
+    ms_slab = rank_max(ev0.elapsed_time(ev1))
+    m32.set_schedule(0)
+    slab_schedule = {"slab_planes": slab, "value": whole_job_value(world, cells, 2 * args.steps, ms_slab),
+                     "unit": UNIT, "ms_per_step": ms_slab / args.steps,
+                     "vs_whole_mesh_schedule": ms / ms_slab}
 
     # ---------------- stage kernel alone: roofline ----------------
     U1 = torch.empty_like(U)
@@ -652,6 +692,7 @@ def main():
                    "tile": {"chosen": tuned["info"], "ms_per_stage": tuned["ms"]},
                    "step": "CFL rate + stage 1 + stage 2 + FP64 totals"},
         "roofline": roofline,
+        "slab_schedule": slab_schedule,
         "weno5z_hll": weno,
         "rad_exchange": rad,
         "radiation_advection": advect,

@@ -69,6 +69,8 @@ __device__ __forceinline__ StageArgs<T> batch_stage_args(const BatchProblem& P, 
     A.dt_dev = nullptr;
     A.stage = stage;
     A.zchunk = 1;
+    A.zlo = 0;
+    A.zhi = 1;
     A.rate_slot = nullptr;
     A.tot_partial = nullptr;
     A.status = nullptr;

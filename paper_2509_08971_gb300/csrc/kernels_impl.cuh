@@ -42,6 +42,8 @@ StageArgs<T> make_args(const MeshDesc& m, const TileDesc& td, const StageCall& c
     A.dt_dev = c.dt_dev;
     A.stage = c.stage;
     A.zchunk = td.zc > 0 ? td.zc : 1;
+    A.zlo = m.dim == 3 ? c.zlo : 0;
+    A.zhi = m.dim == 3 ? (c.zhi < 0 ? m.n[2] : c.zhi) : 1;
     A.rate_slot = c.rate_slot;
     A.tot_partial = c.tot_partial;
     A.status = c.status;
@@ -53,7 +55,7 @@ template <int TX, int TY, int DIM, int PX, int PY>
 cudaError_t run_stage(const MeshDesc& m, const TileDesc& td, const StageCall& c, cudaStream_t s) {
     StageArgs<T> A = make_args(m, td, c);
     dim3 grid(cdiv(m.n[0], TX), DIM >= 2 ? cdiv(m.n[1], TY) : 1,
-              DIM == 3 ? cdiv(m.n[2], A.zchunk) : 1);
+              DIM == 3 ? cdiv(A.zhi - A.zlo, A.zchunk) : 1);
     const size_t smem = StageSmem<T, TX, TY, DIM>::bytes;
     auto kern = stage_kernel<T, TX, TY, DIM, PX, PY, false>;
     static bool attr = false;
@@ -135,7 +137,7 @@ cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall
             !encode_state_map(&maps.u0, c.stage == 2 ? c.U0 : c.Uc, m, TX, TY))
             return cudaSuccess;
         StageArgs<T> A = make_args(m, td, c);
-        dim3 grid(cdiv(m.n[0], TX), cdiv(m.n[1], TY), cdiv(m.n[2], A.zchunk));
+        dim3 grid(cdiv(m.n[0], TX), cdiv(m.n[1], TY), cdiv(A.zhi - A.zlo, A.zchunk));
         auto kern = c.stage == 1 ? stage_tma_kernel<T, TX, TY, 1> : stage_tma_kernel<T, TX, TY, 2>;
         constexpr size_t b1 = TmaLayout<T, TX, TY, 1>::bytes, b2 = L::bytes;
         static bool attr = false;

@@ -34,6 +34,8 @@ struct StageCall {
     unsigned long long* rate_slot; // nullptr = no rate epilogue
     double* tot_partial;           // nullptr = no totals epilogue
     int* status;
+    int zlo = 0, zhi = -1;         // 3D: the kernel-z cells [zlo, zhi) to update (-1: to nz);
+                                   // zlo a multiple of the tile's z-chunk
 };
 
 // Tile configurations per number of active axes (the autotuner's space).

@@ -39,6 +39,7 @@ struct StageArgs {
     const double* dt_dev;
     int stage;                    // 1 or 2
     int zchunk;
+    int zlo, zhi;                 // 3D: kernel-z cells [zlo, zhi) of this launch (zlo a multiple of zchunk)
     unsigned long long* rate_slot;    // epilogue max-rate (nullptr = off)
     double* tot_partial;              // epilogue totals [nblocks][5] (nullptr = off)
     int* status;                      // non-physical flag
@@ -279,8 +280,8 @@ stage_kernel(const StageArgs<T> A) {
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX;
     const int y0 = DIM >= 2 ? blockIdx.y * TY : 0;
-    const int z0 = DIM == 3 ? blockIdx.z * A.zchunk : 0;
-    const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.n[2]) : 1;
+    const int z0 = DIM == 3 ? A.zlo + blockIdx.z * A.zchunk : 0;
+    const int z1 = DIM == 3 ? min(z0 + A.zchunk, A.zhi) : 1;
     TileAcc<T> acc;
     acc.rate_max = T(0);
     acc.bad = false;
@@ -322,7 +323,8 @@ stage_kernel(const StageArgs<T> A) {
             atomicMax(A.rate_slot, b);
         }
         if (A.tot_partial) {
-            const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            const long long bz = DIM == 3 ? A.zlo / A.zchunk + blockIdx.z : blockIdx.z;
+            const long long blk = (bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             for (int f = 0; f < NF; ++f) {
                 double s = 0.0;
                 for (int w = 0; w < NT / 32; ++w) s += red_tot[w][f];

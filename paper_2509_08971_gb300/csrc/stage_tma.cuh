@@ -104,8 +104,8 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < nx && y < ny;
-    const int z0 = blockIdx.z * A.zchunk;
-    const int z1 = min(z0 + A.zchunk, nz);
+    const int z0 = A.zlo + blockIdx.z * A.zchunk;
+    const int z1 = min(z0 + A.zchunk, A.zhi);
     const int jbeg = z0 - 2;
     const int niter = (z1 + 2) - jbeg;
     // boundary tiles and their periodic strips (uniform over the CTA)
@@ -428,7 +428,8 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             atomicMax(A.rate_slot, b);
         }
         if (A.tot_partial) {
-            const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            const long long bz = A.zlo / A.zchunk + blockIdx.z;
+            const long long blk = (bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             for (int f = 0; f < NF; ++f) {
                 double s = 0.0;
                 for (int w = 0; w < NT / 32; ++w) s += red_tot[w][f];
