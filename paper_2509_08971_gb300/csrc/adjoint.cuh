@@ -41,6 +41,14 @@ __device__ __forceinline__ void accumulate_cell(double* rec, const double v[NF])
     for (int f = 0; f < NF; ++f) atomicAdd(rec + f, v[f]);
 }
 
+// Division and square root of the adjoint: FP64 exact IEEE operations (the
+// order of the formulas below is the oracle transcription's); FP32 through the
+// approximate reciprocal and square root that the FP32 forward stage uses.
+__device__ __forceinline__ double adiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float adiv(float a, float b) { return a * vrcp(b); }
+__device__ __forceinline__ double asqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float asqrt(float a) { return vsqrt(a); }
+
 template <typename T>
 struct AdjArgs {
     const T* Uc;          // state the flux difference is taken of
@@ -70,7 +78,7 @@ __device__ __forceinline__ void flux_vjp(const T W[NF], T gamma, const T Fb[NF],
                                          T& Eb) {
     const T r = W[0], u = W[1], v = W[2], w = W[3], p = W[4];
     const T g1 = gamma - T(1);
-    const T E = p / g1 + T(0.5) * r * (u * u + v * v + w * w);
+    const T E = adiv(p, g1) + T(0.5) * r * (u * u + v * v + w * w);
     Wb[0] += Fb[0] * u + Fb[1] * u * u + Fb[2] * u * v + Fb[3] * u * w;
     Wb[1] += Fb[0] * r + Fb[1] * T(2) * r * u + Fb[2] * r * v + Fb[3] * r * w + Fb[4] * (E + p);
     Wb[2] += Fb[2] * r * u;
@@ -88,18 +96,18 @@ __device__ __forceinline__ void energy_vjp(const T W[NF], T gamma, T Eb, T Wb[NF
     Wb[1] += Eb * r * u;
     Wb[2] += Eb * r * v;
     Wb[3] += Eb * r * w;
-    Wb[4] += Eb / g1;
-    gb -= Eb * p / (g1 * g1);
+    Wb[4] += adiv(Eb, g1);
+    gb -= adiv(Eb * p, g1 * g1);
 }
 
 // Reverse of c = sqrt(gamma p / r).
 template <typename T>
 __device__ __forceinline__ void sound_vjp(const T W[NF], T gamma, T c, T cb, T Wb[NF], T& gb) {
     const T r = W[0], p = W[4];
-    const T zb = cb / (T(2) * c);            // z = gamma p / r
-    gb += zb * p / r;
-    Wb[4] += zb * gamma / r;
-    Wb[0] -= zb * gamma * p / (r * r);
+    const T zb = adiv(cb, T(2) * c);         // z = gamma p / r
+    gb += adiv(zb * p, r);
+    Wb[4] += adiv(zb * gamma, r);
+    Wb[0] -= adiv(zb * gamma * p, r * r);
 }
 
 // HLLC on rotated states (normal along slot 1): recompute the forward pass,
@@ -112,7 +120,7 @@ __device__ void hllc_vjp(const T WL[NF], const T WR[NF], T gamma, const T Fb[NF]
     const T g1 = gamma - T(1);
     const T rL = WL[0], uL = WL[1], pL = WL[4];
     const T rR = WR[0], uR = WR[1], pR = WR[4];
-    const T cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+    const T cL = asqrt(adiv(gamma * pL, rL)), cR = asqrt(adiv(gamma * pR, rR));
     const T aL = uL - cL, aR = uR - cR, bL = uL + cL, bR = uR + cR;
     const bool minL = aL <= aR, maxL = bL >= bR;     // which side set S_L / S_R
     const T SL = minL ? aL : aR;
@@ -131,20 +139,20 @@ __device__ void hllc_vjp(const T WL[NF], const T WR[NF], T gamma, const T Fb[NF]
     const T mL = rL * (SL - uL), mR = rR * (SR - uR);
     const T num = pR - pL + mL * uL - mR * uR;
     const T den = mL - mR;
-    const T Ss = num / den;
+    const T Ss = adiv(num, den);
     const bool left = Ss >= T(0);
     const T* WK = left ? WL : WR;
     T* WKb = left ? WLb : WRb;
     const T rK = WK[0], uK = WK[1], vK = WK[2], wK = WK[3], pK = WK[4];
-    const T EK = pK / g1 + T(0.5) * rK * (uK * uK + vK * vK + wK * wK);
+    const T EK = adiv(pK, g1) + T(0.5) * rK * (uK * uK + vK * vK + wK * wK);
     const T SK = left ? SL : SR;
     const T mK = left ? mL : mR;
     const T D = SK - Ss;
-    const T fac = mK / D;
+    const T fac = adiv(mK, D);
     const T A = Ss - uK;
-    const T q = pK / mK;
+    const T q = adiv(pK, mK);
     const T Bq = Ss + q;
-    const T es = EK / rK + A * Bq;
+    const T es = adiv(EK, rK) + A * Bq;
     const T Us[NF] = {fac, fac * Ss, fac * vK, fac * wK, fac * es};
     const T UK[NF] = {rK, rK * uK, rK * vK, rK * wK, EK};
     // F = F_K + S_K (U* - U_K)
@@ -165,22 +173,22 @@ __device__ void hllc_vjp(const T WL[NF], const T WR[NF], T gamma, const T Fb[NF]
     WKb[3] += SK * Fb[3] * fac;
     const T esb = SK * Fb[4] * fac;
     // es = E/r + A Bq
-    EKb += esb / rK;
-    WKb[0] -= esb * EK / (rK * rK);
+    EKb += adiv(esb, rK);
+    WKb[0] -= adiv(esb * EK, rK * rK);
     const T Ab = esb * Bq, Bqb = esb * A;
     Ssb += Bqb;                                      // Bq = S* + q
-    WKb[4] += Bqb / mK;                              // q = p / m
-    mKb -= Bqb * pK / (mK * mK);
+    WKb[4] += adiv(Bqb, mK);                         // q = p / m
+    mKb -= adiv(Bqb * pK, mK * mK);
     Ssb += Ab;                                       // A = S* - u
     WKb[1] -= Ab;
-    mKb += facb / D;                                 // fac = m / D
-    const T Db = -facb * mK / (D * D);
+    mKb += adiv(facb, D);                            // fac = m / D
+    const T Db = adiv(-facb * mK, D * D);
     SKb += Db;                                       // D = S_K - S*
     Ssb -= Db;
     energy_vjp(WK, gamma, EKb, WKb, gb);
     // S* = num / den
-    const T numb = Ssb / den;
-    const T denb = -Ssb * Ss / den;
+    const T numb = adiv(Ssb, den);
+    const T denb = adiv(-Ssb * Ss, den);
     T mLb = denb + numb * uL + (left ? mKb : T(0));
     T mRb = -denb - numb * uR + (left ? T(0) : mKb);
     WRb[4] += numb;
@@ -275,23 +283,35 @@ __device__ __forceinline__ void face_vjp_one(const AdjArgs<T>& A, const int c3[3
     }
 }
 
-// All faces of a stage in one launch.  The index space is the cell grid
-// extended by one along every active axis, x fastest (coalesced): the point
-// (i0, i1, i2) owns the x face left of cell (i0, i1, i2) when i1, i2 are in
-// range, the y face below it when i0, i2 are, and the z face when i0, i1 are.
+// All faces of a stage in one launch, one thread per face.  The index space
+// is DIM copies (one per axis, axis slowest, so that a warp evaluates faces
+// of one axis) of the cell grid extended by one along every active axis, x
+// fastest (coalesced): the point (i0, i1, i2) of copy d owns the face of axis
+// d on the low side of cell (i0, i1, i2) when the other two indices are in
+// range.
+// 128-thread blocks, seven per SM (72 registers in FP32): every face of a
+// 256^2 mesh is resident at once, so the launch takes one pass of the VJP's
+// long dependency chain instead of two.
+constexpr int FACES_VJP_THREADS = 128;
 template <typename T, int DIM, int PX, int PY>
-__global__ void __launch_bounds__(256) faces_vjp_kernel(const AdjArgs<T> A) {
+__global__ void __launch_bounds__(FACES_VJP_THREADS, 7) faces_vjp_kernel(const AdjArgs<T> A) {
     const int e0 = A.n[0] + 1, e1 = DIM >= 2 ? A.n[1] + 1 : 1, e2 = DIM >= 3 ? A.n[2] + 1 : 1;
     const long long total = (long long)e0 * e1 * e2;
     double gacc = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < DIM * total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int axis = (int)(g / total);
+        const long long e = g - axis * total;
         const int c3[3] = {(int)(e % e0), (int)((e / e0) % e1), (int)(e / ((long long)e0 * e1))};
         const bool in0 = c3[0] < A.n[0], in1 = DIM < 2 || c3[1] < A.n[1];
         const bool in2 = DIM < 3 || c3[2] < A.n[2];
-        if (in1 && in2) face_vjp_one<T, 0, PX>(A, c3, gacc);
-        if (DIM >= 2 && in0 && in2) face_vjp_one<T, 1, PY>(A, c3, gacc);
-        if (DIM >= 3 && in0 && in1) face_vjp_one<T, 2, 2>(A, c3, gacc);
+        if (axis == 0) {
+            if (in1 && in2) face_vjp_one<T, 0, PX>(A, c3, gacc);
+        } else if (axis == 1) {
+            if (DIM >= 2 && in0 && in2) face_vjp_one<T, 1, PY>(A, c3, gacc);
+        } else {
+            if (DIM >= 3 && in0 && in1) face_vjp_one<T, 2, 2>(A, c3, gacc);
+        }
     }
     // block sum of the explicit d/dgamma, one atomic per block
     __shared__ double red[8];
@@ -333,13 +353,13 @@ __global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, T* gW, const
         cons_to_prim(U, g1, W);
         const T r = W[0], u = W[1], v = W[2], w = W[3];
         T Ub[NF];
-        Ub[1] = Wb[1] / r - Wb[4] * g1 * u;
-        Ub[2] = Wb[2] / r - Wb[4] * g1 * v;
-        Ub[3] = Wb[3] / r - Wb[4] * g1 * w;
+        Ub[1] = adiv(Wb[1], r) - Wb[4] * g1 * u;
+        Ub[2] = adiv(Wb[2], r) - Wb[4] * g1 * v;
+        Ub[3] = adiv(Wb[3], r) - Wb[4] * g1 * w;
         Ub[4] = Wb[4] * g1;
-        Ub[0] = Wb[0] - (Wb[1] * u + Wb[2] * v + Wb[3] * w) / r +
+        Ub[0] = Wb[0] - adiv(Wb[1] * u + Wb[2] * v + Wb[3] * w, r) +
                 Wb[4] * g1 * T(0.5) * (u * u + v * v + w * w);
-        gacc += (double)(Wb[4] * W[4] / g1);
+        gacc += (double)adiv(Wb[4] * W[4], g1);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const T gf = G[f * N + c];

@@ -326,11 +326,11 @@ AdjArgs<T> make_adj(const MeshDesc& m, const AdjointCall& c) {
 
 template <int DIM, int PX, int PY>
 cudaError_t run_faces_vjp(const AdjArgs<T>& A, int dim, cudaStream_t s) {
-    long long total = (long long)(A.n[0] + 1) * (dim >= 2 ? A.n[1] + 1 : 1) *
-                      (dim >= 3 ? A.n[2] + 1 : 1);
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    faces_vjp_kernel<T, DIM, PX, PY><<<(int)blocks, 256, 0, s>>>(A);
+    long long total = (long long)DIM * (A.n[0] + 1) * (dim >= 2 ? A.n[1] + 1 : 1) *
+                      (dim >= 3 ? A.n[2] + 1 : 1);     // one thread per face
+    long long blocks = (total + FACES_VJP_THREADS - 1) / FACES_VJP_THREADS;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    faces_vjp_kernel<T, DIM, PX, PY><<<(int)blocks, FACES_VJP_THREADS, 0, s>>>(A);
     return cudaGetLastError();
 }
 

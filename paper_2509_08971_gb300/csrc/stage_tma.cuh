@@ -47,17 +47,18 @@ struct TmaLayout {
     static constexpr int NP = NF * HYP * HXP;           // one primitive plane
     static constexpr int NFX = NF * TY * (TX + 1);      // one plane of x-face fluxes
     static constexpr int NFY = NF * (TY + 1) * TX;      // one plane of y-face fluxes
-    // the primitive and face-flux planes are double-buffered by plane parity
+    // one primitive plane and one plane of x / y face fluxes (see the barrier
+    // comment in the kernel for why one of each suffices)
     static constexpr size_t BAR_BYTES = 128;            // D mbarriers, then the ring
     static constexpr size_t RED_BYTES = (TX * TY / 32) * (NF + 1) * 8;
     static constexpr size_t data_bytes =
-        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NU0 * U0S + 2 * (NP + NFX + NFY)) + RED_BYTES;
+        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NU0 * U0S + NP + NFX + NFY) + RED_BYTES;
     static constexpr size_t bytes = data_bytes + 128;   // slack to align the base by hand
     static constexpr uint32_t MAIN_BYTES = sizeof(T) * NF * HYC * HXC;
     static constexpr uint32_t XS_BYTES = sizeof(T) * NF * HYC * 4;
     static constexpr uint32_t YS_BYTES = sizeof(T) * NF * 2 * HXC;
     static constexpr size_t RED_OFF =
-        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NU0 * U0S + 2 * (NP + NFX + NFY));
+        BAR_BYTES + sizeof(T) * (size_t(D) * SLOT + NU0 * U0S + NP + NFX + NFY);
     static_assert((U0S * sizeof(T)) % 128 == 0, "U0 slots must start on 128-byte boundaries");
     static_assert((SLOT * sizeof(T)) % 128 == 0 && (XLO * sizeof(T)) % 128 == 0 &&
                   (XHI * sizeof(T)) % 128 == 0 && (YLO * sizeof(T)) % 128 == 0 &&
@@ -91,10 +92,10 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     static_assert(8 * D + 2 * sizeof(int) <= L::BAR_BYTES, "barrier block too small");
     T* ring = reinterpret_cast<T*>(base + L::BAR_BYTES);
     T* u0s = ring + D * L::SLOT;                      // NU0 x [NF][TY][TX]
-    T* Ps2 = u0s + L::NU0 * L::U0S;                   // 2 x [NF][HYP][HXP]
-    T* Fx2 = Ps2 + 2 * L::NP;                         // 2 x [NF][TY][TX+1]
-    T* Fy2 = Fx2 + 2 * L::NFX;                        // 2 x [NF][TY+1][TX]
-    double (*red_tot)[NF] = reinterpret_cast<double (*)[NF]>(Fy2 + 2 * L::NFY);
+    T* Ps = u0s + L::NU0 * L::U0S;                    // [NF][HYP][HXP]
+    T* Fx = Ps + L::NP;                               // [NF][TY][TX+1]
+    T* Fy = Fx + L::NFX;                              // [NF][TY+1][TX]
+    double (*red_tot)[NF] = reinterpret_cast<double (*)[NF]>(Fy + L::NFY);
     unsigned long long* red_rate =
         reinterpret_cast<unsigned long long*>(reinterpret_cast<double*>(red_tot) + (NT / 32) * NF);
 
@@ -209,15 +210,15 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
 
     // Barriers: two per plane.  Barrier A (the plane's primitives are in shared
     // memory) also marks every thread done with iteration it-1, which frees
-    // the ring slot that the next load overwrites; the primitive and flux
-    // planes alternate by parity, so a new plane never overwrites one that a
-    // slower thread may still be reading.
+    // the ring slot that the next load overwrites.  One primitive plane and
+    // one flux plane suffice: the primitives of a plane are read only between
+    // its barriers A and B, and a thread writes the next plane's primitives
+    // after barrier B; the fluxes are read after barrier B, and the next
+    // plane's are written after the next barrier A, which no thread passes
+    // before every thread has finished reading them.
     int it = 0;
     for (; it < niter; ++it) {
         const int j = jbeg + it;
-        T* Ps = Ps2 + (it & 1) * L::NP;
-        T* Fx = Fx2 + (it & 1) * L::NFX;
-        T* Fy = Fy2 + (it & 1) * L::NFY;
         const bool upd = it >= 4 && own;              // completes cell j - 2 (z0 at it = 4)
         if (!mbar_wait(bars + (it % D), (uint32_t)((it / D) & 1))) {
             atomicOr(A.status, 4);
@@ -226,6 +227,28 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         const T* S = slot_main(it);
         const bool xy = j >= z0 && j < z1;
         T qj[NF], Dj[NF], Fown_x[NF], Fown_y[NF];
+        // z direction: streaming stencil of this column.  It needs only this
+        // cell's primitives, so it runs before the x / y faces, in the same
+        // stretch between the barriers, where its work fills in for warps that
+        // wait for the edge faces.
+        T Fz[NF] = {T(0), T(0), T(0), T(0), T(0)};
+        T dcur[NF];
+        auto zstep = [&]() {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) dcur[f] = qj[f] - qm1[f];
+            if (it >= 2) {
+                T qL[NF], qR[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T d = minmod(dprev[f], dcur[f]);
+                    qR[f] = madd(T(-0.5), d, qm1[f]);
+                    qL[f] = madd(T(0.5), d, qm1[f]);
+                }
+                if (it >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, igm1, Fz);  // face j-3/2
+#pragma unroll
+                for (int f = 0; f < NF; ++f) qLp[f] = qL[f];
+            }
+        };
         if (xy) {
             // conserved -> primitive over the haloed (TX+4) x (TY+4) plane
             if (!edge) {
@@ -269,6 +292,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             // this thread's own cell: shared by its x face, its y face and the z stencil
 #pragma unroll
             for (int f = 0; f < NF; ++f) qj[f] = Ps[(f * HYP + ty + 2) * HXP + tx + 2];
+            zstep();
             // the x face left of the cell and the y face below it
             T q[4][NF], F[NF];
 #pragma unroll
@@ -334,25 +358,9 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             __syncthreads();                          // barrier A of a column-only plane
             if (s_abort[it & 1]) break;
             if (tid == 0 && it + P < niter) issue(it + P);
+            zstep();
         }
 
-        // z direction: streaming stencil of this column
-        T Fz[NF] = {T(0), T(0), T(0), T(0), T(0)};
-        T dcur[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) dcur[f] = qj[f] - qm1[f];
-        if (it >= 2) {
-            T qL[NF], qR[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const T d = minmod(dprev[f], dcur[f]);
-                qR[f] = madd(T(-0.5), d, qm1[f]);
-                qL[f] = madd(T(0.5), d, qm1[f]);
-            }
-            if (it >= 3) hllc_axis<2>(qLp, qR, gamma, gm1, igm1, Fz);      // face j-3/2
-#pragma unroll
-            for (int f = 0; f < NF; ++f) qLp[f] = qL[f];
-        }
         if (upd) {
             const T* Sk = slot_main(it - 2);
             T Uo[NF];
