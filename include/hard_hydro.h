@@ -268,7 +268,10 @@ int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, doub
  * minmod and the Davis min/max pass the cotangent to the argument they
  * selected (subgradients).  gU_in may alias gU_out.  Summation into the
  * cotangents uses device atomics, so results agree to rounding, not bitwise,
- * from run to run.  Device pointers, 16-byte aligned; asynchronous. */
+ * from run to run.  Device pointers, 16-byte aligned; asynchronous.  Faces
+ * are indexed in 32 bits: a mesh with (number of active axes) x
+ * prod_d (n_d + 1) >= 2^31 (about 7e8 cells in 3D) returns
+ * HARD_EUNSUPPORTED. */
 int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_out, void* gU_in,
                              double dt, double* g_gamma, void* stream);
 

@@ -211,6 +211,53 @@ __device__ void hllc_vjp(const T WL[NF], const T WR[NF], T gamma, const T Fb[NF]
     sound_vjp(WR, gamma, cR, cRb, WRb, gb);
 }
 
+// The reverse of one face's flux along physical axis PA: from the primitives
+// q of its four stencil cells (boundary map and reflections applied), the
+// lambdas of the two cells it separates (zero for a cell outside the mesh)
+// and the kernel-axis width parameter, the cotangents qb of the four stencil
+// primitives (reflections not yet undone) and the face's explicit d/dgamma.
+template <typename T, int PA>
+__device__ __forceinline__ void face_vjp_core(const T q[4][NF], const T ll[NF], const T lr[NF],
+                                              T dxk, T gamma, T qb[4][NF], T& gb) {
+    using R = Rot<PA>;
+    // face flux cotangent (lambda_m - lambda_{m-1}) / dx
+    T Fb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) Fb[f] = sub_over_dx(T(0), ll[f] - lr[f], dxk);
+    // forward face states, remembering the minmod selections
+    T qL[NF], qR[NF];
+    int s1[NF], s2[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const T d0 = q[1][f] - q[0][f], d1 = q[2][f] - q[1][f], d2 = q[3][f] - q[2][f];
+        s1[f] = minmod_sel(d0, d1);
+        s2[f] = minmod_sel(d1, d2);
+        const T m1 = s1[f] == 1 ? d0 : (s1[f] == 2 ? d1 : T(0));
+        const T m2 = s2[f] == 1 ? d1 : (s2[f] == 2 ? d2 : T(0));
+        qL[f] = madd(T(0.5), m1, q[1][f]);
+        qR[f] = madd(T(-0.5), m2, q[2][f]);
+    }
+    const T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
+    const T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
+    const T Fn_b[NF] = {Fb[0], Fb[R::n], Fb[R::t1], Fb[R::t2], Fb[4]};
+    T WLb[NF], WRb[NF];
+    gb = T(0);
+    hllc_vjp(WL, WR, gamma, Fn_b, WLb, WRb, gb);
+    T qLb[NF], qRb[NF];
+    qLb[0] = WLb[0]; qLb[R::n] = WLb[1]; qLb[R::t1] = WLb[2]; qLb[R::t2] = WLb[3]; qLb[4] = WLb[4];
+    qRb[0] = WRb[0]; qRb[R::n] = WRb[1]; qRb[R::t1] = WRb[2]; qRb[R::t2] = WRb[3]; qRb[4] = WRb[4];
+    // face states backwards onto the four stencil primitives
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        qb[0][f] = T(0); qb[1][f] = qLb[f]; qb[2][f] = qRb[f]; qb[3][f] = T(0);
+        const T s1b = T(0.5) * qLb[f], s2b = T(-0.5) * qRb[f];
+        if (s1[f] == 1) { qb[1][f] += s1b; qb[0][f] -= s1b; }
+        if (s1[f] == 2) { qb[2][f] += s1b; qb[1][f] -= s1b; }
+        if (s2[f] == 1) { qb[2][f] += s2b; qb[1][f] -= s2b; }
+        if (s2[f] == 2) { qb[3][f] += s2b; qb[2][f] -= s2b; }
+    }
+}
+
 // The reverse of one face's contribution to L: the face between cells m-1
 // and m along kernel axis KA (physical axis PA), at transverse coordinates
 // c3 (c3[KA] = m), scattered onto its four stencil cells.
@@ -233,47 +280,15 @@ __device__ __forceinline__ void face_vjp_one(const AdjArgs<T>& A, const int c3[3
         if (flip[s]) U[R::n] = -U[R::n];
         cons_to_prim(U, A.gm1, q[s]);
     }
-    // face flux cotangent from the two neighbouring cells' lambda
-    T Fb[NF];
+    T ll[NF], lr[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        const T lr = m < na ? A.lam * A.gout[f * A.N + src[2]] : T(0);
-        const T ll = m > 0 ? A.lam * A.gout[f * A.N + src[1]] : T(0);
-        Fb[f] = sub_over_dx(T(0), ll - lr, A.dxk[KA]);   // (lambda_m - lambda_{m-1}) / dx
+        lr[f] = m < na ? A.lam * A.gout[f * A.N + src[2]] : T(0);
+        ll[f] = m > 0 ? A.lam * A.gout[f * A.N + src[1]] : T(0);
     }
-    // forward face states, remembering the minmod selections
-    T qL[NF], qR[NF];
-    int s1[NF], s2[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        const T d0 = q[1][f] - q[0][f], d1 = q[2][f] - q[1][f], d2 = q[3][f] - q[2][f];
-        s1[f] = minmod_sel(d0, d1);
-        s2[f] = minmod_sel(d1, d2);
-        const T m1 = s1[f] == 1 ? d0 : (s1[f] == 2 ? d1 : T(0));
-        const T m2 = s2[f] == 1 ? d1 : (s2[f] == 2 ? d2 : T(0));
-        qL[f] = madd(T(0.5), m1, q[1][f]);
-        qR[f] = madd(T(-0.5), m2, q[2][f]);
-    }
-    const T WL[NF] = {qL[0], qL[R::n], qL[R::t1], qL[R::t2], qL[4]};
-    const T WR[NF] = {qR[0], qR[R::n], qR[R::t1], qR[R::t2], qR[4]};
-    const T Fn_b[NF] = {Fb[0], Fb[R::n], Fb[R::t1], Fb[R::t2], Fb[4]};
-    T WLb[NF], WRb[NF], gb = T(0);
-    hllc_vjp(WL, WR, A.gamma, Fn_b, WLb, WRb, gb);
+    T qb[4][NF], gb;
+    face_vjp_core<T, PA>(q, ll, lr, A.dxk[KA], A.gamma, qb, gb);
     gacc += (double)gb;
-    T qLb[NF], qRb[NF];
-    qLb[0] = WLb[0]; qLb[R::n] = WLb[1]; qLb[R::t1] = WLb[2]; qLb[R::t2] = WLb[3]; qLb[4] = WLb[4];
-    qRb[0] = WRb[0]; qRb[R::n] = WRb[1]; qRb[R::t1] = WRb[2]; qRb[R::t2] = WRb[3]; qRb[4] = WRb[4];
-    // face states backwards onto the four stencil primitives
-    T qb[4][NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        qb[0][f] = T(0); qb[1][f] = qLb[f]; qb[2][f] = qRb[f]; qb[3][f] = T(0);
-        const T s1b = T(0.5) * qLb[f], s2b = T(-0.5) * qRb[f];
-        if (s1[f] == 1) { qb[1][f] += s1b; qb[0][f] -= s1b; }
-        if (s1[f] == 2) { qb[2][f] += s1b; qb[1][f] -= s1b; }
-        if (s2[f] == 1) { qb[2][f] += s2b; qb[1][f] -= s2b; }
-        if (s2[f] == 2) { qb[3][f] += s2b; qb[2][f] -= s2b; }
-    }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         if (flip[s]) qb[s][R::n] = -qb[s][R::n];
@@ -295,14 +310,16 @@ __device__ __forceinline__ void face_vjp_one(const AdjArgs<T>& A, const int c3[3
 constexpr int FACES_VJP_THREADS = 128;
 template <typename T, int DIM, int PX, int PY>
 __global__ void __launch_bounds__(FACES_VJP_THREADS, 7) faces_vjp_kernel(const AdjArgs<T> A) {
-    const int e0 = A.n[0] + 1, e1 = DIM >= 2 ? A.n[1] + 1 : 1, e2 = DIM >= 3 ? A.n[2] + 1 : 1;
-    const long long total = (long long)e0 * e1 * e2;
+    // 32-bit index arithmetic (the launcher keeps DIM * total below 2^31)
+    const unsigned e0 = A.n[0] + 1, e1 = DIM >= 2 ? A.n[1] + 1 : 1, e2 = DIM >= 3 ? A.n[2] + 1 : 1;
+    const unsigned total = e0 * e1 * e2;
     double gacc = 0.0;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < DIM * total;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int axis = (int)(g / total);
-        const long long e = g - axis * total;
-        const int c3[3] = {(int)(e % e0), (int)((e / e0) % e1), (int)(e / ((long long)e0 * e1))};
+    for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < DIM * total;
+         g += gridDim.x * blockDim.x) {
+        const unsigned axis = g / total;
+        const unsigned e = g - axis * total;
+        const unsigned row = e / e0;
+        const int c3[3] = {(int)(e - row * e0), (int)(row % e1), (int)(row / e1)};
         const bool in0 = c3[0] < A.n[0], in1 = DIM < 2 || c3[1] < A.n[1];
         const bool in2 = DIM < 3 || c3[2] < A.n[2];
         if (axis == 0) {
@@ -340,11 +357,15 @@ __global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, T* gW, const
     const T g1 = gamma - T(1);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
-        T U[NF], W[NF], Wb[NF];
+        // every load first (the stores below could alias them as far as the
+        // compiler knows), so that the cell takes one round trip to memory
+        T U[NF], W[NF], Wb[NF], Gc[NF], Oc[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             U[f] = Uc[f * N + c];
             Wb[f] = gW[c * GW_STRIDE + f];
+            Gc[f] = G[f * N + c];
+            Oc[f] = accumulate ? out_c[f * N + c] : T(0);
         }
         if (clear_gW) {
 #pragma unroll
@@ -362,10 +383,9 @@ __global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, T* gW, const
         gacc += (double)adiv(Wb[4] * W[4], g1);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const T gf = G[f * N + c];
-            const T val = b * gf + Ub[f];
-            out_c[f * N + c] = accumulate ? out_c[f * N + c] + val : val;
-            if (out0) out0[f * N + c] = a * gf;
+            const T val = b * Gc[f] + Ub[f];
+            out_c[f * N + c] = accumulate ? Oc[f] + val : val;
+            if (out0) out0[f * N + c] = a * Gc[f];
         }
     }
     __shared__ double red[8];

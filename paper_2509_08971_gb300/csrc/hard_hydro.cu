@@ -580,6 +580,12 @@ int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_ou
     if (!aligned16(U_in) || !aligned16(gU_out) || !aligned16(gU_in)) return HARD_EINVAL;
     if (weno(h)) return HARD_EUNSUPPORTED;
     if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    {
+        // the face VJP kernel indexes faces in 32 bits
+        long long faces = h->mesh.dim;
+        for (int k = 0; k < 3; ++k) faces *= (long long)h->mesh.n[k] + (k < h->mesh.dim ? 1 : 0);
+        if (faces >= (1ll << 31)) return HARD_EUNSUPPORTED;
+    }
     int rc = ensure_U1(h);
     if (rc) return rc;
     // adjoint scratch: the primitive cotangent accumulator (8 slots per cell,

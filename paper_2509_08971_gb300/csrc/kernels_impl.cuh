@@ -328,6 +328,7 @@ template <int DIM, int PX, int PY>
 cudaError_t run_faces_vjp(const AdjArgs<T>& A, int dim, cudaStream_t s) {
     long long total = (long long)DIM * (A.n[0] + 1) * (dim >= 2 ? A.n[1] + 1 : 1) *
                       (dim >= 3 ? A.n[2] + 1 : 1);     // one thread per face
+    if (total >= (1ll << 31)) return cudaErrorInvalidValue;   // 32-bit face indices
     long long blocks = (total + FACES_VJP_THREADS - 1) / FACES_VJP_THREADS;
     if (blocks > 152 * 32) blocks = 152 * 32;
     faces_vjp_kernel<T, DIM, PX, PY><<<(int)blocks, FACES_VJP_THREADS, 0, s>>>(A);

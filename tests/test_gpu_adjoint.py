@@ -38,7 +38,10 @@ def rel_err(a, b):
 
 
 CASES = [((1, 1, 40), (1,) * 6), ((1, 16, 16), (0,) * 6), ((1, 12, 20), (1,) * 6),
-         ((1, 14, 10), (2,) * 6), ((5, 6, 7), (0,) * 6), ((4, 5, 6), (2, 1, 0, 0, 1, 2))]
+         ((1, 14, 10), (2,) * 6), ((5, 6, 7), (0,) * 6), ((4, 5, 6), (2, 1, 0, 0, 1, 2)),
+         # several tiles of the fused 1D / 2D kernel, ragged edges, each boundary kind
+         ((1, 40, 70), (0,) * 6), ((1, 19, 45), (2, 2, 1, 1, 0, 0)),
+         ((1, 24, 33), (0, 0, 2, 2, 0, 0)), ((1, 1, 300), (0,) * 6), ((1, 35, 1), (2,) * 6)]
 
 
 @pytest.mark.parametrize("shape,bc6", CASES)
