@@ -122,7 +122,18 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     const T dt = (T)(A.dt_dev ? *A.dt_dev : A.dt);
     const T gamma = A.gamma, gm1 = A.gm1, igm1 = A.igm1;
     constexpr int NPF = HXP * HYP;                    // one field of the primitive plane
-    constexpr int MAXE = (NPF + NT - 1) / NT;         // plane cells converted per thread
+    // Work split per plane.  The first EW warps evaluate the TX+TY faces on
+    // the tile's top and right edges beside their own x and y faces, and
+    // their z face after barrier B; the other NC threads evaluate their z
+    // face before barrier B and convert the primitive plane.  Each warp then
+    // evaluates three faces between the barriers, and the edge warps' z face
+    // stands against the conversion after barrier B.
+    constexpr int EW = (TX + TY + 31) / 32;           // edge warps
+    constexpr int NC = NT - 32 * EW;                  // converting threads
+    static_assert(NC >= 32, "tile too small for the edge-warp split");
+    constexpr int MAXE = (NPF + NC - 1) / NC;         // plane cells converted per thread
+    const bool edge_warp = tid < 32 * EW;             // warp-uniform
+    const int ct = tid - 32 * EW;                     // conversion thread index
 
     auto slot_main = [&](int it) { return ring + (it % D) * L::SLOT; };
     auto issue = [&](int it) {
@@ -167,7 +178,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
     int cv[MAXE];
 #pragma unroll
     for (int q = 0; q < MAXE; ++q) {
-        const int e = tid + q * NT;
+        const int e = edge_warp ? 0 : ct + q * NC;
         const int cx = e % HXP - 2, cy = e / HXP - 2;
         int src = (cy + 2) * HXC + cx + 4, fs = HYC * HXC, flip = 0;
         if (edge) {
@@ -228,9 +239,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         const bool xy = j >= z0 && j < z1;
         T qj[NF], Dj[NF], Fown_x[NF], Fown_y[NF];
         // z direction: streaming stencil of this column.  It needs only this
-        // cell's primitives, so it runs before the x / y faces, in the same
-        // stretch between the barriers, where its work fills in for warps that
-        // wait for the edge faces.
+        // cell's primitives (the work split above says where it runs).
         T Fz[NF] = {T(0), T(0), T(0), T(0), T(0)};
         T dcur[NF];
         auto zstep = [&]() {
@@ -255,8 +264,8 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                 // interior tile: every plane cell is in the main box
 #pragma unroll
                 for (int q = 0; q < MAXE; ++q) {
-                    const int e = tid + q * NT;
-                    if (q == MAXE - 1 && e >= NPF) break;
+                    const int e = ct + q * NC;
+                    if (edge_warp || e >= NPF) break;
                     T U[NF], W[NF];
                     const T* src = S + cv[q];
 #pragma unroll
@@ -268,8 +277,8 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             } else {
 #pragma unroll
                 for (int q = 0; q < MAXE; ++q) {
-                    const int e = tid + q * NT;
-                    if (q == MAXE - 1 && e >= NPF) break;
+                    const int e = ct + q * NC;
+                    if (edge_warp || e >= NPF) break;
                     T U[NF], W[NF];
                     const int off = cv[q] & 0xFFFF, fs = (cv[q] >> 16) & 0xFFF;
                     if (off != 0xFFFF) {
@@ -292,7 +301,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             // this thread's own cell: shared by its x face, its y face and the z stencil
 #pragma unroll
             for (int f = 0; f < NF; ++f) qj[f] = Ps[(f * HYP + ty + 2) * HXP + tx + 2];
-            zstep();
+            if (!edge_warp) zstep();
             // the x face left of the cell and the y face below it
             T q[4][NF], F[NF];
 #pragma unroll
@@ -336,6 +345,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             };
             if (tid < TX + TY) edge_face(tid);
             __syncthreads();                          // barrier B: every face of the plane
+            if (edge_warp) zstep();
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fown_x[f];
