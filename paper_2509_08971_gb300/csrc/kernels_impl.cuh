@@ -2,6 +2,8 @@
 // their launchers.  Included by exactly one translation unit per type with
 // HH_T defined (float or double) and HH_SUFFIX (f32 or f64).
 #pragma once
+#include <cstdlib>
+
 #include "adjoint.cuh"
 #include "batched.cuh"
 #include "launch.h"
@@ -48,6 +50,7 @@ StageArgs<T> make_args(const MeshDesc& m, const TileDesc& td, const StageCall& c
     A.tot_partial = c.tot_partial;
     A.status = c.status;
     A.tmap = nullptr;
+    A.starve_tma = false;
     return A;
 }
 
@@ -137,6 +140,10 @@ cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall
             !encode_state_map(&maps.u0, c.stage == 2 ? c.U0 : c.Uc, m, TX, TY))
             return cudaSuccess;
         StageArgs<T> A = make_args(m, td, c);
+        // failure-path test: HARD_HYDRO_STARVE_TMA=1 makes the ring's waits
+        // run out (the stage then reports HARD_ETIMEOUT and leaves Uout unset)
+        const char* starve = std::getenv("HARD_HYDRO_STARVE_TMA");
+        A.starve_tma = starve && starve[0] == '1';
         dim3 grid(cdiv(m.n[0], TX), cdiv(m.n[1], TY), cdiv(A.zhi - A.zlo, A.zchunk));
         auto kern = c.stage == 1 ? stage_tma_kernel<T, TX, TY, 1> : stage_tma_kernel<T, TX, TY, 2>;
         constexpr size_t b1 = TmaLayout<T, TX, TY, 1>::bytes, b2 = L::bytes;

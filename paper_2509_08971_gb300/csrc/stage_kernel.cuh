@@ -44,6 +44,7 @@ struct StageArgs {
     double* tot_partial;              // epilogue totals [nblocks][5] (nullptr = off)
     int* status;                      // non-physical flag
     const CUtensorMap* tmap;          // TMA descriptor of Uc (fused variant)
+    bool starve_tma;                  // test switch: arm the ring's barriers, issue no copies
 };
 
 // Boundary map of one kernel axis: m in [-2, n+1] -> interior index, flip set

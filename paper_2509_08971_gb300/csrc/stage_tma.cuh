@@ -144,6 +144,9 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         // stage 2, update iterations: the U0 plane of the cell completed then
         const bool with_u0 = STAGE == 2 && it >= 4;
         mbar_arrive_expect_tx(bar, tx_bytes + (with_u0 ? L::U0_BYTES : 0u));
+        // test switch: the barrier expects bytes that never come, so every
+        // wait on it runs to its limit (no copy is ever in flight)
+        if (A.starve_tma) return;
         if (with_u0) tma_load_4d(u0s + (it & 1) * L::U0S, &M.u0, x0, y0, jbeg + it - 2, 0, bar);
         tma_load_4d(s, &M.main, x0 - 4, y0 - 2, jj, 0, bar);
         if (px_lo) tma_load_4d(s + L::XLO, &M.xstrip, nx - 4, y0 - 2, jj, 0, bar);

@@ -75,6 +75,26 @@ def test_allocation_failure_is_reported(monkeypatch):
     m.step(U, 1e-3)                          # recovers once allocation works
 
 
+def test_bounded_wait_timeout_is_reported(monkeypatch):
+    """Failure detection of the TMA ring: with HARD_HYDRO_STARVE_TMA=1 the
+    ring's barriers expect bytes that are never sent (no copy is issued, so
+    nothing is in flight), every bounded wait runs out, and the stage reports
+    HARD_ETIMEOUT instead of hanging; the next stage runs normally."""
+    shape = (16, 8, 32)             # rows of 32 floats: the TMA path, one block
+    gam = 5.0 / 3.0
+    U = dev(H.smooth_3d(0, seed=5, gamma=gam, shape=shape), torch.float32)
+    m = hh.HardHydro(shape, gam, hh.HARD_BC_PERIODIC, kernel=hh.HARD_KERNEL_FUSED)
+    plain = hh.HardHydro(shape, gam, hh.HARD_BC_PERIODIC, kernel=hh.HARD_KERNEL_PLAIN)
+    dt = m.cfl_dt(U, 0.4)
+    monkeypatch.setenv("HARD_HYDRO_STARVE_TMA", "1")
+    m.stage(1, None, U, dt)
+    assert m.get_error() == hh.HARD_ETIMEOUT
+    monkeypatch.delenv("HARD_HYDRO_STARVE_TMA")
+    got = m.stage(1, None, U, dt)
+    assert m.get_error() == hh.HARD_OK
+    assert torch.equal(got, plain.stage(1, None, U, dt))
+
+
 def _oracle_window_step(U, c, dt, gam, half=4):
     """Oracle step of the cell c = (k, j, i) of a periodic mesh from its own
     (2*half+1)^3 periodic neighbourhood: a two-stage update reaches 4 cells."""
