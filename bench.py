@@ -58,23 +58,48 @@ def kernel_sources_digest():
     return h.hexdigest()
 
 
-def profiled_traffic():
-    """DRAM bytes per stage launch (read + write, mean of the two stages) from
-    the committed ncu summary, or None when the kernels changed since."""
+def profiled(key):
+    """A figure of the committed ncu summary of the stage kernel
+    ("traffic-bytes-per-launch": DRAM bytes read + written per launch, mean of
+    the two stages; "instructions-per-cell-stage": thread instructions per
+    cell, mean of the two stages), or None when the kernels changed since."""
     path = os.path.join(ROOT, "profiles", "stage_tma_kernel_smooth3d_256.md")
     try:
         rec = {}
         with open(path) as fh:
             for line in fh:
-                if ":" in line and line.split(":", 1)[0] in ("sources-sha256",
-                                                             "traffic-bytes-per-launch"):
+                if ":" in line and line.split(":", 1)[0] in ("sources-sha256", key):
                     k, v = line.split(":", 1)
                     rec[k.strip()] = v.strip()
         if rec.get("sources-sha256") != kernel_sources_digest():
             return None
-        return float(rec["traffic-bytes-per-launch"])
+        return float(rec[key])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def profiled_traffic():
+    return profiled("traffic-bytes-per-launch")
+
+
+SCHEDULERS = 152 * 4       # GB300: 152 SMs, four warp schedulers each
+
+
+def issue_roofline(cells, stage_ms, sm_mhz):
+    """The stage kernel against the SMs' instruction issue rate: warp
+    instructions per second (profiled thread instructions per cell-stage x
+    cells / 32 / launch time) over one warp instruction per scheduler per
+    clock at the median SM clock sampled during the timed steps."""
+    ipc = profiled("instructions-per-cell-stage")
+    if ipc is None or not sm_mhz:
+        return None
+    achieved = ipc * cells / 32.0 / (stage_ms * 1e-3)
+    peak = SCHEDULERS * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak,
+            "unit": "warp-instructions/s", "frac": achieved / peak,
+            "instructions_per_cell_stage": ipc,
+            "source": "ncu smsp__inst_executed of the profiled stage launches; SM clock sampled "
+                      "by nvidia-smi during the timed steps"}
 
 
 def peaks():
@@ -448,6 +473,7 @@ def main():
                 "kernel": "stage_tma_kernel<float,%d,%d> z-chunk %d (mean of stage 1 and stage 2)"
                           % tuple(tuned["info"][:3]),
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": stage_ms}
+    issue = issue_roofline(cells, stage_ms, clocks.get("sm_mhz"))
     del U1, U2
 
     # ---------------- second scheme: WENO5-Z + HLL, FP32 ----------------
@@ -717,7 +743,7 @@ def main():
                    "l2": "state 336 MB > 129 MB L2 (no flush needed)", "kernel": "fused",
                    "tile": {"chosen": tuned["info"], "ms_per_stage": tuned["ms"]},
                    "step": "CFL rate + stage 1 + stage 2 + FP64 totals"},
-        "roofline": roofline,
+        "roofline": roofline, "issue_roofline": issue,
         "slab_schedule": slab_schedule,
         "weno5z_hll": weno,
         "rad_exchange": rad,
