@@ -763,6 +763,11 @@ def main():
         rate, sec, used = time_oracle(shape, 2, threads)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
                                 "sample": f"2 RK2 steps of the full 256^3 workload ({sec:.1f} s)"}
+        # the same oracle on one thread, on a 256 x 256 x 8 slab of the flow
+        rate1, sec1, _ = time_oracle((8, N_SIDE, N_SIDE), 1, 1)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": rate1, "unit": UNIT, "cores": 1,
+            "sample": f"1 RK2 step of a 256x256x8 slab of the workload ({sec1:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
