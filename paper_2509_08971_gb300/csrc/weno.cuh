@@ -251,8 +251,9 @@ struct WenoSmem {
     static constexpr int NP = NF * HX * HY;
     static constexpr int NFX = NF * TY * (TX + 1);                 // one x-face array
     static constexpr int NFY = DIM >= 2 ? NF * (TY + 1) * TX : 0;  // one y-face array
-    // primitive plane; face states (left, right) and fluxes of the x and y faces
-    static constexpr size_t bytes = sizeof(T) * (NP + 3 * NFX + 3 * NFY);
+    // two primitive planes (by plane parity); face states (left, right) and
+    // fluxes of the x and y faces
+    static constexpr size_t bytes = sizeof(T) * (2 * NP + 3 * NFX + 3 * NFY);
 };
 
 template <typename T, int TX, int TY, int DIM, int PX, int PY>
@@ -264,8 +265,8 @@ weno_stage_kernel(const StageArgs<T> A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red_tot[NT / 32][NF];
     __shared__ unsigned long long red_rate[NT / 32];
-    T* Ps = reinterpret_cast<T*>(smem_raw);          // [NF][HY][HX]
-    T* Fx = Ps + S::NP;                               // [NF][TY][TX+1]
+    T* Ps2 = reinterpret_cast<T*>(smem_raw);         // 2 x [NF][HY][HX]
+    T* Fx = Ps2 + 2 * S::NP;                          // [NF][TY][TX+1]
     T* QLx = Fx + S::NFX;                             // left states of the x faces
     T* QRx = QLx + S::NFX;                            // right states
     T* Fy = QRx + S::NFX;                             // [NF][TY+1][TX]
@@ -304,8 +305,14 @@ weno_stage_kernel(const StageArgs<T> A) {
     for (int j = jbeg; j < jend; ++j) {
         const bool xy = DIM < 3 || (j >= z0 && j < z1);
         T qj[NF], Dj[NF];
+        // Three barriers per plane.  The primitive planes alternate by parity:
+        // plane j's is last read (own cell) after the third barrier of plane
+        // j-2, and every thread has passed the barriers of plane j-1 before
+        // any thread writes plane j; the face states and fluxes of plane j
+        // are written after its first barrier, which no thread passes before
+        // every thread has finished plane j-1.
+        T* Ps = Ps2 + ((j - jbeg) & 1) * S::NP;
         if (xy) {
-            __syncthreads();                       // previous plane fully consumed
             for (int e = tid; e < HX * HY; e += NT) {
                 const int hx = e % HX, hy = e / HX;
                 T W[NF];
