@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T
     constexpr int NT = TX * TY;
     constexpr int HX = TX + 2 * WENO_G, HY = DIM >= 2 ? TY + 2 * WENO_G : 1;
     constexpr int NPF = HX * HY;
-    __shared__ T Ps[4 * NPF];                        // E, u', v', w' planes
+    __shared__ T Ps2[2 * 4 * NPF];                   // E, u', v', w' planes, two by plane parity
     __shared__ T Fx[TY * (TX + 1)];
     __shared__ T Fy[DIM >= 2 ? (TY + 1) * TX : 1];
     const int tid = threadIdx.x;
@@ -595,8 +595,12 @@ __global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T
     for (int j = jbeg; j < jend; ++j) {
         const bool xy = DIM < 3 || (j >= z0 && j < z1);
         T ej, wj, Dj;
+        // two barriers per plane: the planes alternate by parity (plane j's is
+        // last read after the second barrier of plane j-2), and the face
+        // fluxes are written after the first barrier, which no thread passes
+        // before every thread has finished the previous plane
+        T* Ps = Ps2 + ((j - jbeg) & 1) * 4 * NPF;
         if (xy) {
-            __syncthreads();
             for (int e = tid; e < NPF; e += NT) {
                 const int hx = e % HX, hy = e / HX;
                 T v[4];
