@@ -2,9 +2,11 @@
 // small operation helpers (vadd, vfma, vminmod, ...).  Every operation is a
 // single IEEE operation with the rounding written in the source (explicit
 // fmaf, single-instruction approximate reciprocal and square root), so each
-// kernel that evaluates a face rounds it identically.  (Paired f32x2
-// arithmetic was measured: it does not round lane-for-lane like the scalar
-// instructions and did not speed the stage kernel up, so it is not used.)
+// kernel that evaluates a face rounds it identically.  (Packed f32x2
+// arithmetic rounds lane for lane like these scalar operations as long as the
+// assembler is kept from contracting a packed product into a packed sum; it
+// was measured in the stage kernel, bit-identical, and did not speed it up,
+// so it is not used.)
 //
 // Formulas: minmod-limited PLM face states and the one-sided HLLC flux with
 // Davis wave-speed bounds (see hydro_math.cuh for the statement).
