@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(TX1) batched_kernel(const BatchArgs<T> B) {
             acc.bad = false;
 #pragma unroll
             for (int f = 0; f < NF; ++f) acc.tot[f] = T(0);
+            int tile = 0;                   // tile count: the parity of stage_tile's plane
             for (int stage = 1; stage <= 2; ++stage) {
                 StageArgs<T> A = batch_stage_args<T>(P, U, W, stage, dt);
                 // non-null: stage_tile folds the signal rate of the new state
@@ -157,10 +158,12 @@ __global__ void __launch_bounds__(TX1) batched_kernel(const BatchArgs<T> B) {
                 if (two_d) {
                     for (int y0 = 0; y0 < P.ny; y0 += TY2)
                         for (int x0 = 0; x0 < P.nx; x0 += TX2)
-                            stage_tile<T, TX2, TY2, 2, 0, 1, false>(A, smem_raw, x0, y0, 0, 1, acc);
+                            stage_tile<T, TX2, TY2, 2, 0, 1, false>(A, smem_raw, x0, y0, 0, 1, acc,
+                                                                    tile++);
                 } else {
                     for (int x0 = 0; x0 < P.nx; x0 += TX1)
-                        stage_tile<T, TX1, 1, 1, 0, 0, false>(A, smem_raw, x0, 0, 0, 1, acc);
+                        stage_tile<T, TX1, 1, 1, 0, 0, false>(A, smem_raw, x0, 0, 0, 1, acc,
+                                                              tile++);
                 }
                 __syncthreads();            // every cell of this stage written
             }

@@ -72,7 +72,9 @@ struct StageSmem {
     static constexpr int NP = NF * HX * HY;                       // primitive plane
     static constexpr int NFX = NF * TY * (TX + 1);                // x-face fluxes
     static constexpr int NFY = DIM >= 2 ? NF * (TY + 1) * TX : 0; // y-face fluxes
-    static constexpr size_t bytes = sizeof(T) * (NP + NFX + NFY);
+    // two primitive planes (by plane parity, or by tile parity when a block
+    // evaluates one tile after another), one plane of x and y face fluxes
+    static constexpr size_t bytes = sizeof(T) * (2 * NP + NFX + NFY);
 };
 
 // Load the conserved values of kernel cell (gx, gy, gz) with the boundary map
@@ -111,14 +113,19 @@ struct TileAcc {
 // One tile of one stage: the TX x TY column at (x0, y0), z-planes [z0, z1)
 // (DIM == 3; a single plane otherwise).  Writes the completed cells of the
 // tile to A.Uo and folds them into `acc`.  All threads of the block call it.
+// A block that evaluates tiles one after another numbers them in `tile`: the
+// primitive plane alternates by that parity (by plane parity along z), so a
+// tile's loads never overwrite the plane that the previous tile's cells are
+// still reading, and no barrier is needed before them.
 template <typename T, int TX, int TY, int DIM, int PX, int PY, bool NC>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, unsigned char* smem_raw, int x0,
-                                           int y0, int z0, int z1, TileAcc<T>& acc) {
+                                           int y0, int z0, int z1, TileAcc<T>& acc,
+                                           int tile = 0) {
     using S = StageSmem<T, TX, TY, DIM>;
     constexpr int NT = TX * TY;
     constexpr int HX = S::HX, HY = S::HY;
-    T* Ps = reinterpret_cast<T*>(smem_raw);          // [NF][HY][HX]
-    T* Fx = Ps + S::NP;                               // [NF][TY][TX+1]
+    T* Ps2 = reinterpret_cast<T*>(smem_raw);         // 2 x [NF][HY][HX]
+    T* Fx = Ps2 + 2 * S::NP;                          // [NF][TY][TX+1]
     T* Fy = Fx + S::NFX;                              // [NF][TY+1][TX]
 
     const int tid = threadIdx.x;
@@ -143,8 +150,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, unsigned char*
         const bool xy = DIM < 3 || (j >= z0 && j < z1);
         T qj[NF];
         T Dj[NF];
+        T* Ps = Ps2 + (((DIM == 3 ? j : tile) & 1) * S::NP);
         if (xy) {
-            __syncthreads();                       // previous plane fully consumed
+            // Ps of the previous plane (tile) stays untouched; the fluxes are
+            // written after the next barrier, which no thread passes before
+            // every thread has finished reading the previous ones
             for (int e = tid; e < HX * HY; e += NT) {
                 int hx = e % HX, hy = e / HX;
                 T W[NF];
