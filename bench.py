@@ -429,8 +429,9 @@ def main():
     status = m32.get_error()
     clocks = clk.summary()
     # kernels of this library launched in the timed region:
-    # 1 signal rate + per step (finalize dt, stage 1, stage 2, finalize totals)
-    launches = 1 + 4 * args.steps
+    # signal rate and the first step's dt, then per step stage 1, stage 2 and
+    # one finalize launch (the step's totals and the next step's dt)
+    launches = 2 + 3 * args.steps
 
     # ---------------- the same step, stages blocked through L2 (z slabs) ----------------
     slab = 2 * tuned["info"][2]                       # two z-chunks of the tuned tile per slab

@@ -229,8 +229,9 @@ int read_status(hard_hydro_s* h, cudaStream_t s) {
 
 // ---- finalize kernels ----
 
-__global__ void finalize_dt_kernel(unsigned long long* slot, double cfl, double t_end, double* t,
-                                   double* dt_out, double* dt_log, int step, int* status) {
+// dt of a step from the largest signal rate of the state it starts from.
+__device__ void finalize_dt(unsigned long long* slot, double cfl, double t_end, double* t,
+                            double* dt_out, double* dt_log, int step, int* status) {
     const double r = __longlong_as_double((long long)*slot);
     *slot = 0ull;                                  // ready for this step's stage-2 epilogue
     double dt;
@@ -250,17 +251,37 @@ __global__ void finalize_dt_kernel(unsigned long long* slot, double cfl, double 
     if (dt_log) dt_log[step] = dt;
 }
 
+__global__ void finalize_dt_kernel(unsigned long long* slot, double cfl, double t_end, double* t,
+                                   double* dt_out, double* dt_log, int step, int* status) {
+    finalize_dt(slot, cfl, t_end, t, dt_out, dt_log, step, status);
+}
+
 // Fixed-order sum of the per-block partials: warp f sums field f, lane l the
 // rows l, l+32, ..., then a fixed xor tree.  Deterministic for a fixed grid.
-__global__ void finalize_totals_kernel(const double* partial, long long rows, double dV,
-                                       double* out5) {
+__device__ void finalize_totals(const double* partial, long long rows, double dV, double* out5) {
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (f >= 5) return;
     double s = 0.0;
     for (long long r = lane; r < rows; r += 32) s += partial[r * 5 + f];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out5[f] = s * dV;
+}
+
+__global__ void finalize_totals_kernel(const double* partial, long long rows, double dV,
+                                       double* out5) {
+    if ((threadIdx.x >> 5) < 5) finalize_totals(partial, rows, dV, out5);
+}
+
+// The end of one step of the time loop in one launch: warps 0-4 sum that
+// step's totals, lane 0 of warp 5 sets the dt of the step after it (from the
+// rate that the step's stage 2 left in the slot) when next_step >= 0.
+__global__ void finalize_step_kernel(const double* partial, long long rows, double dV,
+                                     double* out5, unsigned long long* slot, double cfl,
+                                     double t_end, double* t, double* dt_out, double* dt_log,
+                                     int next_step, int* status) {
+    if ((threadIdx.x >> 5) < 5) finalize_totals(partial, rows, dV, out5);
+    else if (threadIdx.x == 160 && next_step >= 0)
+        finalize_dt(slot, cfl, t_end, t, dt_out, dt_log, next_step, status);
 }
 
 }  // namespace
@@ -277,6 +298,16 @@ cudaError_t launch_finalize_dt(unsigned long long* rs, double cfl, double t_end,
 cudaError_t launch_finalize_totals(const double* partial, long long rows, double dV, double* out5,
                                    cudaStream_t s) {
     finalize_totals_kernel<<<1, 160, 0, s>>>(partial, rows, dV, out5);
+    return cudaGetLastError();
+}
+
+// Totals of step `next_step - 1` and, when next_step >= 0, the dt of next_step.
+cudaError_t launch_finalize_step(const double* partial, long long rows, double dV, double* out5,
+                                 unsigned long long* rs, double cfl, double t_end, double* t_dev,
+                                 double* dt_dev, double* dt_log, int next_step, int* status,
+                                 cudaStream_t s) {
+    finalize_step_kernel<<<1, 192, 0, s>>>(partial, rows, dV, out5, rs, cfl, t_end, t_dev, dt_dev,
+                                           dt_log, next_step, status);
     return cudaGetLastError();
 }
 
@@ -447,27 +478,37 @@ int hard_hydro_advance(hard_hydro_t h, void* U, int nsteps, double cfl, double t
     if (e == cudaSuccess) e = cudaMemsetAsync(rate_slot(h), 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = rate_launch(h, U, s);
     const double dV = h->mesh.dx[0] * h->mesh.dx[1] * h->mesh.dx[2];
-    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
-        e = hh::launch_finalize_dt(rate_slot(h), cfl, t_end, t, dt_slot(h), dt_log_dev, step,
+    // launches per step: stage 1, stage 2, then one finalize kernel that
+    // closes the step (its totals) and sets the next step's dt
+    if (e == cudaSuccess && nsteps > 0)
+        e = hh::launch_finalize_dt(rate_slot(h), cfl, t_end, t, dt_slot(h), dt_log_dev, 0,
                                    status_slot(h), s);
-        if (e != cudaSuccess) break;
+    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
         StageCall c1{1, U, U, h->U1, 0.0, dt_slot(h), nullptr, nullptr, status_slot(h)};
         double* part = (totals_log_dev && h->mesh.dim > 0) ? h->tot_partial : nullptr;
         StageCall c2{2, U, h->U1, U, 0.0, dt_slot(h), rate_slot(h), part, status_slot(h)};
         e = two_stages(h, c1, c2, s);
-        if (e != cudaSuccess || !totals_log_dev) continue;
+        if (e != cudaSuccess) break;
+        const int next = step + 1 < nsteps ? step + 1 : -1;
+        if (!totals_log_dev) {
+            if (next >= 0)
+                e = hh::launch_finalize_dt(rate_slot(h), cfl, t_end, t, dt_slot(h), dt_log_dev,
+                                           next, status_slot(h), s);
+            continue;
+        }
+        long long prow = rows;
         if (!part) {
             // no active axis: the stage kernel has no totals epilogue
             rc = ensure_partial(h, hh::totals_blocks());
             if (rc) return rc;
             e = h->dtype == HARD_F64 ? hh::launch_totals_f64(h->mesh, U, h->tot_partial, s)
                                      : hh::launch_totals_f32(h->mesh, U, h->tot_partial, s);
-            if (e == cudaSuccess)
-                e = hh::launch_finalize_totals(h->tot_partial, hh::totals_blocks(), dV,
-                                               totals_log_dev + 5 * step, s);
-        } else {
-            e = hh::launch_finalize_totals(h->tot_partial, rows, dV, totals_log_dev + 5 * step, s);
+            prow = hh::totals_blocks();
         }
+        if (e == cudaSuccess)
+            e = hh::launch_finalize_step(h->tot_partial, prow, dV, totals_log_dev + 5 * step,
+                                         rate_slot(h), cfl, t_end, t, dt_slot(h), dt_log_dev,
+                                         next, status_slot(h), s);
     }
     return from_cuda(e);
 }

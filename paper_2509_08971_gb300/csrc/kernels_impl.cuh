@@ -241,7 +241,9 @@ cudaError_t dispatch_tile(const MeshDesc& m, int kernel, int tile, const StageCa
                           cudaStream_t s) {
     const TileDesc td = tile_desc(DIM, tile);
     if constexpr (DIM == 3) {
-        if (kernel == 0 && tma_eligible(m, c.Uc)) {
+        // the TMA kernel carries the rate / totals epilogue for stage 2 only
+        const bool epi_ok = c.stage == 2 || (!c.rate_slot && !c.tot_partial);
+        if (kernel == 0 && epi_ok && tma_eligible(m, c.Uc)) {
             bool used = false;
             cudaError_t e;
             switch (tile) {

@@ -110,6 +110,58 @@ struct TileAcc {
     bool bad;
 };
 
+// Warp sum of the five per-lane FP64 totals as a reduce-scatter butterfly:
+// over the first three levels the lanes split the fields between them, so
+// each lane takes 8 shuffles and 8 additions instead of 25 of each (FP64
+// runs at a small fraction of the FP32 rate on this part).  Returns the
+// warp's total of field sum5_field(lane) in the lanes where sum5_writer(lane)
+// holds: field 0 in lane 0, 1 in lane 4, 2 in lane 8, 3 in lane 16, 4 in
+// lane 24.  The order of the additions is fixed, so the sum is deterministic.
+__device__ __forceinline__ double warp_sum5(const double v[NF], int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    // offset 16: lanes 0-15 keep fields 0, 1, 2; lanes 16-31 keep 3, 4
+    double a0 = h16 ? v[3] : v[0];
+    double a1 = h16 ? v[4] : v[1];
+    double a2 = h16 ? 0.0 : v[2];
+    const double s0 = h16 ? v[0] : v[3];
+    const double s1 = h16 ? v[1] : v[4];
+    const double s2 = h16 ? v[2] : 0.0;
+    a0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    a1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    a2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+    // offset 8: lanes 0-7 keep fields 0, 1; 8-15 field 2; 16-23 field 3;
+    // 24-31 field 4
+    double c0, c1, t0, t1;
+    if (!h16) {
+        c0 = h8 ? a2 : a0;
+        c1 = h8 ? 0.0 : a1;
+        t0 = h8 ? a0 : a2;
+        t1 = h8 ? a1 : 0.0;
+    } else {
+        c0 = h8 ? a1 : a0;
+        c1 = 0.0;
+        t0 = h8 ? a0 : a1;
+        t1 = 0.0;
+    }
+    c0 += __shfl_xor_sync(0xffffffffu, t0, 8);
+    c1 += __shfl_xor_sync(0xffffffffu, t1, 8);
+    // offset 4: lanes 0-3 keep field 0, 4-7 field 1; every other lane holds
+    // one field already and adds its partner's share of it
+    const bool two = !h16 && !h8;
+    double k = (two && h4) ? c1 : c0;
+    const double t = two ? (h4 ? c0 : c1) : c0;
+    k += __shfl_xor_sync(0xffffffffu, t, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+__device__ __forceinline__ int sum5_field(int lane) {
+    return (lane & 16) ? ((lane & 8) ? 4 : 3) : ((lane & 8) ? 2 : ((lane & 4) ? 1 : 0));
+}
+__device__ __forceinline__ bool sum5_writer(int lane) {
+    return lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
+}
+
 // One tile of one stage: the TX x TY column at (x0, y0), z-planes [z0, z1)
 // (DIM == 3; a single plane otherwise).  Writes the completed cells of the
 // tile to A.Uo and folds them into `acc`.  All threads of the block call it.
@@ -317,13 +369,11 @@ stage_kernel(const StageArgs<T> A) {
         if (lane == 0) red_rate[warp] = b;
     }
     if (A.tot_partial) {
+        double v[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            double v = (double)tot[f];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red_tot[warp][f] = v;
-        }
+        for (int f = 0; f < NF; ++f) v[f] = (double)tot[f];
+        const double s = warp_sum5(v, lane);
+        if (sum5_writer(lane)) red_tot[warp][sum5_field(lane)] = s;
     }
     const int any_bad = __syncthreads_or(bad);
     if (tid == 0) {
@@ -333,15 +383,13 @@ stage_kernel(const StageArgs<T> A) {
             for (int w = 0; w < NT / 32; ++w) b = red_rate[w] > b ? red_rate[w] : b;
             atomicMax(A.rate_slot, b);
         }
-        if (A.tot_partial) {
-            const long long bz = DIM == 3 ? A.zlo / A.zchunk + blockIdx.z : blockIdx.z;
-            const long long blk = (bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            for (int f = 0; f < NF; ++f) {
-                double s = 0.0;
-                for (int w = 0; w < NT / 32; ++w) s += red_tot[w][f];
-                A.tot_partial[blk * NF + f] = s;
-            }
-        }
+    }
+    if (A.tot_partial && tid < NF) {
+        const long long bz = DIM == 3 ? A.zlo / A.zchunk + blockIdx.z : blockIdx.z;
+        const long long blk = (bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += red_tot[w][tid];
+        A.tot_partial[blk * NF + tid] = s;
     }
 }
 

@@ -73,12 +73,15 @@ struct TmaLayout {
 // FP32 blocks of up to 256 threads run two per SM (register cap 128 per
 // thread); FP64 rings fill an SM's shared memory with one block.
 // STAGE (1 or 2) is a template parameter: the stage-2 combine and its U0
-// stream compile away from stage 1.
+// stream, and the signal-rate and totals epilogue (which the time loop asks
+// of stage 2 only; the launcher sends any other such call to the plain
+// kernel), compile away from stage 1.
 template <typename T, int TX, int TY, int STAGE>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
 stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__ TmaMaps M) {
     using L = TmaLayout<T, TX, TY, STAGE>;
     constexpr int NT = TX * TY;
+    constexpr bool EPI = STAGE == 2;
     constexpr int D = L::D, P = L::P;
     constexpr int HXC = L::HXC, HYC = L::HYC, HXP = L::HXP, HYP = L::HYP;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -388,13 +391,13 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
                 A.Uo[f * Nu + cell] = Uo[f];
             }
             cell += plane;
-            if (A.rate_slot) {
+            if (EPI && A.rate_slot) {
                 T W[NF];
                 cons_to_prim(Uo, gm1, W);
                 const T r = cell_rate(W, gamma, A.act, A.rdx);
                 rate_max = (r > rate_max || r != r) ? r : rate_max;
             }
-            if (A.tot_partial) {
+            if (EPI && A.tot_partial) {
 #pragma unroll
                 for (int f = 0; f < NF; ++f) tot[f] += Uo[f];
             }
@@ -422,7 +425,7 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
 
     // ---- epilogue: block reductions ----
     const int lane = tid & 31, warp = tid >> 5;
-    if (A.rate_slot) {
+    if (EPI && A.rate_slot) {
         unsigned long long b = rate_bits(rate_max);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -431,32 +434,28 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         }
         if (lane == 0) red_rate[warp] = b;
     }
-    if (A.tot_partial) {
+    if (EPI && A.tot_partial) {
+        double v[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            double v = (double)tot[f];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red_tot[warp][f] = v;
-        }
+        for (int f = 0; f < NF; ++f) v[f] = (double)tot[f];
+        const double s = warp_sum5(v, lane);
+        if (sum5_writer(lane)) red_tot[warp][sum5_field(lane)] = s;
     }
     const int any_bad = __syncthreads_or(bad);
     if (tid == 0) {
         if (any_bad) atomicOr(A.status, 1);
-        if (A.rate_slot) {
+        if (EPI && A.rate_slot) {
             unsigned long long b = 0;
             for (int w = 0; w < NT / 32; ++w) b = red_rate[w] > b ? red_rate[w] : b;
             atomicMax(A.rate_slot, b);
         }
-        if (A.tot_partial) {
-            const long long bz = A.zlo / A.zchunk + blockIdx.z;
-            const long long blk = (bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            for (int f = 0; f < NF; ++f) {
-                double s = 0.0;
-                for (int w = 0; w < NT / 32; ++w) s += red_tot[w][f];
-                A.tot_partial[blk * NF + f] = s;
-            }
-        }
+    }
+    if (EPI && A.tot_partial && tid < NF) {
+        const long long bz = A.zlo / A.zchunk + blockIdx.z;
+        const long long blk = (bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += red_tot[w][tid];
+        A.tot_partial[blk * NF + tid] = s;
     }
 }
 

@@ -474,13 +474,11 @@ weno_stage_kernel(const StageArgs<T> A) {
         if (lane == 0) red_rate[warp] = b;
     }
     if (A.tot_partial) {
+        double v[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            double v = (double)tot[f];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red_tot[warp][f] = v;
-        }
+        for (int f = 0; f < NF; ++f) v[f] = (double)tot[f];
+        const double s = warp_sum5(v, lane);
+        if (sum5_writer(lane)) red_tot[warp][sum5_field(lane)] = s;
     }
     const int any_bad = __syncthreads_or(bad);
     if (tid == 0) {
@@ -490,14 +488,12 @@ weno_stage_kernel(const StageArgs<T> A) {
             for (int wi = 0; wi < NT / 32; ++wi) b = red_rate[wi] > b ? red_rate[wi] : b;
             atomicMax(A.rate_slot, b);
         }
-        if (A.tot_partial) {
-            const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            for (int f = 0; f < NF; ++f) {
-                double s = 0.0;
-                for (int wi = 0; wi < NT / 32; ++wi) s += red_tot[wi][f];
-                A.tot_partial[blk * NF + f] = s;
-            }
-        }
+    }
+    if (A.tot_partial && tid < NF) {
+        const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        double s = 0.0;
+        for (int wi = 0; wi < NT / 32; ++wi) s += red_tot[wi][tid];
+        A.tot_partial[blk * NF + tid] = s;
     }
 }
 
