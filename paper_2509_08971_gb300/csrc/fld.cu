@@ -36,7 +36,6 @@ struct FldLevel {
     bool coarsened[3];       // this level's axes halved into the next level
     void* x;                 // solution / correction (level 0: the caller's Er)
     void* b;                 // right-hand side
-    void* r;                 // residual
     void* D;                 // cell coefficient
 };
 
@@ -55,7 +54,6 @@ template <typename T>
 struct LvlArgs {
     T* x;
     const T* b;
-    T* r;
     const T* D;
     int n[3];
     T idx2[3];               // 1 / dx^2 per axis (0: inactive)
@@ -117,17 +115,6 @@ __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int col
     a.x[q] = (a.b[q] + off) / diag;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) residual_kernel(const LvlArgs<T> a) {
-    const int j = blockIdx.y, k = blockIdx.z;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n[0]) return;
-    const int q = (k * a.n[1] + j) * a.n[0] + i;
-    T diag, off;
-    stencil(a, i, j, k, q, diag, off);
-    a.r[q] = a.b[q] - (diag * a.x[q] - off);
-}
-
 // Residual of level l restricted to level l+1 in one pass: one thread per
 // coarse cell computes its children's residuals and writes their mean to the
 // coarse right-hand side, and zeroes the coarse correction.
@@ -153,40 +140,40 @@ __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T>
     xc[Q] = T(0);
 }
 
-// sum r^2 and sum b^2 into norms[0..1]: grid-stride, one atomic per block
+// Convergence check of the fine level: sum r^2 and sum b^2 (r = b - A x) into
+// norms[0..1], without storing r.  Blocks take rows (j, k) in a grid-stride
+// loop, one pair of atomics per block.  FP32: sums over runs of 32 cells in
+// FP32, each run added in FP64 (the FP64 pipe of this GPU is a small
+// fraction of its FP32 rate; a run of 32 positive FP32 terms is exact to
+// ~2e-6 relative, far inside what a convergence test of the residual needs).
+// FP64: every term added in FP64.
 template <typename T>
-__global__ void __launch_bounds__(256) norms_kernel(const T* r, const T* b, long long N,
-                                                    double* norms) {
-    __shared__ double sr[8], sb[8];
+__global__ void __launch_bounds__(128) residual_norms_kernel(const LvlArgs<T> a, double* norms) {
+    __shared__ double sr[4], sb[4];
     double rr = 0.0, bb = 0.0;
-    if constexpr (sizeof(T) == 4) {
-        // FP32 sums over runs of 32 elements, each run added in FP64: the
-        // FP64 pipe of this GPU is a small fraction of its FP32 rate, and an
-        // FP64 multiply-add per element made this pass compute-bound.  A run
-        // of 32 positive FP32 terms is exact to ~2e-6 relative, far inside
-        // what a convergence test of the residual needs.
-        float pr = 0.0f, pb = 0.0f;
-        int run = 0;
-        for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
-             q += (long long)gridDim.x * blockDim.x) {
-            pr = fmaf(r[q], r[q], pr);
-            pb = fmaf(b[q], b[q], pb);
-            if (++run == 32) {
+    T pr = T(0), pb = T(0);
+    int run = 0;
+    const int rows = a.n[1] * a.n[2];
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % a.n[1], k = row / a.n[1];
+        for (int i = threadIdx.x; i < a.n[0]; i += blockDim.x) {
+            const int q = (k * a.n[1] + j) * a.n[0] + i;
+            T diag, off;
+            stencil(a, i, j, k, q, diag, off);
+            const T bq = a.b[q];
+            const T r = bq - (diag * a.x[q] - off);
+            pr = fma(r, r, pr);
+            pb = fma(bq, bq, pb);
+            if (sizeof(T) == 8 || ++run == 32) {
                 rr += (double)pr;
                 bb += (double)pb;
-                pr = pb = 0.0f;
+                pr = pb = T(0);
                 run = 0;
             }
         }
-        rr += (double)pr;
-        bb += (double)pb;
-    } else {
-        for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
-             q += (long long)gridDim.x * blockDim.x) {
-            rr += (double)r[q] * (double)r[q];
-            bb += (double)b[q] * (double)b[q];
-        }
     }
+    rr += (double)pr;
+    bb += (double)pb;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         rr += __shfl_xor_sync(0xffffffffu, rr, o);
@@ -325,7 +312,6 @@ LvlArgs<T> level_args(const FldHierarchy* H, int l, double dt) {
     LvlArgs<T> a;
     a.x = static_cast<T*>(L.x);
     a.b = static_cast<const T*>(L.b);
-    a.r = static_cast<T*>(L.r);
     a.D = static_cast<const T*>(L.D);
     for (int ax = 0; ax < 3; ++ax) {
         a.n[ax] = L.n[ax];
@@ -405,9 +391,9 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
         done = cyc + 1;
         if (rtol > 0.0) {
             if ((e = cudaMemsetAsync(H->norms, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
-            residual_kernel<T><<<rows_grid(L0, 1), 128, 0, s>>>(level_args<T>(H, 0, dt));
-            norms_kernel<T><<<grid_for(L0.N) < 152 * 4 ? grid_for(L0.N) : 152 * 4, 256, 0, s>>>(
-                static_cast<const T*>(L0.r), static_cast<const T*>(L0.b), L0.N, H->norms);
+            const int rows = L0.n[1] * L0.n[2];
+            residual_norms_kernel<T><<<rows < 152 * 16 ? rows : 152 * 16, 128, 0, s>>>(
+                level_args<T>(H, 0, dt), H->norms);
             double nr[2];
             if ((e = cudaMemcpyAsync(nr, H->norms, sizeof(nr), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
                 return e;
@@ -451,7 +437,6 @@ FldHierarchy* fld_create(const MeshDesc& m, int dtype) {
         L.x = nullptr;
         if (nl > 0 && cudaMalloc(&L.x, es * L.N) != cudaSuccess) ok = false;
         if (cudaMalloc(&L.b, es * L.N) != cudaSuccess) ok = false;
-        if (cudaMalloc(&L.r, es * L.N) != cudaSuccess) ok = false;
         if (cudaMalloc(&L.D, es * L.N) != cudaSuccess) ok = false;
         ++nl;
         if (!ok) break;
@@ -485,7 +470,6 @@ void fld_destroy(FldHierarchy* H) {
     for (int l = 0; l < H->nl; ++l) {
         if (l > 0) cudaFree(H->L[l].x);
         cudaFree(H->L[l].b);
-        cudaFree(H->L[l].r);
         cudaFree(H->L[l].D);
     }
     cudaFree(H->norms);
