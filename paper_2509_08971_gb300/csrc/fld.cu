@@ -69,14 +69,45 @@ __device__ __forceinline__ void cell_ijk(long long q, const int n[3], int& i, in
     k = (int)(t / n[1]);
 }
 
-// the cell's stencil: diagonal 1 + sum w and sum w x_nb (32-bit cell
-// indices: a level has fewer than 2^31 cells)
+// The cell's stencil: diagonal 1 + sum w and sum w x_nb (32-bit cell
+// indices: a level has fewer than 2^31 cells), in two steps so that a kernel
+// can issue the loads of several cells before any of their arithmetic.  The
+// neighbour indices are selects (across the wrap on a periodic axis; at a
+// wall the cell itself, with weight 0: a wall carries no flux).
 template <typename T>
-__device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k, int q, T& diag,
-                                        T& off) {
+struct StencilVals {
+    T Dc;
+    T Dn[6], xn[6];           // neighbours (axis, side): 2 ax + (s > 0)
+    int face;                 // bit 2 ax + (s > 0): that face carries a flux
+};
+
+template <typename T>
+__device__ __forceinline__ void stencil_load(const LvlArgs<T>& a, int i, int j, int k, int q,
+                                             StencilVals<T>& v) {
     const int c[3] = {i, j, k};
     const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
-    const T Dc = a.D[q];
+    v.Dc = a.D[q];
+    v.face = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const int n = a.n[ax];
+        if (n <= 1) continue;                       // inactive axis: the same for every thread
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            const int m = c[ax] + s;
+            const bool in = m >= 0 && m < n;
+            const int wrap = q + (m < 0 ? (n - 1) : -(n - 1)) * stride[ax];
+            const int qn = in ? q + s * stride[ax] : (a.per[ax] ? wrap : q);
+            v.Dn[2 * ax + (s > 0)] = a.D[qn];
+            v.xn[2 * ax + (s > 0)] = a.x[qn];
+            v.face |= (in || a.per[ax]) ? 1 << (2 * ax + (s > 0)) : 0;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stencil_eval(const LvlArgs<T>& a, const StencilVals<T>& v,
+                                             T& diag, T& off) {
     diag = T(1);
     off = T(0);
 #pragma unroll
@@ -85,50 +116,88 @@ __device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k
         if (n <= 1) continue;
 #pragma unroll
         for (int s = -1; s <= 1; s += 2) {
-            const int m = c[ax] + s;
-            int qn;
-            if (m >= 0 && m < n) {
-                qn = q + s * stride[ax];
-            } else if (a.per[ax]) {
-                qn = q + (m < 0 ? (n - 1) : -(n - 1)) * stride[ax];    // across the wrap
-            } else {
-                continue;                                               // a wall: no flux
-            }
-            const T w = a.dt * (T(0.5) * (Dc + a.D[qn])) * a.idx2[ax];
+            const bool use = (v.face >> (2 * ax + (s > 0))) & 1;
+            const T Dn = v.Dn[2 * ax + (s > 0)], xn = v.xn[2 * ax + (s > 0)];
+            const T w = use ? a.dt * (T(0.5) * (v.Dc + Dn)) * a.idx2[ax] : T(0);
             diag += w;
-            off += w * a.x[qn];
+            off += w * xn;
         }
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k, int q, T& diag,
+                                        T& off) {
+    StencilVals<T> v;
+    stencil_load(a, i, j, k, q, v);
+    stencil_eval(a, v, diag, off);
+}
+
 // Launch shape of the level kernels: x along threads (and blockIdx.x), one
-// row j per blockIdx.y, one plane k per blockIdx.z: no index division.
+// row j per blockIdx.y (SMOOTH_ROWS rows for the smoother), one plane k per
+// blockIdx.z: no index division.
+//
+// The smoother gives each thread its colour's cell in SMOOTH_ROWS consecutive
+// rows.  The rows' stencil loads are independent, so several are in flight
+// per thread (with one cell per thread the kernel waited on load latency),
+// and the rows share their y neighbours through L1.  A half-sweep writes only
+// cells of its colour and reads only the other colour's x, so all of a
+// thread's stores can wait until its loads are done.
+constexpr int SMOOTH_ROWS = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int color) {
-    const int j = blockIdx.y, k = blockIdx.z;
-    // the cells of this colour in the row: i = 2p + ((j + k + color) & 1)
-    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
-    if (i >= a.n[0]) return;
-    const int q = (k * a.n[1] + j) * a.n[0] + i;
-    T diag, off;
-    stencil(a, i, j, k, q, diag, off);
-    a.x[q] = (a.b[q] + off) / diag;
+    const int k = blockIdx.z;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    StencilVals<T> v[SMOOTH_ROWS];
+    T bq[SMOOTH_ROWS];
+    int qs[SMOOTH_ROWS];
+    bool on[SMOOTH_ROWS];
+    // all rows' loads first (a row outside the level evaluates cell (0, 0, k)
+    // and is not stored), then the arithmetic, then the stores
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r) {
+        const int j = blockIdx.y * SMOOTH_ROWS + r;
+        // the cells of this colour in the row: i = 2p + ((j + k + color) & 1)
+        const int i = 2 * p + ((j + k + color) & 1);
+        on[r] = j < a.n[1] && i < a.n[0];
+        const int ii = on[r] ? i : 0, jj = on[r] ? j : 0;
+        qs[r] = (k * a.n[1] + jj) * a.n[0] + ii;
+        stencil_load(a, ii, jj, k, qs[r], v[r]);
+        bq[r] = a.b[qs[r]];
+    }
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r) {
+        T diag, off;
+        stencil_eval(a, v[r], diag, off);
+        bq[r] = (bq[r] + off) / diag;
+    }
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r)
+        if (on[r]) a.x[qs[r]] = bq[r];
 }
 
 // Residual of level l restricted to level l+1 in one pass: one thread per
 // coarse cell computes its children's residuals and writes their mean to the
 // coarse right-hand side, and zeroes the coarse correction.
-template <typename T>
+// H2: every axis coarsened by 2 (the children loops unrolled at compile
+// time, so their loads overlap); otherwise the factors h0, h1, h2 are read at
+// run time.  The children are summed in the same order either way.
+template <typename T, bool H2>
 __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T> a, T* bc, T* xc,
                                                                 int nc0, int nc1, int h0, int h1,
                                                                 int h2) {
     const int J = blockIdx.y, K = blockIdx.z;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc0) return;
+    if (H2) h0 = h1 = h2 = 2;
     T sum = T(0);
-    for (int cz = 0; cz < h2; ++cz)
-        for (int cy = 0; cy < h1; ++cy)
-            for (int cx = 0; cx < h0; ++cx) {
+#pragma unroll
+    for (int cz = 0; cz < (H2 ? 2 : h2); ++cz)
+#pragma unroll
+        for (int cy = 0; cy < (H2 ? 2 : h1); ++cy)
+#pragma unroll
+            for (int cx = 0; cx < (H2 ? 2 : h0); ++cx) {
                 const int i = I * h0 + cx, j = J * h1 + cy, k = K * h2 + cz;
                 const int q = (k * a.n[1] + j) * a.n[0] + i;
                 T diag, off;
@@ -326,7 +395,8 @@ LvlArgs<T> level_args(const FldHierarchy* H, int l, double dt) {
 template <typename T>
 cudaError_t smooth(const FldHierarchy* H, int l, double dt, int sweeps, cudaStream_t s) {
     const LvlArgs<T> a = level_args<T>(H, l, dt);
-    const dim3 g = rows_grid(H->L[l], 2);
+    dim3 g = rows_grid(H->L[l], 2);
+    g.y = (g.y + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
     for (int it = 0; it < sweeps; ++it)
         for (int color = 0; color < 2; ++color) smooth_kernel<T><<<g, 128, 0, s>>>(a, color);
     return cudaGetLastError();
@@ -366,7 +436,9 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             if ((e = smooth<T>(H, l, dt, FLD_PRE, s)) != cudaSuccess) return e;
             const FldLevel& F = H->L[l];
             const FldLevel& C = H->L[l + 1];
-            residual_restrict_kernel<T><<<rows_grid(C, 1), 128, 0, s>>>(
+            const bool h2 = F.coarsened[0] && F.coarsened[1] && F.coarsened[2];
+            auto rr = h2 ? residual_restrict_kernel<T, true> : residual_restrict_kernel<T, false>;
+            rr<<<rows_grid(C, 1), 128, 0, s>>>(
                 level_args<T>(H, l, dt), static_cast<T*>(C.b), static_cast<T*>(C.x), C.n[0],
                 C.n[1], F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
         }
