@@ -155,8 +155,8 @@ __device__ __forceinline__ void weno_face(const T q[6][NF], T gamma, T gx, T F[N
 // (weno5z(v0, .., v4)) and `left` at its left face (weno5z of the mirrored
 // stencil v4, .., v0).  The mirrored stencil has the indicators (b2, b1, b0)
 // and the same tau5, so in FP32 one pass shares the three ratios
-// tau5 / (b_k + eps): candidate k of the left value takes the linear weight
-// d_k with the ratio of b_{2-k}.
+// tau5 / (b_k + eps) (candidate k of the left value takes the linear weight
+// d_k with the ratio of b_{2-k}) and the candidates' differences.
 // FP64 (the parity path) evaluates the two values exactly as weno5z of the
 // stencil and of its mirror, so that they round like the oracle's.
 __device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, double v3, double v4,
@@ -166,30 +166,28 @@ __device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, dou
 }
 __device__ __forceinline__ void weno5z_pair(float v0, float v1, float v2, float v3, float v4,
                                             float& right, float& left) {
-    const float sixth = 1.0f / 6.0f, c = 13.0f / 12.0f;
+    // The candidates as offsets from v2, in terms of the indicators' own
+    // differences: with u_k = s_k / 12 and w_k = t_k / 4, the right value's
+    // candidates are v2 + (u0 + w0), v2 + (u1 - w1), v2 + (u2 - w2).  The
+    // mirrored stencil has s' = (s2, s1, s0) and t' = (t2, -t1, t0), so the
+    // left value's are v2 + (u2 + w2), v2 + (u1 + w1), v2 + (u0 - w0).  Each
+    // value is then v2 + sum a_k (p_k - v2) / sum a_k.
+    const float c = 13.0f / 12.0f, twelfth = 1.0f / 12.0f;
     const float s0 = v0 - 2.0f * v1 + v2, t0 = v0 - 4.0f * v1 + 3.0f * v2;
     const float s1 = v1 - 2.0f * v2 + v3, t1 = v1 - v3;
     const float s2 = v2 - 2.0f * v3 + v4, t2 = 3.0f * v2 - 4.0f * v3 + v4;
-    const float b0 = fmaf(c * s0, s0, 0.25f * t0 * t0);
-    const float b1 = fmaf(c * s1, s1, 0.25f * t1 * t1);
-    const float b2 = fmaf(c * s2, s2, 0.25f * t2 * t2);
+    const float w0 = 0.25f * t0, w1 = 0.25f * t1, w2 = 0.25f * t2;    // exact
+    const float b0 = fmaf(c * s0, s0, w0 * t0);
+    const float b1 = fmaf(c * s1, s1, w1 * t1);
+    const float b2 = fmaf(c * s2, s2, w2 * t2);
     const float tau = fabsf(b0 - b2);
     const float r0 = tau * vrcp(b0 + 1e-30f), r1 = tau * vrcp(b1 + 1e-30f),
                 r2 = tau * vrcp(b2 + 1e-30f);
-    {
-        const float p0 = (2.0f * v0 - 7.0f * v1 + 11.0f * v2) * sixth;
-        const float p1 = (-v1 + 5.0f * v2 + 2.0f * v3) * sixth;
-        const float p2 = (2.0f * v2 + 5.0f * v3 - v4) * sixth;
-        const float a0 = fmaf(0.1f, r0, 0.1f), a1 = fmaf(0.6f, r1, 0.6f), a2 = fmaf(0.3f, r2, 0.3f);
-        right = fmaf(a0, p0, fmaf(a1, p1, a2 * p2)) * vrcp(a0 + a1 + a2);
-    }
-    {
-        const float p0 = (2.0f * v4 - 7.0f * v3 + 11.0f * v2) * sixth;
-        const float p1 = (-v3 + 5.0f * v2 + 2.0f * v1) * sixth;
-        const float p2 = (2.0f * v2 + 5.0f * v1 - v0) * sixth;
-        const float a0 = fmaf(0.1f, r2, 0.1f), a1 = fmaf(0.6f, r1, 0.6f), a2 = fmaf(0.3f, r0, 0.3f);
-        left = fmaf(a0, p0, fmaf(a1, p1, a2 * p2)) * vrcp(a0 + a1 + a2);
-    }
+    const float u0 = s0 * twelfth, u1 = s1 * twelfth, u2 = s2 * twelfth;
+    const float a0 = fmaf(0.1f, r0, 0.1f), a1 = fmaf(0.6f, r1, 0.6f), a2 = fmaf(0.3f, r2, 0.3f);
+    const float l0 = fmaf(0.1f, r2, 0.1f), l2 = fmaf(0.3f, r0, 0.3f);
+    right = fmaf(fmaf(a0, u0 + w0, fmaf(a1, u1 - w1, a2 * (u2 - w2))), vrcp(a0 + a1 + a2), v2);
+    left = fmaf(fmaf(l0, u2 + w2, fmaf(a1, u1 + w1, l2 * (u0 - w0))), vrcp(l0 + a1 + l2), v2);
 }
 
 // HLL flux along physical axis AX from the face states (primitives).
