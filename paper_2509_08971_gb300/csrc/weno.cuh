@@ -553,23 +553,40 @@ __device__ __forceinline__ void load_ev(const AdvectArgs<T>& A, int gx, int gy, 
     out[3] = DIM >= 3 ? m[2] / rho : T(0);
 }
 
-template <typename T>
-__device__ __forceinline__ T advect_face(const T e[6], const T u[6]) {
-    const T EL = weno5z(e[0], e[1], e[2], e[3], e[4]);
-    const T ER = weno5z(e[5], e[4], e[3], e[2], e[1]);
-    const T uL = weno5z(u[0], u[1], u[2], u[3], u[4]);
-    const T uR = weno5z(u[5], u[4], u[3], u[2], u[1]);
-    return rusanov_e(EL, ER, uL, uR);
-}
+// Shared memory of the advection kernel: E and the three velocities of the
+// haloed plane, two planes by parity; the face states of the plane's x faces
+// ([TY][TX+1]: E and u' on the left and right of each face) and y faces
+// ([TY+1][TX]: E and v').
+template <typename T, int TX, int TY, int DIM>
+struct AdvectSmem {
+    static constexpr int HX = TX + 2 * WENO_G, HY = DIM >= 2 ? TY + 2 * WENO_G : 1;
+    static constexpr int NPF = HX * HY;
+    static constexpr int NQX = (TX + 1) * TY;
+    static constexpr int NQY = DIM >= 2 ? TX * (TY + 1) : 0;
+    static constexpr size_t bytes = sizeof(T) * (2 * 4 * NPF + 4 * NQX + 4 * NQY);
+};
 
+// Per plane: every cell of the tile, and one halo cell on each side along the
+// axis, evaluates the WENO5-Z pair of E and of the normal velocity along x and
+// y (its upper value is the left state of the face above it, its lower value
+// the right state of the face below).  After the second barrier each thread
+// takes the Rusanov fluxes of its own cell's four faces from those states:
+// an interior face is evaluated by both of its cells (identically), which
+// keeps the block at two barriers per plane.  Along z the thread's own column
+// takes one pair per plane and quantity and carries the upper value to the
+// next face.  FP64 evaluates each value as weno5z of its stencil, exactly the
+// face-by-face form.
 template <typename T, int TX, int TY, int DIM, int PX, int PY>
 __global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T> A) {
+    using S = AdvectSmem<T, TX, TY, DIM>;
     constexpr int NT = TX * TY;
-    constexpr int HX = TX + 2 * WENO_G, HY = DIM >= 2 ? TY + 2 * WENO_G : 1;
-    constexpr int NPF = HX * HY;
-    __shared__ T Ps2[2 * 4 * NPF];                   // E, u', v', w' planes, two by plane parity
-    __shared__ T Fx[TY * (TX + 1)];
-    __shared__ T Fy[DIM >= 2 ? (TY + 1) * TX : 1];
+    constexpr int HX = S::HX, HY = S::HY, NPF = S::NPF, NQX = S::NQX, NQY = S::NQY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* Ps2 = reinterpret_cast<T*>(smem_raw);         // E, u', v', w' planes, two by plane parity
+    T* QxE = Ps2 + 2 * 4 * NPF;                       // [2][TY][TX+1]: left, right state of E
+    T* QxU = QxE + 2 * NQX;                           // [2][TY][TX+1]: of u'
+    T* QyE = QxU + 2 * NQX;                           // [2][TY+1][TX]: of E
+    T* QyV = QyE + 2 * NQY;                           // [2][TY+1][TX]: of v'
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX;
@@ -580,9 +597,11 @@ __global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T
     const bool own = x < A.n[0] && (DIM < 2 || y < A.n[1]);
     const T dt = (T)A.dt;
 
-    T we[6], ww[6], Fzp = T(0), Da = T(0), Db = T(0), Dc = T(0);
+    // z: E and w' of the last five planes, the pending left states of the
+    // next z face, the previous z-face flux, the x/y flux differences
+    T we[5], ww[5], eUp = T(0), wUp = T(0), Fzp = T(0), Da = T(0), Db = T(0), Dc = T(0);
 #pragma unroll
-    for (int s = 0; s < 6; ++s) we[s] = ww[s] = T(0);
+    for (int s = 0; s < 5; ++s) we[s] = ww[s] = T(0);
 
     const int jbeg = DIM == 3 ? z0 - WENO_G : 0;
     const int jend = DIM == 3 ? z1 + WENO_G : 1;
@@ -590,9 +609,9 @@ __global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T
         const bool xy = DIM < 3 || (j >= z0 && j < z1);
         T ej, wj, Dj;
         // two barriers per plane: the planes alternate by parity (plane j's is
-        // last read after the second barrier of plane j-2), and the face
-        // fluxes are written after the first barrier, which no thread passes
-        // before every thread has finished the previous plane
+        // last read after the second barrier of plane j-2); the face states
+        // are written after the first barrier, which no thread passes before
+        // every thread has finished the previous plane
         T* Ps = Ps2 + ((j - jbeg) & 1) * 4 * NPF;
         if (xy) {
             for (int e = tid; e < NPF; e += NT) {
@@ -603,36 +622,60 @@ __global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T
                 for (int f = 0; f < 4; ++f) Ps[f * NPF + e] = v[f];
             }
             __syncthreads();
-            for (int e = tid; e < (TX + 1) * TY; e += NT) {
-                const int fx = e % (TX + 1), row = e / (TX + 1);
-                const int hy = DIM >= 2 ? row + WENO_G : 0;
-                T ee[6], uu[6];
-#pragma unroll
-                for (int s = 0; s < 6; ++s) {
-                    ee[s] = Ps[0 * NPF + hy * HX + fx + s];
-                    uu[s] = Ps[1 * NPF + hy * HX + fx + s];
-                }
-                Fx[row * (TX + 1) + fx] = advect_face(ee, uu);
-            }
-            if (DIM >= 2) {
-                for (int e = tid; e < TX * (TY + 1); e += NT) {
-                    const int col = e % TX, fy = e / TX;
-                    T ee[6], vv[6];
-#pragma unroll
-                    for (int s = 0; s < 6; ++s) {
-                        ee[s] = Ps[0 * NPF + (fy + s) * HX + col + WENO_G];
-                        vv[s] = Ps[2 * NPF + (fy + s) * HX + col + WENO_G];
+            constexpr int NRX = (TX + 2) * TY, NRY = DIM >= 2 ? TX * (TY + 2) : 0;
+            for (int e = tid; e < NRX + NRY; e += NT) {
+                if (e < NRX) {
+                    // cell cx of the row: face cx+1 above it, face cx below
+                    const int cx = e % (TX + 2) - 1, row = e / (TX + 2);
+                    const int hy = DIM >= 2 ? row + WENO_G : 0;
+                    const T* ve = Ps + hy * HX + cx + WENO_G;
+                    const T* vu = ve + NPF;
+                    T er, el, ur, ul;
+                    weno5z_pair(ve[-2], ve[-1], ve[0], ve[1], ve[2], er, el);
+                    weno5z_pair(vu[-2], vu[-1], vu[0], vu[1], vu[2], ur, ul);
+                    const int q = row * (TX + 1) + cx;
+                    if (cx + 1 <= TX) {
+                        QxE[q + 1] = er;
+                        QxU[q + 1] = ur;
                     }
-                    Fy[fy * TX + col] = advect_face(ee, vv);
+                    if (cx >= 0) {
+                        QxE[NQX + q] = el;
+                        QxU[NQX + q] = ul;
+                    }
+                } else {
+                    const int e2 = e - NRX;
+                    const int col = e2 % TX, cy = e2 / TX - 1;
+                    const T* ve = Ps + (cy + WENO_G) * HX + col + WENO_G;
+                    const T* vv = ve + 2 * NPF;
+                    T er, el, vr, vl;
+                    weno5z_pair(ve[-2 * HX], ve[-HX], ve[0], ve[HX], ve[2 * HX], er, el);
+                    weno5z_pair(vv[-2 * HX], vv[-HX], vv[0], vv[HX], vv[2 * HX], vr, vl);
+                    const int q = cy * TX + col;
+                    if (cy + 1 <= TY) {
+                        QyE[q + TX] = er;
+                        QyV[q + TX] = vr;
+                    }
+                    if (cy >= 0) {
+                        QyE[NQY + q] = el;
+                        QyV[NQY + q] = vl;
+                    }
                 }
             }
             __syncthreads();
+            const int fx = ty * (TX + 1) + tx;        // the x face below this cell
+            const T Fxl = rusanov_e(QxE[fx], QxE[NQX + fx], QxU[fx], QxU[NQX + fx]);
+            const T Fxr = rusanov_e(QxE[fx + 1], QxE[NQX + fx + 1], QxU[fx + 1], QxU[NQX + fx + 1]);
+            Dj = sub_over_dx(T(0), Fxr - Fxl, A.dxk[0]);
+            if (DIM >= 2) {
+                const int fy = ty * TX + tx;          // the y face below this cell
+                const T Fyl = rusanov_e(QyE[fy], QyE[NQY + fy], QyV[fy], QyV[NQY + fy]);
+                const T Fyr = rusanov_e(QyE[fy + TX], QyE[NQY + fy + TX], QyV[fy + TX],
+                                        QyV[NQY + fy + TX]);
+                Dj = sub_over_dx(Dj, Fyr - Fyl, A.dxk[1]);
+            }
             const int hyc = DIM >= 2 ? ty + WENO_G : 0;
             ej = Ps[0 * NPF + hyc * HX + tx + WENO_G];
             wj = Ps[3 * NPF + hyc * HX + tx + WENO_G];
-            Dj = sub_over_dx(T(0), Fx[ty * (TX + 1) + tx + 1] - Fx[ty * (TX + 1) + tx], A.dxk[0]);
-            if (DIM >= 2)
-                Dj = sub_over_dx(Dj, Fy[(ty + 1) * TX + tx] - Fy[ty * TX + tx], A.dxk[1]);
         } else {
             T v[4];
             load_ev<T, DIM, PX, PY>(A, min(x, A.n[0] - 1), min(y, A.n[1] - 1), j, v);
@@ -645,14 +688,23 @@ __global__ void __launch_bounds__(TX * TY) weno_advect_kernel(const AdvectArgs<T
         if (DIM == 3) {
             const int cnt = j - jbeg;
 #pragma unroll
-            for (int s = 0; s < 5; ++s) {
+            for (int s = 0; s < 4; ++s) {
                 we[s] = we[s + 1];
                 ww[s] = ww[s + 1];
             }
-            we[5] = ej;
-            ww[5] = wj;
+            we[4] = ej;
+            ww[4] = wj;
+            // cell j-2 (planes j-4 .. j): its lower values close the face
+            // between j-3 and j-2; its upper values wait for the next plane
             T Fz = T(0);
-            if (cnt >= 5) Fz = advect_face(we, ww);
+            if (cnt >= 4) {
+                T eu, el, wu, wl;
+                weno5z_pair(we[0], we[1], we[2], we[3], we[4], eu, el);
+                weno5z_pair(ww[0], ww[1], ww[2], ww[3], ww[4], wu, wl);
+                if (cnt >= 5) Fz = rusanov_e(eUp, el, wUp, wl);
+                eUp = eu;
+                wUp = wu;
+            }
             k = cnt >= 6 ? j - WENO_G : -1;
             L = sub_over_dx(Da, Fz - Fzp, A.dxk[2]);
             if (cnt >= 5) Fzp = Fz;

@@ -70,7 +70,16 @@ template <int TX, int TY, int DIM, int PX, int PY>
 cudaError_t run_advect(const MeshDesc& m, const AdvectArgs<T>& A, cudaStream_t s) {
     const dim3 grid(wcdiv(m.n[0], TX), DIM >= 2 ? wcdiv(m.n[1], TY) : 1,
                     DIM == 3 ? wcdiv(m.n[2], A.zchunk) : 1);
-    weno_advect_kernel<T, TX, TY, DIM, PX, PY><<<grid, TX * TY, 0, s>>>(A);
+    constexpr size_t smem = AdvectSmem<T, TX, TY, DIM>::bytes;
+    auto kern = weno_advect_kernel<T, TX, TY, DIM, PX, PY>;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    kern<<<grid, TX * TY, smem, s>>>(A);
     return cudaGetLastError();
 }
 
