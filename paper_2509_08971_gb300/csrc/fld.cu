@@ -272,7 +272,14 @@ template <typename T>
 __global__ void __launch_bounds__(1024) coarse_solve_kernel(const LvlArgs<T> a, int sweeps) {
     // the level fits in shared memory (at most FLD_COARSE_SMEM cells)
     __shared__ T sx[FLD_COARSE_SMEM], sb[FLD_COARSE_SMEM], sD[FLD_COARSE_SMEM];
+    // changed[it & 1]: sweep it altered some x.  A sweep that alters nothing
+    // has reached a fixed point: every later sweep would return the same
+    // values, so the loop stops there with the result of all `sweeps`.  The
+    // slot of sweep it+1 is cleared after the first barrier of sweep it,
+    // when every thread has read sweep it-1's flag and none writes it yet.
+    __shared__ int changed[2];
     const int N = (int)a.N;
+    if (threadIdx.x == 0) changed[0] = 0;
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
         sx[q] = a.x[q];
         sb[q] = a.b[q];
@@ -283,18 +290,23 @@ __global__ void __launch_bounds__(1024) coarse_solve_kernel(const LvlArgs<T> a, 
     s.x = sx;
     s.b = sb;
     s.D = sD;
-    for (int it = 0; it < sweeps; ++it)
+    for (int it = 0; it < sweeps; ++it) {
         for (int color = 0; color < 2; ++color) {
+            if (color == 1 && threadIdx.x == 0) changed[(it + 1) & 1] = 0;
             for (int q = threadIdx.x; q < N; q += blockDim.x) {
                 const int i = q % a.n[0], t = q / a.n[0];
                 const int j = t % a.n[1], k = t / a.n[1];
                 if (((i + j + k) & 1) != color) continue;
                 T diag, off;
                 stencil(s, i, j, k, q, diag, off);
-                sx[q] = (sb[q] + off) / diag;
+                const T nx = (sb[q] + off) / diag;
+                if (!(nx == sx[q])) changed[it & 1] = 1;    // also NaN: keep sweeping
+                sx[q] = nx;
             }
             __syncthreads();
         }
+        if (!changed[it & 1]) break;              // the same value in every thread
+    }
     for (int q = threadIdx.x; q < N; q += blockDim.x) a.x[q] = sx[q];
 }
 
