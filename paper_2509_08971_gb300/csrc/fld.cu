@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int col
 // Residual of level l restricted to level l+1 in one pass: one thread per
 // coarse cell computes its children's residuals and writes their mean to the
 // coarse right-hand side, and zeroes the coarse correction.
-// H2: every axis coarsened by 2 (the children loops unrolled at compile
-// time, so their loads overlap); otherwise the factors h0, h1, h2 are read at
-// run time.  The children are summed in the same order either way.
+// H2: every axis coarsened by 2 (the children of each child plane loaded
+// together, then evaluated, so their loads overlap); otherwise the factors
+// h0, h1, h2 are read at run time.  The children are summed in the same order
+// (z, then y, then x) either way.
 template <typename T, bool H2>
 __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T> a, T* bc, T* xc,
                                                                 int nc0, int nc1, int h0, int h1,
@@ -190,20 +191,40 @@ __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T>
     const int J = blockIdx.y, K = blockIdx.z;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc0) return;
-    if (H2) h0 = h1 = h2 = 2;
     T sum = T(0);
+    if (H2) {
+        h0 = h1 = h2 = 2;
+        // per child plane: the four children's loads, then their residuals
 #pragma unroll
-    for (int cz = 0; cz < (H2 ? 2 : h2); ++cz)
+        for (int cz = 0; cz < 2; ++cz) {
+            StencilVals<T> v[4];
+            T bq[4], xq[4];
 #pragma unroll
-        for (int cy = 0; cy < (H2 ? 2 : h1); ++cy)
-#pragma unroll
-            for (int cx = 0; cx < (H2 ? 2 : h0); ++cx) {
-                const int i = I * h0 + cx, j = J * h1 + cy, k = K * h2 + cz;
+            for (int c = 0; c < 4; ++c) {
+                const int i = 2 * I + (c & 1), j = 2 * J + (c >> 1), k = 2 * K + cz;
                 const int q = (k * a.n[1] + j) * a.n[0] + i;
-                T diag, off;
-                stencil(a, i, j, k, q, diag, off);
-                sum += a.b[q] - (diag * a.x[q] - off);
+                stencil_load(a, i, j, k, q, v[c]);
+                bq[c] = a.b[q];
+                xq[c] = a.x[q];
             }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                T diag, off;
+                stencil_eval(a, v[c], diag, off);
+                sum += bq[c] - (diag * xq[c] - off);
+            }
+        }
+    } else {
+        for (int cz = 0; cz < h2; ++cz)
+            for (int cy = 0; cy < h1; ++cy)
+                for (int cx = 0; cx < h0; ++cx) {
+                    const int i = I * h0 + cx, j = J * h1 + cy, k = K * h2 + cz;
+                    const int q = (k * a.n[1] + j) * a.n[0] + i;
+                    T diag, off;
+                    stencil(a, i, j, k, q, diag, off);
+                    sum += a.b[q] - (diag * a.x[q] - off);
+                }
+    }
     const int Q = (K * nc1 + J) * nc0 + I;
     bc[Q] = sum / T(h0 * h1 * h2);
     xc[Q] = T(0);
@@ -332,14 +353,31 @@ __global__ void __launch_bounds__(256) restrict_kernel(const T* fine, T* coarse,
 }
 
 // fine[i] += coarse[parent(i)]
+// fine += the coarse correction of the parent cell (piecewise constant).  Each
+// thread takes its x cell in SMOOTH_ROWS consecutive rows, loads first.
 template <typename T>
 __global__ void __launch_bounds__(128) prolong_kernel(T* fine, const T* coarse, int nf0, int nf1,
                                                       int nc0, int nc1, int h0, int h1, int h2) {
-    const int j = blockIdx.y, k = blockIdx.z;
+    const int k = blockIdx.z;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf0) return;
-    const long long q = ((long long)k * nf1 + j) * nf0 + i;
-    fine[q] += coarse[((long long)(k / h2) * nc1 + j / h1) * nc0 + i / h0];
+    const int ic = i / h0;
+    const long long kc = (long long)(k / h2) * nc1;
+    T f[SMOOTH_ROWS], c[SMOOTH_ROWS];
+    long long qs[SMOOTH_ROWS];
+    bool on[SMOOTH_ROWS];
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r) {
+        const int j = blockIdx.y * SMOOTH_ROWS + r;
+        on[r] = j < nf1;
+        const int jj = on[r] ? j : 0;
+        qs[r] = ((long long)k * nf1 + jj) * nf0 + i;
+        f[r] = fine[qs[r]];
+        c[r] = coarse[(kc + jj / h1) * nc0 + ic];
+    }
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r)
+        if (on[r]) fine[qs[r]] = f[r] + c[r];
 }
 
 // D = c lambda(R) / (kappa rho), R = |grad E| / (rho kappa E), on level 0
@@ -467,7 +505,9 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
         for (int l = H->nl - 2; l >= 0; --l) {
             const FldLevel& F = H->L[l];
             const FldLevel& C = H->L[l + 1];
-            prolong_kernel<T><<<rows_grid(F, 1), 128, 0, s>>>(
+            dim3 gp = rows_grid(F, 1);
+            gp.y = (gp.y + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
+            prolong_kernel<T><<<gp, 128, 0, s>>>(
                 static_cast<T*>(F.x), static_cast<const T*>(C.x), F.n[0], F.n[1], C.n[0], C.n[1],
                 F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
             if ((e = smooth<T>(H, l, dt, FLD_POST, s)) != cudaSuccess) return e;
