@@ -249,9 +249,9 @@ struct WenoSmem {
     static constexpr int NP = NF * HX * HY;
     static constexpr int NFX = NF * TY * (TX + 1);                 // one x-face array
     static constexpr int NFY = DIM >= 2 ? NF * (TY + 1) * TX : 0;  // one y-face array
-    // two primitive planes (by plane parity); face states (left, right) and
-    // fluxes of the x and y faces
-    static constexpr size_t bytes = sizeof(T) * (2 * NP + 3 * NFX + 3 * NFY);
+    // two primitive planes (by plane parity); face states (left, right) of
+    // the x and y faces
+    static constexpr size_t bytes = sizeof(T) * (2 * NP + 2 * NFX + 2 * NFY);
 };
 
 template <typename T, int TX, int TY, int DIM, int PX, int PY>
@@ -264,11 +264,9 @@ weno_stage_kernel(const StageArgs<T> A) {
     __shared__ double red_tot[NT / 32][NF];
     __shared__ unsigned long long red_rate[NT / 32];
     T* Ps2 = reinterpret_cast<T*>(smem_raw);         // 2 x [NF][HY][HX]
-    T* Fx = Ps2 + 2 * S::NP;                          // [NF][TY][TX+1]
-    T* QLx = Fx + S::NFX;                             // left states of the x faces
+    T* QLx = Ps2 + 2 * S::NP;                         // left states of the x faces [NF][TY][TX+1]
     T* QRx = QLx + S::NFX;                            // right states
-    T* Fy = QRx + S::NFX;                             // [NF][TY+1][TX]
-    T* QLy = Fy + S::NFY;
+    T* QLy = QRx + S::NFX;                            // of the y faces [NF][TY+1][TX]
     T* QRy = QLy + S::NFY;
 
     const int tid = threadIdx.x;
@@ -303,12 +301,14 @@ weno_stage_kernel(const StageArgs<T> A) {
     for (int j = jbeg; j < jend; ++j) {
         const bool xy = DIM < 3 || (j >= z0 && j < z1);
         T qj[NF], Dj[NF];
-        // Three barriers per plane.  The primitive planes alternate by parity:
-        // plane j's is last read (own cell) after the third barrier of plane
+        // Two barriers per plane.  The primitive planes alternate by parity:
+        // plane j's is last read (own cell) after the second barrier of plane
         // j-2, and every thread has passed the barriers of plane j-1 before
-        // any thread writes plane j; the face states and fluxes of plane j
-        // are written after its first barrier, which no thread passes before
-        // every thread has finished plane j-1.
+        // any thread writes plane j; the face states of plane j are written
+        // after its first barrier, which no thread passes before every thread
+        // has finished plane j-1.  Each thread takes the HLL fluxes of its
+        // own cell's four x/y faces from the face states (an interior face is
+        // evaluated by both of its cells, identically).
         T* Ps = Ps2 + ((j - jbeg) & 1) * S::NP;
         if (xy) {
             for (int e = tid; e < HX * HY; e += NT) {
@@ -350,41 +350,44 @@ weno_stage_kernel(const StageArgs<T> A) {
                 }
             }
             __syncthreads();
-            // the HLL flux of every x and y face of the plane
-            constexpr int NX = (TX + 1) * TY, NY = DIM >= 2 ? TX * (TY + 1) : 0;
-            for (int e = tid; e < NX + NY; e += NT) {
-                T qL[NF], qR[NF], F[NF];
-                if (e < NX) {
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        qL[f] = QLx[f * NX + e];
-                        qR[f] = QRx[f * NX + e];
-                    }
-                    hll_face<PX>(qL, qR, gamma, gx, F);
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) Fx[f * NX + e] = F[f];
-                } else {
-                    const int e2 = e - NX;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        qL[f] = QLy[f * NY + e2];
-                        qR[f] = QRy[f * NY + e2];
-                    }
-                    hll_face<PY>(qL, qR, gamma, gx, F);
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) Fy[f * NY + e2] = F[f];
-                }
-            }
-            __syncthreads();
             const int hyc = DIM >= 2 ? ty + WENO_G : 0;
+            {
+                constexpr int NX = (TX + 1) * TY, NY = DIM >= 2 ? TX * (TY + 1) : 0;
+                const int ex = ty * (TX + 1) + tx;    // the x face below this cell
+                T qL[NF], qR[NF], Fl[NF], Fr[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                qj[f] = Ps[(f * HY + hyc) * HX + tx + WENO_G];
-                const T a = Fx[(f * TY + ty) * (TX + 1) + tx + 1] - Fx[(f * TY + ty) * (TX + 1) + tx];
-                Dj[f] = sub_over_dx(T(0), a, A.dxk[0]);
+                for (int f = 0; f < NF; ++f) {
+                    qL[f] = QLx[f * NX + ex];
+                    qR[f] = QRx[f * NX + ex];
+                }
+                hll_face<PX>(qL, qR, gamma, gx, Fl);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    qL[f] = QLx[f * NX + ex + 1];
+                    qR[f] = QRx[f * NX + ex + 1];
+                }
+                hll_face<PX>(qL, qR, gamma, gx, Fr);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    qj[f] = Ps[(f * HY + hyc) * HX + tx + WENO_G];
+                    Dj[f] = sub_over_dx(T(0), Fr[f] - Fl[f], A.dxk[0]);
+                }
                 if (DIM >= 2) {
-                    const T b = Fy[(f * (TY + 1) + ty + 1) * TX + tx] - Fy[(f * (TY + 1) + ty) * TX + tx];
-                    Dj[f] = sub_over_dx(Dj[f], b, A.dxk[1]);
+                    const int ey = ty * TX + tx;      // the y face below this cell
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        qL[f] = QLy[f * NY + ey];
+                        qR[f] = QRy[f * NY + ey];
+                    }
+                    hll_face<PY>(qL, qR, gamma, gx, Fl);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        qL[f] = QLy[f * NY + ey + TX];
+                        qR[f] = QRy[f * NY + ey + TX];
+                    }
+                    hll_face<PY>(qL, qR, gamma, gx, Fr);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) Dj[f] = sub_over_dx(Dj[f], Fr[f] - Fl[f], A.dxk[1]);
                 }
             }
         } else {
