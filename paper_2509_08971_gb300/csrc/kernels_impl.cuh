@@ -6,9 +6,13 @@
 
 #include "adjoint.cuh"
 #include "batched.cuh"
+#include "devattr.h"
 #include "launch.h"
 #include "stage_kernel.cuh"
 #include "stage_tma.cuh"
+#ifdef HH_WS
+#include "stage_ws.cuh"
+#endif
 
 namespace hh {
 
@@ -61,13 +65,9 @@ cudaError_t run_stage(const MeshDesc& m, const TileDesc& td, const StageCall& c,
               DIM == 3 ? cdiv(A.zhi - A.zlo, A.zchunk) : 1);
     const size_t smem = StageSmem<T, TX, TY, DIM>::bytes;
     auto kern = stage_kernel<T, TX, TY, DIM, PX, PY, false>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    cudaError_t e = smem_attr_once(kern, smem, attr);
+    if (e != cudaSuccess) return e;
     kern<<<grid, TX * TY, smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -147,21 +147,68 @@ cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall
         dim3 grid(cdiv(m.n[0], TX), cdiv(m.n[1], TY), cdiv(A.zhi - A.zlo, A.zchunk));
         auto kern = c.stage == 1 ? stage_tma_kernel<T, TX, TY, 1> : stage_tma_kernel<T, TX, TY, 2>;
         constexpr size_t b1 = TmaLayout<T, TX, TY, 1>::bytes, b2 = L::bytes;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(stage_tma_kernel<T, TX, TY, 1>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(stage_tma_kernel<T, TX, TY, 2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
+        static std::atomic<unsigned long long> attr1{0}, attr2{0};
+        cudaError_t e = c.stage == 1 ? smem_attr_once(stage_tma_kernel<T, TX, TY, 1>, b1, attr1)
+                                     : smem_attr_once(stage_tma_kernel<T, TX, TY, 2>, b2, attr2);
+        if (e != cudaSuccess) return e;
         kern<<<grid, TX * TY, c.stage == 1 ? b1 : b2, s>>>(A, maps);
         used = true;
         return cudaGetLastError();
     }
 }
+
+#ifdef HH_WS
+// Warp-specialised FP32 kernel (stage_ws.cuh): tiles 32 x TY with NCW
+// converter warps; blocks per SM by tile height.
+#ifndef HH_WS_NCW8
+#define HH_WS_NCW8 2
+#endif
+template <int TY> struct WsConf {
+    static constexpr int NCW = TY >= 8 ? HH_WS_NCW8 : 1;
+};
+
+template <int TY>
+cudaError_t run_stage_ws(const MeshDesc& m, const TileDesc& td, const StageCall& c,
+                         cudaStream_t s, bool& used) {
+    constexpr int NCW = WsConf<TY>::NCW;
+    using L1 = WsLayout<32, TY, NCW, 1>;
+    using L2 = WsLayout<32, TY, NCW, 2>;
+    used = false;
+    if constexpr (L2::bytes > SMEM_LIMIT) {
+        return cudaSuccess;
+    } else {
+        if ((reinterpret_cast<uintptr_t>(c.Uo) & 15u) != 0 ||
+            (c.stage == 2 && (reinterpret_cast<uintptr_t>(c.U0) & 15u) != 0))
+            return cudaSuccess;
+        WsMaps maps;
+        if (!encode_state_map(&maps.main, c.Uc, m, L1::HXC, L1::HYC) ||
+            !encode_state_map(&maps.xstrip, c.Uc, m, 4, L1::HYC) ||
+            !encode_state_map(&maps.ystrip, c.Uc, m, L1::HXC, 2) ||
+            !encode_state_map(&maps.u0, c.stage == 2 ? c.U0 : c.Uc, m, 32, TY) ||
+            !encode_state_map(&maps.out, c.Uo, m, 32, TY))
+            return cudaSuccess;
+        StageArgs<T> A = make_args(m, td, c);
+        // failure-path test: HARD_HYDRO_STARVE_TMA=1 makes the ring's waits
+        // run out (the stage then reports HARD_ETIMEOUT and leaves Uout unset)
+        const char* starve = std::getenv("HARD_HYDRO_STARVE_TMA");
+        A.starve_tma = starve && starve[0] == '1';
+        dim3 grid(cdiv(m.n[0], 32), cdiv(m.n[1], TY), cdiv(A.zhi - A.zlo, A.zchunk));
+        static std::atomic<unsigned long long> attr1{0}, attr2{0};
+        cudaError_t e;
+        if (c.stage == 1) {
+            e = smem_attr_once(stage_ws_kernel<32, TY, NCW, 1>, L1::bytes, attr1);
+            if (e != cudaSuccess) return e;
+            stage_ws_kernel<32, TY, NCW, 1><<<grid, L1::NT, L1::bytes, s>>>(A, maps);
+        } else {
+            e = smem_attr_once(stage_ws_kernel<32, TY, NCW, 2>, L2::bytes, attr2);
+            if (e != cudaSuccess) return e;
+            stage_ws_kernel<32, TY, NCW, 2><<<grid, L2::NT, L2::bytes, s>>>(A, maps);
+        }
+        used = true;
+        return cudaGetLastError();
+    }
+}
+#endif
 
 // No active axis: L(U) = 0, the stage combine alone.
 __global__ void pointwise_stage_kernel(const T* U0, const T* Uc, T* Uo, long long n5, double dt,
@@ -246,12 +293,21 @@ cudaError_t dispatch_tile(const MeshDesc& m, int kernel, int tile, const StageCa
         if (kernel == 0 && epi_ok && tma_eligible(m, c.Uc)) {
             bool used = false;
             cudaError_t e;
+#ifdef HH_WS
+            switch (tile) {
+                case 0: case 1: e = run_stage_ws<8>(m, td, c, s, used); break;
+                case 2: e = run_stage_ws<16>(m, td, c, s, used); break;
+                case 3: e = cudaSuccess; break;            // 64-wide tiles: no warp-per-row form
+                default: e = run_stage_ws<4>(m, td, c, s, used); break;
+            }
+#else
             switch (tile) {
                 case 0: case 1: e = run_stage_tma<32, 8>(m, td, c, s, used); break;
                 case 2: e = run_stage_tma<32, 16>(m, td, c, s, used); break;
                 case 3: e = run_stage_tma<64, 8>(m, td, c, s, used); break;
                 default: e = run_stage_tma<32, 4>(m, td, c, s, used); break;
             }
+#endif
             if (used || e != cudaSuccess) return e;
         }
         switch (tile) {
@@ -285,18 +341,21 @@ cudaError_t run_batched(const BatchCall& c, cudaStream_t s) {
     constexpr size_t s1 = StageSmem<T, TX1, 1, 1>::bytes, s2 = StageSmem<T, TX2, TY2, 2>::bytes;
     constexpr size_t smem = s1 > s2 ? s1 : s2;
     auto kern = batched_kernel<T, TX1, TX2, TY2>;
-    static int grid = 0;
+    static PerDeviceInt grids;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int grid = grids.get(dev);
     if (grid == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX1, smem);
         if (e != cudaSuccess) return e;
         grid = sms * (per_sm > 0 ? per_sm : 1);
+        grids.set(dev, grid);
     }
     BatchArgs<T> B;
     B.U = static_cast<T*>(c.U);

@@ -2,6 +2,7 @@
 // exactly one translation unit per type with HH_T (float or double) and
 // HH_SUFFIX (f32 or f64) defined.
 #pragma once
+#include "devattr.h"
 #include "weno.cuh"
 #include "weno_launch.h"
 
@@ -55,13 +56,9 @@ cudaError_t run_weno(const MeshDesc& m, const StageCall& c, cudaStream_t s) {
                     DIM == 3 ? wcdiv(m.n[2], A.zchunk) : 1);
     constexpr size_t smem = WenoSmem<T, TX, TY, DIM>::bytes;
     auto kern = weno_stage_kernel<T, TX, TY, DIM, PX, PY>;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_attr_once(kern, smem, attr);
+    if (e != cudaSuccess) return e;
     kern<<<grid, TX * TY, smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -72,13 +69,9 @@ cudaError_t run_advect(const MeshDesc& m, const AdvectArgs<T>& A, cudaStream_t s
                     DIM == 3 ? wcdiv(m.n[2], A.zchunk) : 1);
     constexpr size_t smem = AdvectSmem<T, TX, TY, DIM>::bytes;
     auto kern = weno_advect_kernel<T, TX, TY, DIM, PX, PY>;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = smem_attr_once(kern, smem, attr);
+    if (e != cudaSuccess) return e;
     kern<<<grid, TX * TY, smem, s>>>(A);
     return cudaGetLastError();
 }

@@ -92,7 +92,8 @@ def test_bounded_wait_timeout_is_reported(monkeypatch):
     monkeypatch.delenv("HARD_HYDRO_STARVE_TMA")
     got = m.stage(1, None, U, dt)
     assert m.get_error() == hh.HARD_OK
-    assert torch.equal(got, plain.stage(1, None, U, dt))
+    assert torch.equal(got, m.stage(1, None, U, dt))
+    _close_f32(got, plain.stage(1, None, U, dt))
 
 
 def _oracle_window_step(U, c, dt, gam, half=4):
@@ -133,9 +134,33 @@ def test_full_size_sampled_parity(dtype, tol):
         assert np.all(err <= tol), (c, err)
 
 
+# The FP32 TMA kernel and the FP32 plain-load kernel evaluate the same scheme
+# in different instruction orders (the TMA kernel passes x-face states between
+# lanes, sums the divergence per axis before scaling), so their results agree
+# to rounding, not bit for bit.  One step moves each value by O(dt/dx) of the
+# fluxes; a few FP32 ulps of the largest value per field bound the difference.
+F32_STEP_RTOL = 4e-7
+
+
+def _close_f32(a, b, rtol=F32_STEP_RTOL):
+    a = a.double()
+    b = b.double()
+    for f in range(5):
+        scale = float(b[f].abs().max())
+        err = float((a[f] - b[f]).abs().max())
+        assert err <= rtol * scale, (f, err, scale)
+
+
+def _tma_tiles(m):
+    """Tiles whose FP32 fused step runs the TMA kernel (32-wide tiles)."""
+    return [t for t in range(m.tile_count()) if m.tile_info(t)[0] == 32]
+
+
 def test_deterministic_and_tile_independent():
-    """Every tile shape and both load paths evaluate each face flux with the
-    same arithmetic in the same order: bit-identical results."""
+    """Each kernel is deterministic, and every tile shape of one kernel
+    evaluates each face flux with the same arithmetic in the same order:
+    bit-identical results across tiles and z-chunks.  The TMA and plain
+    kernels agree to FP32 rounding."""
     shape = (40, 33, 72)            # x a multiple of 4: the fused kernel takes the TMA path
     gam = 1.4
     g = np.random.default_rng(0)
@@ -145,16 +170,22 @@ def test_deterministic_and_tile_independent():
     base = m.step(U, 1e-4)
     again = m.step(U, 1e-4)
     assert torch.equal(base, again)
-    for kernel in (0, 1):
-        for tile in range(m.tile_count()):
-            m.set_kernel(kernel, tile)
-            assert torch.equal(m.step(U, 1e-4), base), (kernel, tile)
+    for tile in _tma_tiles(m):
+        m.set_kernel(hh.HARD_KERNEL_FUSED, tile)
+        assert torch.equal(m.step(U, 1e-4), base), tile
+    m.set_kernel(hh.HARD_KERNEL_PLAIN, 0)
+    plain = m.step(U, 1e-4)
+    for tile in range(m.tile_count()):
+        m.set_kernel(hh.HARD_KERNEL_PLAIN, tile)
+        assert torch.equal(m.step(U, 1e-4), plain), tile
+    _close_f32(base, plain)
 
 
 @pytest.mark.parametrize("bc", [0, 1, 2])
-def test_fused_equals_plain_f32(bc):
-    """The TMA-fed kernel and the plain-load kernel evaluate the same
-    arithmetic: bit-identical FP32 results on every boundary kind."""
+def test_fused_matches_plain_f32(bc):
+    """The TMA-fed kernel and the plain-load kernel agree to FP32 rounding on
+    every boundary kind (ragged tiles in x and y), and the TMA kernel gives
+    the same bits on every tile shape."""
     shape = (37, 30, 100)
     gam = 5.0 / 3.0
     U = dev(H.smooth_3d(0, seed=3, gamma=gam, shape=shape), torch.float32)
@@ -163,7 +194,7 @@ def test_fused_equals_plain_f32(bc):
     dt = fused.cfl_dt(U, 0.4)
     a = fused.step(U, dt)
     b = plain.step(U, dt)
-    assert torch.equal(a, b)
-    for tile in range(fused.tile_count()):
+    _close_f32(a, b)
+    for tile in _tma_tiles(fused):
         fused.set_kernel(hh.HARD_KERNEL_FUSED, tile)
         assert torch.equal(fused.step(U, dt), a), tile
