@@ -1,11 +1,15 @@
 """Benchmark of the fused hydro stage update on GB300.
 
-Workload: the 3D periodic smooth flow on a 256^3 mesh (gamma = 5/3, entropy
-wave rho = 1 + 0.2 sin(2 pi (x+y+z)) advected at (1,1,1), p = 1, plus seeded
-acoustic modes of amplitude 1e-3 in the 8 lowest wave vectors), CFL 0.4.
-A step is one pass of the whole path: the CFL time step from the fused
-signal-rate reduction, both Runge-Kutta stages, and the FP64 conserved totals
-of the new state.  The state (336 MB in FP32) is larger than the 129 MB L2.
+Headline workload: the strong spherical blast on a 512^3 mesh (gamma = 1.4,
+ambient rho = 1 with seeded +-1 % noise, p = 1e-5, total energy 1 spread over
+the cells within four cells of the centre, reflecting walls, CFL 0.3), FP32
+bulk with FP64 conserved-total reductions, 200 steps from t = 0.  A step is
+one pass of the whole path: the CFL time step from the fused signal-rate
+reduction, both Runge-Kutta stages, and the FP64 conserved totals of the new
+state.  The state (2.7 GB in FP32) is far larger than the 129 MB L2.  The
+FP64 plain path runs the same configuration; the 256^3 periodic smooth flow
+(gamma = 5/3, CFL 0.4) is a secondary line, as are the second scheme, the
+radiation operators, the batched launch and the adjoint.
 
 metric: cell-updates per RK stage per second = cells * 2 * steps / time.
 
@@ -32,18 +36,27 @@ if ROOT not in sys.path:
 
 METRIC = "cell-updates/s per RK stage (FP32 fused vs FP64 plain) and % HBM roofline"
 UNIT = "cell-updates/s"
-N_SIDE = 256
-GAMMA = 5.0 / 3.0
-CFL = 0.4
-WORKLOAD = ("3D periodic smooth flow 256^3, gamma=5/3, entropy wave + 8 seeded acoustic "
-            "modes (amplitude 1e-3), CFL 0.4")
+N_SIDE = 512
+GAMMA = 1.4
+CFL = 0.3
+STEPS = 200
+WORKLOAD = ("3D strong spherical blast 512^3, gamma=1.4, ambient rho=1 with seeded +-1% noise, "
+            "p=1e-5, energy 1.0 within 4 cells of the centre, reflecting walls, CFL 0.3, "
+            "200 steps; FP32 bulk with FP64 conserved-total reductions")
+SMOOTH_N = 256
+SMOOTH_GAMMA = 5.0 / 3.0
+SMOOTH_CFL = 0.4
+SMOOTH_WORKLOAD = ("3D periodic smooth flow 256^3, gamma=5/3, entropy wave + 8 seeded acoustic "
+                   "modes (amplitude 1e-3), CFL 0.4")
 BYTES_PER_CELL_STAGE = {4: 50.0, 8: 100.0}     # algorithmic: (5+5 + 10+5)/2 values
 L2_BYTES = 129 * 2 ** 20
 
 
 # The sources the profiled stage kernel is compiled and launched from.
-STAGE_KERNEL_SOURCES = ("hydro_math.cuh", "kernels_impl.cuh", "launch.h", "stage_f32.cu",
-                        "stage_kernel.cuh", "stage_tma.cuh", "tma.cuh", "vec2.cuh")
+STAGE_KERNEL_SOURCES = ("devattr.h", "hydro_math.cuh", "kernels_impl.cuh", "launch.h",
+                        "stage_f32.cu", "stage_kernel.cuh", "stage_tma.cuh", "stage_ws.cuh",
+                        "tma.cuh", "vec2.cuh")
+STAGE_PROFILE = os.path.join("profiles", "stage_ws_kernel_blast3d_256.md")
 
 
 def kernel_sources_digest():
@@ -60,10 +73,11 @@ def kernel_sources_digest():
 
 def profiled(key):
     """A figure of the committed ncu summary of the stage kernel
-    ("traffic-bytes-per-launch": DRAM bytes read + written per launch, mean of
-    the two stages; "instructions-per-cell-stage": thread instructions per
-    cell, mean of the two stages), or None when the kernels changed since."""
-    path = os.path.join(ROOT, "profiles", "stage_tma_kernel_smooth3d_256.md")
+    ("traffic-bytes-per-cell-stage": DRAM bytes read + written per cell, mean
+    of the two stage launches; "instructions-per-cell-stage": warp-instruction
+    issue slots x 32 per cell, mean of the two), or None when the kernel's
+    sources changed since the capture."""
+    path = os.path.join(ROOT, STAGE_PROFILE)
     try:
         rec = {}
         with open(path) as fh:
@@ -78,8 +92,12 @@ def profiled(key):
         return None
 
 
-def profiled_traffic():
-    return profiled("traffic-bytes-per-launch")
+def profiled_traffic(cells):
+    """DRAM bytes per stage launch on `cells` cells: the profiled per-cell
+    figure (captured on a 256^3 case of the same kernel) times the cells; the
+    kernel streams each plane once, so its traffic grows with the cells."""
+    b = profiled("traffic-bytes-per-cell-stage")
+    return None if b is None else b * cells
 
 
 SCHEDULERS = 152 * 4       # GB300: 152 SMs, four warp schedulers each
@@ -220,41 +238,72 @@ def cpu_threads():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
-def time_oracle(shape, steps, threads):
-    """The oracle as it stands (FP64 C, OpenMP over cells) on the same
-    per-cell arithmetic.  Returns (cell-stages/s, seconds, threads used)."""
+def blast_slab(planes):
+    """The middle `planes` z planes of the 512^3 blast (seed 0): the same cells,
+    noise and energy density as the full state, the blast inside."""
     import hydro_inputs as H
+    k0 = (N_SIDE - planes) // 2
+    return H.blast_3d(N_SIDE, seed=0, gamma=GAMMA, planes=(k0, k0 + planes))
+
+
+def time_oracle(U, steps, threads, bc, gamma, cfl):
+    """The oracle as it stands (FP64 C, OpenMP over cells) on state U.
+    Returns (cell-stages/s, seconds, threads used)."""
     import oracle
     oracle.set_threads(threads)
     used = oracle.get_threads()
-    U = H.smooth_3d(0, seed=0, gamma=GAMMA, shape=shape)
-    g = oracle.Grid(shape, GAMMA, oracle.BC_PERIODIC)
+    shape = U.shape[1:]
+    g = oracle.Grid(shape, gamma, bc)
     t0 = time.perf_counter()
-    g.run(U, steps, CFL)
+    g.run(U, steps, cfl)
     sec = time.perf_counter() - t0
     cells = shape[0] * shape[1] * shape[2]
     return cells * 2 * steps / sec, sec, used
 
 
+def time_oracle_riemann():
+    """Configuration 1 in full: the seeded two-state problem (seed 0) on 400
+    cells, outflow, CFL 0.4, run to t = 0.15 by the oracle on one thread.
+    Returns (cell-stages/s, seconds, steps)."""
+    import hydro_inputs as H
+    import oracle
+    oracle.set_threads(1)
+    pb = H.riemann_1d(0)
+    U = pb.U(400)
+    g = oracle.Grid((1, 1, 400), pb.gamma, oracle.BC_OUTFLOW)
+    t0 = time.perf_counter()
+    _, _, dts = g.run(U, 10 ** 6, 0.4, 0.15)
+    sec = time.perf_counter() - t0
+    return 400 * 2 * len(dts) / sec, sec, len(dts)
+
+
+REF_PLANES = 8          # z planes of the blast per reference step
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle on the host cores, each step a
-    bounded sample of the workload (a 256 x 256 x 8 periodic slab of the same
-    flow: the same per-cell arithmetic at 1/32 of the cells)."""
+    bounded sample of the workload: the middle 8 z planes of the 512^3 blast
+    (512 x 512 x 8 cells, reflecting walls, CFL 0.3), the same per-cell
+    arithmetic at 1/64 of the cells."""
     if rank != 0:
         return
-    shape = (8, N_SIDE, N_SIDE)
+    import oracle
+    U = blast_slab(REF_PLANES)
     threads = cpu_threads()
-    time_oracle(shape, max(args.warmup, 0), threads) if args.warmup else None
-    rate, sec, used = time_oracle(shape, args.steps, threads)
+    if args.warmup:
+        time_oracle(U, args.warmup, threads, oracle.BC_REFLECT, GAMMA, CFL)
+    rate, sec, used = time_oracle(U, args.steps, threads, oracle.BC_REFLECT, GAMMA, CFL)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "256x256x8 periodic slab per step",
-                   "cells_per_step": shape[0] * shape[1] * shape[2]},
+        "config": {"workload": WORKLOAD,
+                   "sample": f"the middle {REF_PLANES} z planes of the 512^3 blast per step",
+                   "cells_per_step": REF_PLANES * N_SIDE * N_SIDE},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
-                         "sample": f"{args.steps} RK2 steps of a 256x256x8 slab"},
+                         "sample": f"{args.steps} RK2 steps of a 512x512x{REF_PLANES} slab "
+                                   "of the blast"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -297,20 +346,20 @@ def precision_report():
     rep["riemann_1d_400_fp32_vs_oracle"] = worst
     # configuration 2: smooth 3D flow, 100 steps
     n = 64
-    U = H.smooth_3d(n, seed=0, gamma=GAMMA)
-    ref, _, _ = oracle.Grid((n, n, n), GAMMA, oracle.BC_PERIODIC).run(U, 100, CFL)
-    m = hh.HardHydro((n, n, n), GAMMA, 0)
+    U = H.smooth_3d(n, seed=0, gamma=SMOOTH_GAMMA)
+    ref, _, _ = oracle.Grid((n, n, n), SMOOTH_GAMMA, oracle.BC_PERIODIC).run(U, 100, SMOOTH_CFL)
+    m = hh.HardHydro((n, n, n), SMOOTH_GAMMA, 0)
     Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
-    m.advance(Ud, 100, CFL)
+    m.advance(Ud, 100, SMOOTH_CFL)
     rep["smooth_3d_64_fp32_vs_oracle"] = _field_errors(Ud.cpu().numpy(), ref)
     n = 256
-    U = H.smooth_3d(n, seed=0, gamma=GAMMA)
-    m64 = hh.HardHydro((n, n, n), GAMMA, 0, dtype=torch.float64)
+    U = H.smooth_3d(n, seed=0, gamma=SMOOTH_GAMMA)
+    m64 = hh.HardHydro((n, n, n), SMOOTH_GAMMA, 0, dtype=torch.float64)
     V = torch.tensor(U, dtype=torch.float64, device="cuda")
-    m64.advance(V, 100, CFL)
-    m32 = hh.HardHydro((n, n, n), GAMMA, 0)
+    m64.advance(V, 100, SMOOTH_CFL)
+    m32 = hh.HardHydro((n, n, n), SMOOTH_GAMMA, 0)
     Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
-    m32.advance(Ud, 100, CFL)
+    m32.advance(Ud, 100, SMOOTH_CFL)
     rep["smooth_3d_256_fp32_vs_fp64_gpu"] = _field_errors(Ud.cpu().numpy(), V.cpu().numpy())
     del V, Ud, m64, m32
     # configuration 3: spherical blast 512^3, reflecting walls, CFL 0.3
@@ -345,7 +394,7 @@ def precision_report():
     # configuration 5: shear layer 256^2, 200 steps
     n = 256
     U = H.shear_2d(n, seed=0, gamma=1.4)
-    ref, _, dts = oracle.Grid((1, n, n), 1.4, oracle.BC_PERIODIC).run(U, 200, CFL)
+    ref, _, dts = oracle.Grid((1, n, n), 1.4, oracle.BC_PERIODIC).run(U, 200, SMOOTH_CFL)
     m = hh.HardHydro((1, n, n), 1.4, 0)
     Ud = torch.tensor(U, dtype=torch.float32, device="cuda")
     for dt in dts:
@@ -354,15 +403,46 @@ def precision_report():
     print(json.dumps(rep), flush=True)
 
 
+def stage_roofline(m, U, hbm, peak_kind, kernel_name, reps=20):
+    """Mean CUDA-event time of the stage-1 and stage-2 launches of handle m on
+    state U (inputs larger than L2), against the HBM roofline at the
+    algorithmic 50 B per FP32 cell-stage."""
+    import torch
+    stream = torch.cuda.current_stream()
+    cells = U[0].numel()
+    U1, U2 = torch.empty_like(U), torch.empty_like(U)
+    dt = m.cfl_dt(U, CFL)
+    for _ in range(3):
+        m.stage(1, None, U, dt, out=U1)
+        m.stage(2, U, U1, dt, out=U2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        m.stage(1, None, U, dt, out=U1)
+        m.stage(2, U, U1, dt, out=U2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stage_ms = e0.elapsed_time(e1) / (2 * reps)
+    alg = BYTES_PER_CELL_STAGE[4] * cells
+    achieved = alg / (stage_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": profiled_traffic(cells), "peak_kind": peak_kind,
+            "kernel": kernel_name, "algorithmic_bytes_per_launch": alg, "launch_ms": stage_ms}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=STEPS)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--f64-steps", type=int, default=20)
+    ap.add_argument("--f64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n", type=int, default=N_SIDE, help="mesh side (profiling runs only)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time the headline workload only (profiling runs)")
+    ap.add_argument("--n", type=int, default=N_SIDE,
+                    help="mesh side of the headline workload (profiling runs only)")
     ap.add_argument("--report", choices=["precision"], default=None,
                     help="print a per-field FP32-vs-FP64 error report instead of the bench line")
     args = ap.parse_args()
@@ -378,6 +458,7 @@ def main():
     import torch.distributed as dist
     import hydro_inputs as H
     import paper_2509_08971_gb300 as hh
+    from paper_2509_08971_gb300 import autotune
 
     if world > 1:
         torch.cuda.set_device(local)
@@ -393,33 +474,35 @@ def main():
     def rank_max(x):
         return max_over_ranks(x, world, dev)
 
+    stream = torch.cuda.current_stream()
+    hbm, peak_kind = peaks()
     n = args.n
     shape = (n, n, n)
     cells = n ** 3
-    U64 = H.smooth_3d(n, seed=rank, gamma=GAMMA)
-    stream = torch.cuda.current_stream()
-
-    # ---------------- FP32 fused: the headline ----------------
-    m32 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32,
-                       kernel=hh.HARD_KERNEL_FUSED)
-    U = torch.tensor(U64, dtype=torch.float32, device=dev)
-    from paper_2509_08971_gb300 import autotune
-    tuned = autotune.tune(m32, U, kernel=hh.HARD_KERNEL_FUSED, reps=5)   # outside the timed region
     t_dev = torch.zeros((), dtype=torch.float64, device=dev)
-    tot_log = torch.zeros((max(args.steps, args.warmup, 3), 5), dtype=torch.float64, device=dev)
 
     def advance(m, Ud, k, tlog):
         hh.check(hh.hard_hydro_advance(m.h, Ud.data_ptr(), k, CFL, 0.0, t_dev.data_ptr(), None,
                                        tlog.data_ptr(), stream.cuda_stream), "advance")
 
+    # ---------------- headline: 512^3 blast, FP32 fused, FP64 totals ----------------
+    Ub = H.blast_3d(n, seed=rank, gamma=GAMMA, dtype=np.float32)
+    U0 = torch.tensor(Ub, device=dev)                    # the initial state, kept for resets
+    m32 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_REFLECT, dtype=torch.float32,
+                       kernel=hh.HARD_KERNEL_FUSED)
+    U = U0.clone()
+    tuned = autotune.tune(m32, U, kernel=hh.HARD_KERNEL_FUSED, reps=5)   # outside the timed region
+    tot_log = torch.zeros((max(args.steps, args.warmup, 3), 5), dtype=torch.float64, device=dev)
     advance(m32, U, max(args.warmup, 3), tot_log)
+    U.copy_(U0)                                          # the timed steps start at t = 0
+    t_dev.zero_()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(dev.index)
     with ClockSampler(gpu_id) as clk:
         barrier()
-        with nvtx_range("whole_mesh_steps"):
+        with nvtx_range("headline_steps"):
             ev0.record(stream)
             advance(m32, U, args.steps, tot_log)
             ev1.record(stream)
@@ -428,69 +511,110 @@ def main():
     value = whole_job_value(world, cells, 2 * args.steps, ms)
     status = m32.get_error()
     clocks = clk.summary()
-    # kernels of this library launched in the timed region:
-    # signal rate and the first step's dt, then per step stage 1, stage 2 and
-    # one finalize launch (the step's totals and the next step's dt)
+    tot = tot_log[:args.steps].cpu().numpy()
+    drift = {"mass_rel": float(abs(tot[-1, 0] - tot[0, 0]) / abs(tot[0, 0])),
+             "energy_rel": float(abs(tot[-1, 4] - tot[0, 4]) / abs(tot[0, 4])),
+             "t_final": float(t_dev)}
+    # kernels of this library launched in the timed region: the signal rate
+    # and the first step's dt, then per step stage 1, stage 2 and one
+    # finalize launch (the step's totals and the next step's dt)
     launches = 2 + 3 * args.steps
+    kname = "stage_ws_kernel<32,%d,*> z-chunk %d (mean of stage 1 and stage 2)" % (
+        tuned["info"][1], tuned["info"][2])
+    roofline = stage_roofline(m32, U, hbm, peak_kind, kname)
+    issue = issue_roofline(cells, roofline["launch_ms"], clocks.get("sm_mhz"))
+    if args.headline_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "ms_per_step": ms / args.steps,
+                              "roofline": roofline, "status": hh.hard_hydro_strerror(status)}))
+        return
 
-    # ---------------- the same step, stages blocked through L2 (z slabs) ----------------
-    slab = 2 * tuned["info"][2]                       # two z-chunks of the tuned tile per slab
-    m32.set_schedule(slab)
-    advance(m32, U, max(args.warmup, 3), tot_log)
+    # ---------------- the same workload end to end through the C ABI, host buffers ----------------
+    Uh = torch.tensor(Ub).pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    m32.advance_host(Uh, 1, CFL, out=Uo)                 # warm the handle's device buffer
     barrier()
-    with nvtx_range("slab_steps"):
-        ev0.record(stream)
-        advance(m32, U, args.steps, tot_log)
-        ev1.record(stream)
-        barrier()
-    ms_slab = rank_max(ev0.elapsed_time(ev1))
-    m32.set_schedule(0)
-    slab_schedule = {"slab_planes": slab, "value": whole_job_value(world, cells, 2 * args.steps, ms_slab),
-                     "unit": UNIT, "ms_per_step": ms_slab / args.steps,
-                     "vs_whole_mesh_schedule": ms / ms_slab}
+    t0 = time.perf_counter()
+    m32.advance_host(Uh, args.steps, CFL, out=Uo)
+    barrier()
+    e2e_s = rank_max(time.perf_counter() - t0)
+    e2e = {"value": whole_job_value(world, cells, 2 * args.steps, e2e_s * 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": Uh.numel() * 4 / args.steps,
+           "d2h_bytes_per_step": Uo.numel() * 4 / args.steps,
+           "call": f"hard_hydro_advance_host: one call of {args.steps} steps of the blast from "
+                   "t = 0, pinned host buffers, both copies in the timed region"}
+    del Uh, Uo, U, U0, m32
 
-    # ---------------- stage kernel alone: roofline ----------------
-    U1 = torch.empty_like(U)
-    U2 = torch.empty_like(U)
-    dt = m32.cfl_dt(U, CFL)
-    for _ in range(3):
-        m32.stage(1, None, U, dt, out=U1)
-        m32.stage(2, U, U1, dt, out=U2)
-    reps = max(20, min(200, args.steps))
+    # ---------------- FP64 plain on the same workload ----------------
+    m64 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_REFLECT, dtype=torch.float64,
+                       kernel=hh.HARD_KERNEL_PLAIN)
+    V0 = torch.tensor(H.blast_3d(n, seed=rank, gamma=GAMMA), dtype=torch.float64, device=dev)
+    V = V0.clone()
+    k64 = max(1, args.f64_steps)
+    tl64 = torch.zeros((max(k64, 3), 5), dtype=torch.float64, device=dev)
+    advance(m64, V, 3, tl64)
+    V.copy_(V0)
+    t_dev.zero_()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    advance(m64, V, k64, tl64)
+    f1.record(stream)
+    barrier()
+    ms64 = rank_max(f0.elapsed_time(f1))
+    value64 = whole_job_value(world, cells, 2 * k64, ms64)
+    fp64 = {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+            "kernel": "stage_kernel<double,...> (plain loads)", "fp32_fused_speedup": value / value64,
+            "status": hh.hard_hydro_strerror(m64.get_error())}
+    del V, V0, m64
+
+    # ---------------- secondary: 256^3 periodic smooth flow, FP32 fused ----------------
+    n2 = SMOOTH_N
+    shape2 = (n2, n2, n2)
+    cells2 = n2 ** 3
+    U64 = H.smooth_3d(n2, seed=rank, gamma=SMOOTH_GAMMA)
+    ms2 = hh.HardHydro(shape2, SMOOTH_GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32)
+    Us = torch.tensor(U64, dtype=torch.float32, device=dev)
+    tuned2 = autotune.tune(ms2, Us, kernel=hh.HARD_KERNEL_FUSED, reps=5)
+
+    def advance2(m, Ud, k, tlog):
+        hh.check(hh.hard_hydro_advance(m.h, Ud.data_ptr(), k, SMOOTH_CFL, 0.0, t_dev.data_ptr(),
+                                       None, tlog.data_ptr(), stream.cuda_stream), "advance")
+
+    ks = max(20, args.steps)
+    tl2 = torch.zeros((ks, 5), dtype=torch.float64, device=dev)
+    advance2(ms2, Us, 3, tl2)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(reps):
-        m32.stage(1, None, U, dt, out=U1)
-        m32.stage(2, U, U1, dt, out=U2)
+    advance2(ms2, Us, ks, tl2)
     e1.record(stream)
     barrier()
-    stage_ms = e0.elapsed_time(e1) / (2 * reps)
-    hbm, peak_kind = peaks()
-    alg_bytes = BYTES_PER_CELL_STAGE[4] * cells
-    achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": profiled_traffic(), "peak_kind": peak_kind,
-                "kernel": "stage_tma_kernel<float,%d,%d> z-chunk %d (mean of stage 1 and stage 2)"
-                          % tuple(tuned["info"][:3]),
-                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": stage_ms}
-    issue = issue_roofline(cells, stage_ms, clocks.get("sm_mhz"))
-    del U1, U2
+    mss = rank_max(e0.elapsed_time(e1))
+    smooth = {"workload": SMOOTH_WORKLOAD, "value": whole_job_value(world, cells2, 2 * ks, mss),
+              "unit": UNIT, "steps": ks, "ms_per_step": mss / ks,
+              "tile": {"chosen": tuned2["info"], "ms_per_stage": tuned2["ms"]},
+              "roofline": stage_roofline(ms2, Us, hbm, peak_kind,
+                                         "stage_ws_kernel<32,%d,*> z-chunk %d" % (
+                                             tuned2["info"][1], tuned2["info"][2])),
+              "status": hh.hard_hydro_strerror(ms2.get_error())}
+    smooth["roofline"]["traffic"] = profiled_traffic(cells2)
+    alg_bytes2 = BYTES_PER_CELL_STAGE[4] * cells2
 
-    # ---------------- second scheme: WENO5-Z + HLL, FP32 ----------------
-    mw = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32,
+    # ---------------- second scheme: WENO5-Z + HLL, FP32, 256^3 smooth flow ----------------
+    mw = hh.HardHydro(shape2, SMOOTH_GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32,
                       scheme=hh.HARD_SCHEME_WENO5Z_HLL)
     Uw = torch.tensor(U64, dtype=torch.float32, device=dev)
-    kw = max(2, args.steps // 4)
-    advance(mw, Uw, 3, tot_log)
+    kw = max(2, min(args.steps, 200) // 4)
+    advance2(mw, Uw, 3, tl2)
     barrier()
     e0.record(stream)
-    advance(mw, Uw, kw, tot_log)
+    advance2(mw, Uw, kw, tl2)
     e1.record(stream)
     barrier()
     msw = rank_max(e0.elapsed_time(e1))
     W1, W2 = torch.empty_like(Uw), torch.empty_like(Uw)
-    dtw = mw.cfl_dt(Uw, CFL)
+    dtw = mw.cfl_dt(Uw, SMOOTH_CFL)
     for _ in range(2):
         mw.stage(1, None, Uw, dtw, out=W1)
         mw.stage(2, Uw, W1, dtw, out=W2)
@@ -502,21 +626,21 @@ def main():
     e1.record(stream)
     barrier()
     wstage_ms = e0.elapsed_time(e1) / 20
-    w_achieved = alg_bytes / (wstage_ms * 1e-3) / 1e9
-    weno = {"workload": WORKLOAD.replace("CFL 0.4", "CFL 0.4, WENO5-Z + HLL"),
-            "value": whole_job_value(world, cells, 2 * kw, msw), "unit": UNIT, "steps": kw,
+    w_achieved = alg_bytes2 / (wstage_ms * 1e-3) / 1e9
+    weno = {"workload": SMOOTH_WORKLOAD.replace("CFL 0.4", "CFL 0.4, WENO5-Z + HLL"),
+            "value": whole_job_value(world, cells2, 2 * kw, msw), "unit": UNIT, "steps": kw,
             "ms_per_step": msw / kw, "status": hh.hard_hydro_strerror(mw.get_error()),
             "roofline": {"bound": "hbm", "achieved": w_achieved, "peak": hbm, "unit": "GB/s",
                          "frac": w_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "weno_stage_kernel<float,32,8,3> z-chunk 32 "
                                    "(mean of stage 1 and stage 2)",
-                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": wstage_ms}}
+                         "algorithmic_bytes_per_launch": alg_bytes2, "launch_ms": wstage_ms}}
     del mw, Uw, W1, W2
 
     # ---------------- radiative heating / cooling exchange, FP32 ----------------
     pbr = H.cooling()
-    Ur, Err = pbr.state(shape, seed=rank, spread=0.5)
-    mr = hh.HardHydro(shape, pbr.gamma, hh.HARD_BC_PERIODIC, dtype=torch.float32)
+    Ur, Err = pbr.state(shape2, seed=rank, spread=0.5)
+    mr = hh.HardHydro(shape2, pbr.gamma, hh.HARD_BC_PERIODIC, dtype=torch.float32)
     Urd = torch.tensor(Ur, dtype=torch.float32, device=dev)
     Erd = torch.tensor(Err, dtype=torch.float32, device=dev)
     del Ur, Err
@@ -530,12 +654,12 @@ def main():
     e1.record(stream)
     barrier()
     rad_ms = e0.elapsed_time(e1) / 20
-    rad_bytes = 8 * 4 * cells                       # reads rho, 3 momenta, E_total, E; writes 2
+    rad_bytes = 8 * 4 * cells2                      # reads rho, 3 momenta, E_total, E; writes 2
     rad_achieved = rad_bytes / (rad_ms * 1e-3) / 1e9
     rad = {"workload": "256^3 radiative heating/cooling exchange (Sec. 3.2 cooling case, "
                        "seeded +-50% spread in rho, T_f, T_r; moving fluid), FP32, dt 1e-12 s, "
                        "state 403 MB > L2",
-           "value": whole_job_value(world, cells, 1, rank_max(rad_ms)), "unit": UNIT,
+           "value": whole_job_value(world, cells2, 1, rank_max(rad_ms)), "unit": UNIT,
            "launch_ms": rad_ms, "status": hh.hard_hydro_strerror(mr.get_error()),
            "roofline": {"bound": "hbm", "achieved": rad_achieved, "peak": hbm, "unit": "GB/s",
                         "frac": rad_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
@@ -544,40 +668,40 @@ def main():
     del mr, Urd, Erd
 
     # ---------------- radiation energy advection (WENO5-Z + Rusanov), FP32 ----------------
-    Ea = torch.tensor(1.0 + 0.5 * np.random.default_rng(200 + rank).random(shape),
+    Ea = torch.tensor(1.0 + 0.5 * np.random.default_rng(200 + rank).random(shape2),
                       dtype=torch.float32, device=dev)
-    dt_adv = m32.cfl_dt(U, CFL)
+    dt_adv = ms2.cfl_dt(Us, SMOOTH_CFL)
     for _ in range(2):
-        m32.advect_E(U, Ea, dt_adv)
+        ms2.advect_E(Us, Ea, dt_adv)
     barrier()
     e0.record(stream)
     for _ in range(5):
-        m32.advect_E(U, Ea, dt_adv)
+        ms2.advect_E(Us, Ea, dt_adv)
     e1.record(stream)
     barrier()
     adv_ms = e0.elapsed_time(e1) / 5
     # per Heun step: two stages, each reading E, rho and the three momenta and
     # writing E (24 B/cell), the second also reading E^n (4 B/cell)
-    adv_bytes = (24.0 + 28.0) * cells
+    adv_bytes = (24.0 + 28.0) * cells2
     adv_achieved = adv_bytes / (adv_ms * 1e-3) / 1e9
-    advect = {"workload": f"{n}^3 periodic radiation energy advection by the smooth-flow velocity "
-                          "field, E ~ 1 + 0.5 U[0,1) (seeded), Heun step, FP32",
-              "value": whole_job_value(world, cells, 2, rank_max(adv_ms)), "unit": UNIT,
+    advect = {"workload": f"{n2}^3 periodic radiation energy advection by the smooth-flow "
+                          "velocity field, E ~ 1 + 0.5 U[0,1) (seeded), Heun step, FP32",
+              "value": whole_job_value(world, cells2, 2, rank_max(adv_ms)), "unit": UNIT,
               "ms_per_step": adv_ms,
               "roofline": {"bound": "hbm", "achieved": adv_achieved, "peak": hbm, "unit": "GB/s",
                            "frac": adv_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
                            "kernel": "weno_advect_kernel<float,32,8,3> (mean of the two stages)",
                            "algorithmic_bytes_per_step": adv_bytes}}
-    del Ea
+    del Ea, ms2, Us
 
     # ---------------- flux-limited radiation diffusion (multigrid), FP32 ----------------
-    mf = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32)
+    mf = hh.HardHydro(shape2, SMOOTH_GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float32)
     gf = np.random.default_rng(100 + rank)
-    Uf = torch.zeros((5,) + shape, dtype=torch.float32, device=dev)
-    Uf[0] = torch.tensor(1.0 + 0.5 * gf.random(shape), dtype=torch.float32, device=dev)
-    Ef0 = torch.tensor(1.0 + 0.5 * gf.random(shape), dtype=torch.float32, device=dev)
+    Uf = torch.zeros((5,) + shape2, dtype=torch.float32, device=dev)
+    Uf[0] = torch.tensor(1.0 + 0.5 * gf.random(shape2), dtype=torch.float32, device=dev)
+    Ef0 = torch.tensor(1.0 + 0.5 * gf.random(shape2), dtype=torch.float32, device=dev)
     Ef = Ef0.clone()
-    dt_fld = 100.0 * (1.0 / n) ** 2 * 3             # diffusion number ~ 100 (c = kappa = 1)
+    dt_fld = 100.0 * (1.0 / n2) ** 2 * 3            # diffusion number ~ 100 (c = kappa = 1)
     mf.fld_step(Uf, Ef, dt_fld, 1.0, 1.0, rtol=1e-5, max_cycles=40)      # builds the levels
     Ef.copy_(Ef0)
     barrier()
@@ -590,12 +714,12 @@ def main():
     # sweeps (24 B/cell each: x read twice, b and D, x written), the fused
     # residual-restriction (13), prolongation (12): 121 B/cell, x 8/7 over
     # the levels
-    fld_bytes = 121.0 * 8.0 / 7.0 * cells * cyc_f
+    fld_bytes = 121.0 * 8.0 / 7.0 * cells2 * cyc_f
     fld_achieved = fld_bytes / (fld_ms * 1e-3) / 1e9
-    fld = {"workload": f"{n}^3 periodic implicit flux-limited diffusion step, c = kappa = 1, "
+    fld = {"workload": f"{n2}^3 periodic implicit flux-limited diffusion step, c = kappa = 1, "
                        "rho, E ~ 1 + 0.5 U[0,1) (seeded), diffusion number ~100, "
                        "V-cycles to a 1e-5 relative residual, FP32",
-           "value": whole_job_value(world, cells, cyc_f, rank_max(fld_ms)),
+           "value": whole_job_value(world, cells2, cyc_f, rank_max(fld_ms)),
            "unit": "cell-V-cycles/s", "cycles": cyc_f, "rel_residual": res_f, "ms": fld_ms,
            "roofline": {"bound": "hbm", "achieved": fld_achieved, "peak": hbm, "unit": "GB/s",
                         "frac": fld_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
@@ -603,44 +727,15 @@ def main():
                         "algorithmic_bytes_per_cycle": fld_bytes / max(cyc_f, 1)}}
     del mf, Uf, Ef, Ef0
 
-    # ---------------- FP64 plain ----------------
-    m64 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_PERIODIC, dtype=torch.float64,
-                       kernel=hh.HARD_KERNEL_PLAIN)
-    V = torch.tensor(U64, dtype=torch.float64, device=dev)
-    k64 = max(1, args.f64_steps)
-    tl64 = torch.zeros((max(k64, 3), 5), dtype=torch.float64, device=dev)
-    advance(m64, V, 3, tl64)
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    advance(m64, V, k64, tl64)
-    f1.record(stream)
-    barrier()
-    ms64 = rank_max(f0.elapsed_time(f1))
-    value64 = whole_job_value(world, cells, 2 * k64, ms64)
-    del V, m64
-
     # ---------------- batched: 4096 independent 1D/2D problems ----------------
     spec = H.batch_spec(4096, seed=rank)
     B = hh.HardBatch(spec.nx, spec.ny, spec.gamma, hh.HARD_BC_OUTFLOW)
     packed0 = B.pack([H.batch_problem_U(spec, q) for q in range(spec.nprob)])
     bcells = int(spec.cells.sum())
-    btimes = {}
-    for tile in range(hh.hard_batch_tile_count()):          # tile choice, untimed
-        B.set_tile(tile)
-        P = packed0.clone()
-        B.step(P, 1, CFL)
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        B.step(P, 5, CFL)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        btimes[tile] = b0.elapsed_time(b1)
-    btile = min(btimes, key=btimes.get)
-    B.set_tile(btile)
+    btune = B.tune(packed0, SMOOTH_CFL)                     # tile choice, untimed
     P = packed0.clone()
     tb = torch.zeros(spec.nprob, dtype=torch.float64, device=dev)
-    graph = B.capture(P, 50, CFL, tb)                       # one persistent launch, captured
+    graph = B.capture(P, 50, SMOOTH_CFL, tb)                # one persistent launch, captured
     P.copy_(packed0)
     tb.zero_()
     barrier()
@@ -653,15 +748,15 @@ def main():
     batched = {"workload": "4096 problems: half 1D n~U{64..4096}, half 2D side~U{32..256}, "
                            "two-state / four-quadrant, gamma 1.4, outflow, CFL 0.4, 50 steps",
                "value": whole_job_value(world, bcells, 2 * 50, bms), "unit": UNIT, "cells": bcells,
-               "ms": bms, "tile": btile, "tile_ms_5_steps": btimes, "graph_captured": True,
-               "status": hh.hard_hydro_strerror(B.get_error())}
+               "ms": bms, "tile": btune["tile"], "tile_ms_5_steps": btune["ms"],
+               "graph_captured": True, "status": hh.hard_hydro_strerror(B.get_error())}
     del P, packed0, B, graph
 
     # ---------------- adjoint cost: 2D shear layer 256^2, FP32 ----------------
     na = 256
     ma = hh.HardHydro((1, na, na), 1.4, hh.HARD_BC_PERIODIC, dtype=torch.float32)
     Ua = torch.tensor(H.shear_2d(na, seed=rank, gamma=1.4), dtype=torch.float32, device=dev)
-    dta = ma.cfl_dt(Ua, CFL)
+    dta = ma.cfl_dt(Ua, SMOOTH_CFL)
     Ga = torch.randn_like(Ua)
     gga = torch.zeros((), dtype=torch.float64, device=dev)
     Va, Ha = torch.empty_like(Ua), torch.empty_like(Ua)
@@ -682,8 +777,8 @@ def main():
                 fn()
             a1.record(stream)
             torch.cuda.synchronize()
-            ms = a0.elapsed_time(a1) / reps_a
-            best = ms if best is None else min(best, ms)
+            t = a0.elapsed_time(a1) / reps_a
+            best = t if best is None else min(best, t)
         return best
 
     fwd_ms = timed(lambda: ma.step(Ua, dta, out=Va))
@@ -705,8 +800,8 @@ def main():
             g.replay()
             a1.record()
             torch.cuda.synchronize()
-            ms = a0.elapsed_time(a1) / k
-            best = ms if best is None else min(best, ms)
+            t = a0.elapsed_time(a1) / k
+            best = t if best is None else min(best, t)
         del g
         return best
 
@@ -720,55 +815,48 @@ def main():
                "backward_includes": "stage-1 recompute + stage-2 and stage-1 VJP"}
     del ma, Ua, Ga, Va, Ha
 
-    # ---------------- end to end through the C ABI, host buffers ----------------
-    Uh = torch.tensor(U64, dtype=torch.float32).pin_memory()
-    Uo = torch.empty_like(Uh).pin_memory()
-    m32.advance_host(Uh, 1, CFL, out=Uo)          # warm the handle's device buffer
-    barrier()
-    t0 = time.perf_counter()
-    m32.advance_host(Uh, args.steps, CFL, out=Uo)
-    barrier()
-    e2e_s = rank_max(time.perf_counter() - t0)
-    e2e = {"value": whole_job_value(world, cells, 2 * args.steps, e2e_s * 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": Uh.numel() * 4 / args.steps,
-           "d2h_bytes_per_step": Uo.numel() * 4 / args.steps,
-           "call": f"hard_hydro_advance_host: one call of {args.steps} steps, pinned host "
-                   "buffers, copies in the timed region"}
-
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "global_cells": world * cells,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "state 336 MB > 129 MB L2 (no flush needed)", "kernel": "fused",
+                   "l2": "state 2.7 GB > 129 MB L2 (no flush needed)", "kernel": "fused",
                    "tile": {"chosen": tuned["info"], "ms_per_stage": tuned["ms"]},
-                   "step": "CFL rate + stage 1 + stage 2 + FP64 totals"},
+                   "step": "CFL rate + stage 1 + stage 2 + FP64 totals",
+                   "conservation": drift},
         "roofline": roofline, "issue_roofline": issue,
-        "slab_schedule": slab_schedule,
+        "fp64_plain": fp64,
+        "smooth_3d_256": smooth,
         "weno5z_hll": weno,
         "rad_exchange": rad,
         "radiation_advection": advect,
         "fld_multigrid": fld,
         "batched": batched,
         "adjoint": adjoint,
-        "fp64_plain": {"value": value64, "unit": UNIT, "steps": k64,
-                       "ms_per_step": ms64 / k64, "fp32_fused_speedup": value / value64},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
         "status": hh.hard_hydro_strerror(status),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         threads = cpu_threads()
-        rate, sec, used = time_oracle(shape, 2, threads)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
-                                "sample": f"2 RK2 steps of the full 256^3 workload ({sec:.1f} s)"}
-        # the same oracle on one thread, on a 256 x 256 x 8 slab of the flow
-        rate1, sec1, _ = time_oracle((8, N_SIDE, N_SIDE), 1, 1)
+        planes = 64
+        rate, sec, used = time_oracle(blast_slab(planes), 2, threads, oracle.BC_REFLECT, GAMMA, CFL)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"2 RK2 steps of the middle {planes} z planes of the 512^3 blast "
+                      f"(512x512x{planes} cells, reflecting walls, CFL 0.3; {sec:.1f} s)"}
+        rate1, sec1, _ = time_oracle(blast_slab(4), 1, 1, oracle.BC_REFLECT, GAMMA, CFL)
         line["cpu_baseline"]["single_thread"] = {
             "value": rate1, "unit": UNIT, "cores": 1,
-            "sample": f"1 RK2 step of a 256x256x8 slab of the workload ({sec1:.1f} s)"}
+            "sample": f"1 RK2 step of the middle 4 z planes of the blast ({sec1:.1f} s)"}
+        rr, rsec, rsteps = time_oracle_riemann()
+        line["cpu_baseline"]["riemann_1d_400"] = {
+            "value": rr, "unit": UNIT, "cores": 1,
+            "sample": f"configuration 1 in full: 400 cells to t = 0.15, {rsteps} steps "
+                      f"({1e3 * rsec:.1f} ms)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

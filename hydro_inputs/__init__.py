@@ -150,22 +150,38 @@ def entropy_wave(shape, direction=(1, 1, 1), amp=0.2, vel=1.0, t=0.0):
 # --------------------------------------------------------------------------
 
 def blast_3d(n, seed=0, gamma=1.4, noise=True, e_total=1.0, radius_cells=4.0, p_amb=1e-5,
-             dtype=np.float64):
+             dtype=np.float64, planes=None):
     """Ambient rho = 1 (+-1% seeded uniform noise), p = 1e-5, v = 0.  Total
     energy e_total spread equally over the cells whose centre lies within
     radius_cells * dx of the centre (0.5, 0.5, 0.5), added to the ambient
-    internal energy."""
+    internal energy.  ``planes=(k0, k1)`` returns only the z planes k0..k1-1
+    of the same n^3 state (same noise, same energy density)."""
     x = centres(n)
     dx = 1.0 / n
-    rho = np.ones((n, n, n))
+    k0, k1 = (0, n) if planes is None else (int(planes[0]), int(planes[1]))
+    nzs = k1 - k0
+    rho = np.ones((nzs, n, n))
     if noise:
-        rho += 0.01 * _rng(seed).uniform(-1.0, 1.0, size=(n, n, n))
-    r2 = ((x[:, None, None] - 0.5) ** 2 + (x[None, :, None] - 0.5) ** 2
+        # the generator's draws for the whole cube in z-plane order: planes
+        # k0..k1-1 are the draws k0*n*n .. k1*n*n - 1
+        g = _rng(seed)
+        if k0:
+            g.uniform(-1.0, 1.0, size=k0 * n * n)
+        rho += 0.01 * g.uniform(-1.0, 1.0, size=(nzs, n, n))
+    z = x[k0:k1]
+    r2 = ((z[:, None, None] - 0.5) ** 2 + (x[None, :, None] - 0.5) ** 2
           + (x[None, None, :] - 0.5) ** 2)
-    inside = r2 <= (radius_cells * dx) ** 2 * (1.0 + 1e-12)
-    zero = np.zeros((n, n, n))
-    U = prim_to_cons((rho, zero, zero, zero, np.full((n, n, n), p_amb)), gamma)
-    U[4] += np.where(inside, e_total / (inside.sum() * dx ** 3), 0.0)
+    lim = (radius_cells * dx) ** 2 * (1.0 + 1e-12)
+    inside = r2 <= lim
+    if planes is None:
+        n_in = int(inside.sum())
+    else:
+        # cells inside the sphere over the whole cube, plane by plane
+        rxy = (x[:, None] - 0.5) ** 2 + (x[None, :] - 0.5) ** 2
+        n_in = sum(int(np.count_nonzero((zz - 0.5) ** 2 + rxy <= lim)) for zz in x)
+    zero = np.zeros((nzs, n, n))
+    U = prim_to_cons((rho, zero, zero, zero, np.full((nzs, n, n), p_amb)), gamma)
+    U[4] += np.where(inside, e_total / (n_in * dx ** 3), 0.0)
     return U.astype(dtype)
 
 

@@ -267,6 +267,9 @@ class HardHydro:
         if self.dtype not in (torch.float32, torch.float64):
             raise ValueError("dtype must be torch.float32 or torch.float64")
         bc6 = [bc] * 6 if isinstance(bc, int) else list(bc)
+        self.bc6 = tuple(int(b) for b in bc6)
+        self.extent = tuple(float(e) for e in extent)
+        self.scheme = int(scheme)
         self.h = hard_hydro_create(nx, ny, nz, gamma, bc6[0])
         if not self.h:
             raise HardHydroError(HARD_EINVAL, "hard_hydro_create")
@@ -285,6 +288,7 @@ class HardHydro:
 
     def set_scheme(self, scheme):
         check(hard_hydro_set_scheme(self.h, scheme), "hard_hydro_set_scheme")
+        self.scheme = int(scheme)
 
     def set_schedule(self, slab_planes):
         check(hard_hydro_set_schedule(self.h, slab_planes), "hard_hydro_set_schedule")
@@ -413,6 +417,8 @@ class HardBatch:
         self.dtype = dtype or torch.float32
         gam = [float(gamma)] * self.nprob if isinstance(gamma, (int, float)) else list(gamma)
         bcs = [int(bc)] * self.nprob if isinstance(bc, int) else list(bc)
+        self.gammas = tuple(float(g) for g in gam)
+        self.bcs = tuple(int(b) for b in bcs)
         self.b = hard_batch_create(self.nprob, self.nx, self.ny, [1] * self.nprob, gam, bcs,
                                    HARD_F64 if self.dtype == torch.float64 else HARD_F32)
         if not self.b:
@@ -469,6 +475,11 @@ class HardBatch:
                                               s.cuda_stream), "hard_hydro_step_batched")
         torch.cuda.current_stream().wait_stream(s)
         return g
+
+    def tune(self, packed, cfl, steps=5, cache_path=None):
+        """Pick the fastest batched tile set on this batch (autotune.tune_batch)."""
+        from . import autotune
+        return autotune.tune_batch(self, packed, cfl, steps=steps, cache_path=cache_path)
 
     def get_error(self):
         return hard_batch_get_error(self.b)
