@@ -13,9 +13,10 @@ radiation operators, the batched launch and the adjoint.
 
 metric: cell-updates per RK stage per second = cells * 2 * steps / time.
 
-Prints one JSON line.  Multi-GPU (torchrun): every rank advances its own
-replica of the workload (no collective on the data path), timing is the max
-over ranks and ``value`` counts the cells of all ranks.
+Prints one JSON line.  Multi-GPU (torchrun): the blast is decomposed into z
+slabs, one per rank, with a ghost exchange per stage and a max-reduction of
+the signal rate per step over NCCL (strong scaling: the whole 512^3 mesh at
+every N); timing is the max over ranks.
 """
 from __future__ import annotations
 
@@ -431,6 +432,103 @@ def stage_roofline(m, U, hbm, peak_kind, kernel_name, reps=20):
             "kernel": kernel_name, "algorithmic_bytes_per_launch": alg, "launch_ms": stage_ms}
 
 
+def run_sharded(args, world, rank, local):
+    """N > 1: the headline workload (the whole 512^3 blast) decomposed into z
+    slabs, one per GPU (paper_2509_08971_gb300.slab): per stage a ghost
+    exchange of two planes with each neighbour over NCCL, per step one
+    all-reduce (max) of the signal rate.  Strong scaling: the job's work is
+    the whole mesh whatever N is."""
+    import torch
+    import torch.distributed as dist
+    import hydro_inputs as H
+    import paper_2509_08971_gb300 as hh
+    from paper_2509_08971_gb300 import autotune, slab
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+    n = args.n
+    shape = (n, n, n)
+    cells = n ** 3
+    L = slab.SlabLayout(n, rank, world, bc_z=(hh.HARD_BC_REFLECT, hh.HARD_BC_REFLECT))
+    m = slab.slab_handle(shape, L, GAMMA, [hh.HARD_BC_REFLECT] * 6, dtype=torch.float32)
+    backend = slab.CudaSlabBackend(m, L)
+    stepper = slab.SlabStepper(backend, slab.HaloExchange(L))
+    Ub = H.blast_3d(n, seed=0, gamma=GAMMA, dtype=np.float32, planes=(L.z0, L.z1))
+    U0 = torch.tensor(Ub, device=dev)
+    U = U0.clone()
+    U1 = torch.empty_like(U)
+    stepper.exchange(U)                                  # valid ghosts for the tile tuner
+    tuned = autotune.tune(m, U, kernel=hh.HARD_KERNEL_FUSED, reps=5)
+    stepper.advance(U, U1, max(args.warmup, 3), CFL)
+    U.copy_(U0)
+    backend.t.zero_()
+    barrier()
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(dev.index)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id) as clk:
+        barrier()
+        ev0.record(stream)
+        stepper.advance(U, U1, args.steps, CFL)
+        ev1.record(stream)
+        barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    value = cells * 2 * args.steps / (ms * 1e-3)
+    status = m.get_error()
+    clocks = clk.summary()
+    hbm, peak_kind = peaks()
+    # this rank's stage kernel on its slab (ghosts from the last exchange)
+    stepper.exchange(U)
+    roofline = stage_roofline(m, U, hbm, peak_kind,
+                              "stage_ws_kernel<32,%d,*> z-chunk %d on a %d-plane slab" % (
+                                  tuned["info"][1], tuned["info"][2], L.planes))
+    # end to end: the slab from pinned host memory, the steps, the slab back
+    Uh = torch.tensor(Ub).pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    U.copy_(Uh, non_blocking=True)
+    backend.t.zero_()
+    stepper.advance(U, U1, args.steps, CFL)
+    Uo.copy_(U, non_blocking=True)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    # per step: stage 1, stage 2, the two rate/dt kernels and two plane packs
+    # (device copies) per rank; the first step adds the rate kernel
+    launches = world * (2 + 4 * args.steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_cells": cells, "cells_per_gpu": L.planes * n * n,
+                   "parallelism": f"z-slabs x{world}: NCCL ghost exchange (2 planes x 5 fields "
+                                  "per neighbour per stage) + one all-reduce (max) of the rate "
+                                  "per step",
+                   "l2": "slab states > 129 MB L2", "tile": {"chosen": tuned["info"]}},
+        "roofline": roofline,
+        "e2e": {"value": cells * 2 * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": world * Uh.numel() * 4 / args.steps,
+                "d2h_bytes_per_step": world * Uo.numel() * 4 / args.steps,
+                "call": "each rank: its slab from pinned host memory, the decomposed steps, "
+                        "the slab back"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "status": hh.hard_hydro_strerror(status),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,6 +541,8 @@ def main():
                     help="time the headline workload only (profiling runs)")
     ap.add_argument("--n", type=int, default=N_SIDE,
                     help="mesh side of the headline workload (profiling runs only)")
+    ap.add_argument("--shard", action="store_true",
+                    help="run the z-slab decomposed path also at N = 1 (checks only)")
     ap.add_argument("--report", choices=["precision"], default=None,
                     help="print a per-field FP32-vs-FP64 error report instead of the bench line")
     args = ap.parse_args()
@@ -452,6 +552,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if world > 1 or args.shard:
+        run_sharded(args, world, rank, local)
         return
 
     import torch

@@ -46,8 +46,11 @@ typedef struct hard_hydro_s* hard_hydro_t;
 
 /* boundary kinds (per face): periodic wrap, outflow (zero gradient: the two
  * ghost layers repeat the edge cell), reflecting wall (mirror image with the
- * normal momentum negated) */
-enum { HARD_BC_PERIODIC = 0, HARD_BC_OUTFLOW = 1, HARD_BC_REFLECT = 2 };
+ * normal momentum negated); HARD_BC_HALO (z faces only): the two ghost planes
+ * are read from a caller buffer (hard_hydro_set_zghost), the planes of the
+ * neighbouring slab of a mesh decomposed along z (the ghost entities of the
+ * N-Array layout of Sec. 2.1) */
+enum { HARD_BC_PERIODIC = 0, HARD_BC_OUTFLOW = 1, HARD_BC_REFLECT = 2, HARD_BC_HALO = 3 };
 
 /* element type of U */
 enum { HARD_F32 = 0, HARD_F64 = 1 };
@@ -80,9 +83,16 @@ hard_hydro_t hard_hydro_create(int nx, int ny, int nz, double gamma, int bc);
 /* Set the element type, the domain extents (cell width = extent / cells) and
  * the boundary kind of each face, ordered x-, x+, y-, y+, z-, z+ (NULL keeps
  * the current kinds).  Periodic must be set on both faces of an axis or on
- * neither.  Frees scratch of a previous element type. */
+ * neither.  HARD_BC_HALO is accepted on the z faces of a mesh with at least
+ * two cells along every axis (HARD_EINVAL otherwise).  Frees scratch of a
+ * previous element type. */
 int hard_hydro_set(hard_hydro_t h, int dtype, double lx, double ly, double lz,
                    const int bc_per_face[6]);
+
+/* Set the cell widths directly (each > 0; the extents become width x cells).
+ * A slab of a mesh decomposed along z uses the whole mesh's widths, which
+ * extent / cells of the slab need not reproduce bit for bit. */
+int hard_hydro_set_cells(hard_hydro_t h, double dx, double dy, double dz);
 
 /* Choose the stage kernel variant and tile configuration (tile < 0 picks the
  * built-in default).  Tile ids index a table that depends on the number of
@@ -116,15 +126,69 @@ int hard_hydro_set_scheme(hard_hydro_t h, int scheme);
 /* One Runge-Kutta stage (Sec. 2.2.2 flux difference, Heun tableau):
  *   stage 1: Uout = Ucur + dt L(Ucur)                       (U0 ignored)
  *   stage 2: Uout = U0/2 + (Ucur + dt L(Ucur))/2
- * Uout must not alias Ucur; it may alias U0. */
+ * Uout must not alias Ucur; it may alias U0.  HARD_BC_HALO faces read their
+ * ghost planes from the buffers set by hard_hydro_set_zghost (HARD_EINVAL
+ * when a halo face has none; HARD_EUNSUPPORTED with the WENO5-Z scheme). */
 int hard_hydro_stage(hard_hydro_t h, int stage, const void* U0, const void* Ucur, void* Uout,
                      double dt, void* stream);
+
+/* hard_hydro_stage with the step taken from device memory and, for stage 2,
+ * the signal rate of the result (the CFL reduction of Sec. 3.1 / Sec. 3.5,
+ * max over the handle's cells of sum_d (|v_d| + c)/dx_d):
+ *   dt_dev    device double read as dt (NULL: the host value dt is used);
+ *   rate_dev  device double that receives the largest signal rate of Uout,
+ *             in double (NULL: none; stage 1 with rate_dev is HARD_EINVAL).
+ * The rate of each slab of a decomposed mesh is reduced over the slabs by
+ * the caller (a max) and turned into the common dt by hard_hydro_finalize_dt.
+ * Asynchronous. */
+int hard_hydro_stage_ex(hard_hydro_t h, int stage, const void* U0, const void* Ucur, void* Uout,
+                        double dt, const double* dt_dev, double* rate_dev, void* stream);
+
+/* ---- z-slab decomposition (ghost exchange between slabs, Sec. 2.1) ----
+ * A mesh decomposed along z gives each slab its own handle, whose z faces
+ * towards a neighbouring slab are HARD_BC_HALO and whose cell widths are the
+ * whole mesh's (hard_hydro_set_cells).  Before each stage the caller packs
+ * the two bottom and the two top planes of the stage's input (Ucur) of every
+ * slab, sends them to the neighbours and receives theirs into the ghost
+ * buffers:
+ *   ghost_lo  the two planes below z = 0 (the neighbour's top planes, lowest
+ *             first), ghost_hi the two planes above z = nz - 1 (the
+ *             neighbour's bottom planes); each [5][2][ny][nx] of the handle's
+ *             element type, 16-byte aligned device memory owned by the caller
+ *             and read by every later stage; NULL where the face is not a
+ *             halo face.
+ * hard_hydro_pack_zhalo copies planes 0, 1 of U into send_lo and planes
+ * nz-2, nz-1 into send_hi (each [5][2][ny][nx]; either may be NULL) with
+ * device copies on `stream`, so the buffers can go straight to a
+ * send/receive.  A step is then: exchange U^n, stage 1, exchange U1,
+ * stage 2 with the rate, a max of the rates over the slabs, and
+ * hard_hydro_finalize_dt.  hard_hydro_step, hard_hydro_advance(_host), the
+ * adjoint, the radiation advection and diffusion and the no-allocation step
+ * return HARD_EUNSUPPORTED on a handle with a halo face (the ghosts change
+ * between the two stages of a step). */
+int hard_hydro_set_zghost(hard_hydro_t h, const void* ghost_lo, const void* ghost_hi);
+int hard_hydro_pack_zhalo(hard_hydro_t h, const void* U, void* send_lo, void* send_hi,
+                          void* stream);
+
+/* Largest signal rate of U over the handle's cells into the device double
+ * *rate_dev (the reduction of hard_hydro_cfl_dt without the division).
+ * Asynchronous. */
+int hard_hydro_local_rate(hard_hydro_t h, const void* U, double* rate_dev, void* stream);
+
+/* dt = cfl / *rate_dev (device doubles), clipped so that t + dt <= t_end when
+ * t_end > 0, then *t_dev += dt (t_dev may be NULL when t_end == 0); the rule
+ * of hard_hydro_advance.  A zero, infinite or NaN rate gives dt = 0 and raises
+ * the device flag (read by hard_hydro_get_error).  Asynchronous. */
+int hard_hydro_finalize_dt(hard_hydro_t h, const double* rate_dev, double cfl, double t_end,
+                           double* t_dev, double* dt_dev, void* stream);
 
 /* One full step (both stages) with a fixed dt > 0.  U_out may alias U_in.
  * The intermediate stage lives in handle-owned scratch. */
 int hard_hydro_step(hard_hydro_t h, const void* U_in, void* U_out, double dt, void* stream);
 
-/* CFL time step of U: dt = cfl / max_cells sum_d (|v_d| + c)/dx_d.  Computed
+/* CFL time step of U (Sec. 3.1: the Courant number of each test, e.g. 0.3;
+ * Sec. 3.5: a CFL-limited step; the multi-axis sum rule is this library's
+ * reading): dt = cfl / max_cells sum_d (|v_d| + c)/dx_d.  Computed
  * in the element type, returned in double.  _host synchronises the stream and
  * writes *dt_host; _dev writes the double at device address dt_dev and does
  * not synchronise. */
@@ -152,10 +216,14 @@ int hard_hydro_advance_host(hard_hydro_t h, const void* U_host_in, void* U_host_
                             double cfl, double t_end, double* t_host, void* stream);
 
 /* Conserved totals sum_cells U_f dV for the 5 fields, summed in FP64 from the
- * warp level up in a fixed order (deterministic).  Synchronises the stream. */
+ * warp level up in a fixed order (deterministic).  Synchronises the stream.
+ * The paper has no counterpart: a diagnostic of the conservation that the
+ * flux form of Sec. 2.2.2 guarantees, kept in FP64 beside an FP32 state. */
 int hard_hydro_totals(hard_hydro_t h, const void* U, double out5[5], void* stream);
 
 /* ---- batched persistent launch (many independent 1D/2D problems) ----
+ * The paper has no counterpart (it runs one mesh per run): these calls serve
+ * throughput on many small problems.
  * A batch is a set of independent problems of uneven size, each a uniform
  * mesh of nx x ny cells (nz must be 1; ny = 1 makes it 1D along x; nx >= 2)
  * on the unit square, with its own gamma and one boundary kind on all faces.
@@ -190,7 +258,8 @@ void hard_batch_destroy(hard_batch_t b);
 /* hard_hydro_step with no device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they
  * step (code running during CUDA-graph stream capture, hosts whose device
- * memory is pre-reserved by another allocator or runtime).  It computes
+ * memory is pre-reserved by another allocator or runtime).  A handle with a
+ * HARD_BC_HALO face returns HARD_EUNSUPPORTED.  It computes
  * exactly what hard_hydro_step computes with the handle's element type,
  * kernel and tile, but keeps the intermediate stage in a fixed 64 MiB
  * (HARD_NOALLOC_SCRATCH_BYTES) device array that the library holds on every
@@ -200,12 +269,19 @@ void hard_batch_destroy(hard_batch_t b);
  *   - The first call on a device, with that device current, looks up the
  *     array's device address; make that first call before any stream capture.
  *   - All calls share the array: calls that overlap on the GPU (other streams
- *     or host threads) race.  Its status word is cleared per call and is not
- *     reported; use hard_hydro_step and hard_hydro_get_error for that check.
+ *     or host threads) race.  Its status word is cleared at the start of each
+ *     call; hard_hydro_noalloc_get_error reads it.
  *   - U_out may alias U_in; U pointers are device pointers, 16-byte aligned. */
 #define HARD_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
 int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U_out, double dt,
                             void* stream);
+
+/* Status word of the no-allocation step on the current device: HARD_OK,
+ * HARD_ENONPHYS or HARD_ETIMEOUT (then cleared), or HARD_ECUDA.  It reflects
+ * the calls that have finished on the device: synchronise their stream
+ * first.  A handle's own flag (hard_hydro_get_error) does not see these
+ * calls. */
+int hard_hydro_noalloc_get_error(void);
 
 /* Radiative heating / cooling (Eq. "heating-cooling"): one backward-Euler
  * step of length dt > 0 of the pointwise exchange
@@ -260,7 +336,9 @@ int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, doub
                         double kappa, double rtol, int max_cycles, int* cycles_out,
                         double* resid_out, void* stream);
 
-/* Adjoint of one full step with dt held constant (a vector-Jacobian product):
+/* The paper has no counterpart (it computes no derivatives): the adjoint
+ * serves gradient-based fitting of initial states and of gamma.
+ * Adjoint of one full step with dt held constant (a vector-Jacobian product):
  * given the cotangent gU_out of U^{n+1} = step(U_in), writes
  * gU_in = (dU^{n+1}/dU_in)^T gU_out and adds (dU^{n+1}/dgamma)^T gU_out to the
  * device double *g_gamma.  The intermediate stage is recomputed from U_in.
@@ -275,8 +353,10 @@ int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, doub
 int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_out, void* gU_in,
                              double dt, double* g_gamma, void* stream);
 
-/* Device status flag: returns HARD_OK or HARD_ENONPHYS and clears the flag.
- * Synchronises the handle's last stream. */
+/* Device status flag: returns HARD_OK, HARD_ENONPHYS (a non-physical state
+ * was met) or HARD_ETIMEOUT (a bounded wait of a TMA-fed stage ran out and
+ * that stage left its output incomplete), and clears the flag.  Synchronises
+ * the handle's last stream. */
 int hard_hydro_get_error(hard_hydro_t h);
 
 /* Static description of an error code. */

@@ -16,7 +16,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhard_hydro.so")
 
-HARD_BC_PERIODIC, HARD_BC_OUTFLOW, HARD_BC_REFLECT = 0, 1, 2
+HARD_BC_PERIODIC, HARD_BC_OUTFLOW, HARD_BC_REFLECT, HARD_BC_HALO = 0, 1, 2, 3
 HARD_F32, HARD_F64 = 0, 1
 HARD_KERNEL_FUSED, HARD_KERNEL_PLAIN = 0, 1
 HARD_SCHEME_PLM_HLLC, HARD_SCHEME_WENO5Z_HLL = 0, 1
@@ -68,6 +68,16 @@ def _declare(lib):
         "hard_hydro_step_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp,
                                                     _vp]),
         "hard_hydro_get_error": (ctypes.c_int, [_vp]),
+        "hard_hydro_noalloc_get_error": (ctypes.c_int, []),
+        "hard_hydro_set_cells": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double]),
+        "hard_hydro_stage_ex": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double,
+                                               _vp, _vp, _vp]),
+        "hard_hydro_set_zghost": (ctypes.c_int, [_vp, _vp, _vp]),
+        "hard_hydro_pack_zhalo": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "hard_hydro_local_rate": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "hard_hydro_finalize_dt": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double,
+                                                  _vp, _vp, _vp]),
         "hard_batch_create": (_vp, [ctypes.c_int, _ip, _ip, _ip, _dp, _ip, ctypes.c_int]),
         "hard_batch_offset": (ctypes.c_longlong, [_vp, ctypes.c_int]),
         "hard_batch_elements": (ctypes.c_longlong, [_vp]),
@@ -120,6 +130,36 @@ def hard_hydro_set_scheme(h, scheme):
 
 def hard_hydro_set_schedule(h, slab_planes):
     return lib().hard_hydro_set_schedule(h, int(slab_planes))
+
+
+def hard_hydro_set_cells(h, dx, dy, dz):
+    return lib().hard_hydro_set_cells(h, float(dx), float(dy), float(dz))
+
+
+def hard_hydro_stage_ex(h, stage, U0, Ucur, Uout, dt, dt_dev, rate_dev, stream):
+    return lib().hard_hydro_stage_ex(h, int(stage), U0, Ucur, Uout, float(dt), dt_dev, rate_dev,
+                                     stream)
+
+
+def hard_hydro_set_zghost(h, ghost_lo, ghost_hi):
+    return lib().hard_hydro_set_zghost(h, ghost_lo, ghost_hi)
+
+
+def hard_hydro_pack_zhalo(h, U, send_lo, send_hi, stream):
+    return lib().hard_hydro_pack_zhalo(h, U, send_lo, send_hi, stream)
+
+
+def hard_hydro_local_rate(h, U, rate_dev, stream):
+    return lib().hard_hydro_local_rate(h, U, rate_dev, stream)
+
+
+def hard_hydro_finalize_dt(h, rate_dev, cfl, t_end, t_dev, dt_dev, stream):
+    return lib().hard_hydro_finalize_dt(h, rate_dev, float(cfl), float(t_end), t_dev, dt_dev,
+                                        stream)
+
+
+def hard_hydro_noalloc_get_error():
+    return lib().hard_hydro_noalloc_get_error()
 
 
 def hard_hydro_advect_E(h, U, Er, dt, stream):

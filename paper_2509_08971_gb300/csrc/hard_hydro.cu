@@ -21,6 +21,8 @@ struct hard_hydro_s {
     double gamma;
     int bc[6];
     double ext[3];
+    double cell[3];                  // cell widths (ext / n unless set directly)
+    const void* zg[2] = {nullptr, nullptr};  // ghost planes of BC_HALO z faces (caller-owned)
     int dtype = HARD_F32;
     int kernel = HARD_KERNEL_FUSED;
     int tile = -1;
@@ -78,7 +80,7 @@ void build_mesh(hard_hydro_s* h) {
     MeshDesc& m = h->mesh;
     int a = 0;
     for (int d = 0; d < 3; ++d) {
-        m.dx[d] = h->ext[d] / h->n[d];
+        m.dx[d] = h->cell[d];
         m.act[d] = h->n[d] > 1;
     }
     m.px = 0;
@@ -164,12 +166,26 @@ int tile_of(const hard_hydro_s* h) { return h->tile < 0 ? 0 : h->tile; }
 
 bool weno(const hard_hydro_s* h) { return h->scheme == HARD_SCHEME_WENO5Z_HLL && h->mesh.dim > 0; }
 
+bool has_halo(const hard_hydro_s* h) {
+    return h->bc[4] == HARD_BC_HALO || h->bc[5] == HARD_BC_HALO;
+}
+
+// Every BC_HALO face has a 16-byte aligned ghost buffer.
+bool halo_ready(const hard_hydro_s* h) {
+    for (int s = 0; s < 2; ++s)
+        if (h->bc[4 + s] == HARD_BC_HALO && (!h->zg[s] || !aligned16(h->zg[s]))) return false;
+    return true;
+}
+
 // blocks of one stage launch (rows of the totals partial array)
 long long launch_blocks(const hard_hydro_s* h) {
     return hh::stage_blocks(h->mesh, weno(h) ? 0 : tile_of(h));
 }
 
-cudaError_t stage_launch(hard_hydro_s* h, const StageCall& c, cudaStream_t s) {
+cudaError_t stage_launch(hard_hydro_s* h, const StageCall& call, cudaStream_t s) {
+    StageCall c = call;
+    c.zg[0] = h->zg[0];
+    c.zg[1] = h->zg[1];
     if (weno(h))
         return h->dtype == HARD_F64 ? hh::launch_weno_stage_f64(h->mesh, c, s)
                                     : hh::launch_weno_stage_f32(h->mesh, c, s);
@@ -256,6 +272,21 @@ __global__ void finalize_dt_kernel(unsigned long long* slot, double cfl, double 
     finalize_dt(slot, cfl, t_end, t, dt_out, dt_log, step, status);
 }
 
+// The largest signal rate left in the slot by a rate reduction, as a double;
+// the slot is cleared for the next reduction.
+__global__ void rate_out_kernel(unsigned long long* slot, double* rate_out) {
+    *rate_out = __longlong_as_double((long long)*slot);
+    *slot = 0ull;
+}
+
+// dt from a rate given as a double (e.g. reduced over the slabs of a
+// decomposed mesh), with the rules of finalize_dt.
+__global__ void finalize_dt_from_kernel(const double* rate, double cfl, double t_end, double* t,
+                                        double* dt_out, int* status) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(*rate);
+    finalize_dt(&bits, cfl, t_end, t, dt_out, nullptr, 0, status);
+}
+
 // Fixed-order sum of the per-block partials: warp f sums field f, lane l the
 // rows l, l+32, ..., then a fixed xor tree.  Deterministic for a fixed grid.
 __device__ void finalize_totals(const double* partial, long long rows, double dV, double* out5) {
@@ -328,6 +359,7 @@ hard_hydro_t hard_hydro_create(int nx, int ny, int nz, double gamma, int bc) {
     h->gamma = gamma;
     for (int f = 0; f < 6; ++f) h->bc[f] = bc;
     h->ext[0] = h->ext[1] = h->ext[2] = 1.0;
+    for (int d = 0; d < 3; ++d) h->cell[d] = h->ext[d] / h->n[d];
     build_mesh(h);
     return h;
 }
@@ -342,13 +374,18 @@ int hard_hydro_set(hard_hydro_t h, int dtype, double lx, double ly, double lz,
     int bc[6];
     for (int f = 0; f < 6; ++f) bc[f] = bc_per_face ? bc_per_face[f] : h->bc[f];
     for (int f = 0; f < 6; ++f)
-        if (!valid_bc(bc[f])) return HARD_EINVAL;
+        if (!valid_bc(bc[f]) && !(f >= 4 && bc[f] == HARD_BC_HALO)) return HARD_EINVAL;
     for (int d = 0; d < 3; ++d)
         if ((bc[2 * d] == HARD_BC_PERIODIC) != (bc[2 * d + 1] == HARD_BC_PERIODIC))
             return HARD_EINVAL;
+    // ghost planes from a neighbouring slab: 3D meshes only (z is kernel axis 3)
+    if ((bc[4] == HARD_BC_HALO || bc[5] == HARD_BC_HALO) &&
+        (h->n[0] < 2 || h->n[1] < 2 || h->n[2] < 2))
+        return HARD_EINVAL;
     if (dtype != h->dtype) free_scratch(h);
     h->dtype = dtype;
     for (int d = 0; d < 3; ++d) h->ext[d] = e[d];
+    for (int d = 0; d < 3; ++d) h->cell[d] = e[d] / h->n[d];
     for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
     build_mesh(h);
     return HARD_OK;
@@ -366,6 +403,7 @@ int hard_hydro_set_kernel(hard_hydro_t h, int kernel, int tile) {
 int hard_hydro_set_scheme(hard_hydro_t h, int scheme) {
     if (!h) return HARD_EINVAL;
     if (scheme != HARD_SCHEME_PLM_HLLC && scheme != HARD_SCHEME_WENO5Z_HLL) return HARD_EINVAL;
+    if (scheme == HARD_SCHEME_WENO5Z_HLL && has_halo(h)) return HARD_EUNSUPPORTED;
     if (scheme == HARD_SCHEME_WENO5Z_HLL)
         for (int a = 0; a < 3; ++a)
             if (h->n[a] > 1 && h->n[a] < 3) return HARD_EINVAL;
@@ -396,21 +434,40 @@ int hard_hydro_tile_info(hard_hydro_t h, int tile, int out4[4]) {
 
 int hard_hydro_stage(hard_hydro_t h, int stage, const void* U0, const void* Ucur, void* Uout,
                      double dt, void* stream) {
+    return hard_hydro_stage_ex(h, stage, U0, Ucur, Uout, dt, nullptr, nullptr, stream);
+}
+
+int hard_hydro_stage_ex(hard_hydro_t h, int stage, const void* U0, const void* Ucur, void* Uout,
+                        double dt, const double* dt_dev, double* rate_dev, void* stream) {
     if (!h || (stage != 1 && stage != 2)) return HARD_EINVAL;
+    if (rate_dev && stage != 2) return HARD_EINVAL;
+    if (has_halo(h) && weno(h)) return HARD_EUNSUPPORTED;
+    if (!halo_ready(h)) return HARD_EINVAL;
     if (!Ucur || !Uout || (stage == 2 && !U0)) return HARD_EINVAL;
     if (!aligned16(Ucur) || !aligned16(Uout) || (stage == 2 && !aligned16(U0))) return HARD_EINVAL;
     if (Uout == Ucur) return HARD_EINVAL;
-    if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    if (!dt_dev && (!(dt > 0.0) || !std::isfinite(dt))) return HARD_EINVAL;
     int rc = ensure_slots(h);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->last = s;
-    StageCall c{stage, U0, Ucur, Uout, dt, nullptr, nullptr, nullptr, status_slot(h)};
-    return from_cuda(stage_launch(h, c, s));
+    StageCall c{stage, U0, Ucur, Uout, dt, dt_dev, nullptr, nullptr, status_slot(h)};
+    cudaError_t e = cudaSuccess;
+    if (rate_dev) {
+        c.rate_slot = rate_slot(h);
+        e = cudaMemsetAsync(rate_slot(h), 0, sizeof(unsigned long long), s);
+    }
+    if (e == cudaSuccess) e = stage_launch(h, c, s);
+    if (e == cudaSuccess && rate_dev) {
+        rate_out_kernel<<<1, 1, 0, s>>>(rate_slot(h), rate_dev);
+        e = cudaGetLastError();
+    }
+    return from_cuda(e);
 }
 
 int hard_hydro_step(hard_hydro_t h, const void* U_in, void* U_out, double dt, void* stream) {
     if (!h || !U_in || !U_out) return HARD_EINVAL;
+    if (has_halo(h)) return HARD_EUNSUPPORTED;      // ghosts change between the stages
     if (!aligned16(U_in) || !aligned16(U_out)) return HARD_EINVAL;
     if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
     int rc = ensure_U1(h);
@@ -457,6 +514,7 @@ int hard_hydro_cfl_dt_dev(hard_hydro_t h, const void* U, double cfl, double* dt_
 int hard_hydro_advance(hard_hydro_t h, void* U, int nsteps, double cfl, double t_end,
                        double* t_dev, double* dt_log_dev, double* totals_log_dev, void* stream) {
     if (!h || !U || !aligned16(U) || nsteps < 0) return HARD_EINVAL;
+    if (has_halo(h)) return HARD_EUNSUPPORTED;      // ghosts change between the stages
     if (!(cfl > 0.0) || !std::isfinite(cfl) || !(t_end >= 0.0) || !std::isfinite(t_end))
         return HARD_EINVAL;
     if (t_end > 0.0 && !t_dev) return HARD_EINVAL;
@@ -516,6 +574,7 @@ int hard_hydro_advance(hard_hydro_t h, void* U, int nsteps, double cfl, double t
 int hard_hydro_advance_host(hard_hydro_t h, const void* U_host_in, void* U_host_out, int nsteps,
                             double cfl, double t_end, double* t_host, void* stream) {
     if (!h || !U_host_in || !U_host_out || !t_host) return HARD_EINVAL;
+    if (has_halo(h)) return HARD_EUNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int rc = ensure_slots(h);
     if (rc) return rc;
@@ -575,6 +634,7 @@ int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const 
 
 int hard_hydro_advect_E(hard_hydro_t h, const void* U, void* Er, double dt, void* stream) {
     if (!h || !U || !Er || !aligned16(U) || !aligned16(Er)) return HARD_EINVAL;
+    if (has_halo(h)) return HARD_EUNSUPPORTED;
     if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (h->n[a] > 1 && h->n[a] < 3) return HARD_EINVAL;
@@ -594,6 +654,7 @@ int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, doub
                         double kappa, double rtol, int max_cycles, int* cycles_out,
                         double* resid_out, void* stream) {
     if (!h || !U || !Er || !aligned16(U) || !aligned16(Er)) return HARD_EINVAL;
+    if (has_halo(h)) return HARD_EUNSUPPORTED;
     if (!(dt > 0.0) || !std::isfinite(dt) || !(c > 0.0) || !std::isfinite(c) ||
         !(kappa > 0.0) || !std::isfinite(kappa) || max_cycles < 1 || !std::isfinite(rtol))
         return HARD_EINVAL;
@@ -618,6 +679,7 @@ int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, doub
 int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_out, void* gU_in,
                              double dt, double* g_gamma, void* stream) {
     if (!h || !U_in || !gU_out || !gU_in || !g_gamma) return HARD_EINVAL;
+    if (has_halo(h)) return HARD_EUNSUPPORTED;
     if (!aligned16(U_in) || !aligned16(gU_out) || !aligned16(gU_in)) return HARD_EINVAL;
     if (weno(h)) return HARD_EUNSUPPORTED;
     if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
@@ -662,6 +724,76 @@ int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_ou
     e = h->dtype == HARD_F64 ? hh::launch_adjoint_stage_f64(h->mesh, a1, s)
                              : hh::launch_adjoint_stage_f32(h->mesh, a1, s);
     return from_cuda(e);
+}
+
+int hard_hydro_set_cells(hard_hydro_t h, double dx, double dy, double dz) {
+    if (!h) return HARD_EINVAL;
+    const double d[3] = {dx, dy, dz};
+    for (int k = 0; k < 3; ++k)
+        if (!(d[k] > 0.0) || !std::isfinite(d[k])) return HARD_EINVAL;
+    for (int k = 0; k < 3; ++k) {
+        h->cell[k] = d[k];
+        h->ext[k] = d[k] * h->n[k];
+    }
+    build_mesh(h);
+    return HARD_OK;
+}
+
+int hard_hydro_set_zghost(hard_hydro_t h, const void* ghost_lo, const void* ghost_hi) {
+    if (!h) return HARD_EINVAL;
+    if ((ghost_lo && !aligned16(ghost_lo)) || (ghost_hi && !aligned16(ghost_hi))) return HARD_EINVAL;
+    h->zg[0] = ghost_lo;
+    h->zg[1] = ghost_hi;
+    return HARD_OK;
+}
+
+int hard_hydro_pack_zhalo(hard_hydro_t h, const void* U, void* send_lo, void* send_hi,
+                          void* stream) {
+    if (!h || !U || !aligned16(U)) return HARD_EINVAL;
+    if ((send_lo && !aligned16(send_lo)) || (send_hi && !aligned16(send_hi))) return HARD_EINVAL;
+    if (h->n[2] < 2) return HARD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t es = elem_size(h);
+    const size_t plane = (size_t)h->n[0] * h->n[1] * es;       // bytes of one z plane of a field
+    const size_t field = plane * h->n[2];
+    const unsigned char* u = static_cast<const unsigned char*>(U);
+    cudaError_t e = cudaSuccess;
+    // five rows (one per field) of two planes each, into [5][2][ny][nx]
+    if (send_lo)
+        e = cudaMemcpy2DAsync(send_lo, 2 * plane, u, field, 2 * plane, 5, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && send_hi)
+        e = cudaMemcpy2DAsync(send_hi, 2 * plane, u + (h->n[2] - 2) * plane, field, 2 * plane, 5,
+                              cudaMemcpyDeviceToDevice, s);
+    return from_cuda(e);
+}
+
+int hard_hydro_local_rate(hard_hydro_t h, const void* U, double* rate_dev, void* stream) {
+    if (!h || !U || !aligned16(U) || !rate_dev) return HARD_EINVAL;
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    cudaError_t e = cudaMemsetAsync(rate_slot(h), 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = rate_launch(h, U, s);
+    if (e == cudaSuccess) {
+        rate_out_kernel<<<1, 1, 0, s>>>(rate_slot(h), rate_dev);
+        e = cudaGetLastError();
+    }
+    return from_cuda(e);
+}
+
+int hard_hydro_finalize_dt(hard_hydro_t h, const double* rate_dev, double cfl, double t_end,
+                           double* t_dev, double* dt_dev, void* stream) {
+    if (!h || !rate_dev || !dt_dev) return HARD_EINVAL;
+    if (!(cfl > 0.0) || !std::isfinite(cfl) || !(t_end >= 0.0) || !std::isfinite(t_end))
+        return HARD_EINVAL;
+    if (t_end > 0.0 && !t_dev) return HARD_EINVAL;
+    int rc = ensure_slots(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    finalize_dt_from_kernel<<<1, 1, 0, s>>>(rate_dev, cfl, t_end, t_dev, dt_dev, status_slot(h));
+    return from_cuda(cudaGetLastError());
 }
 
 int hard_hydro_get_error(hard_hydro_t h) {

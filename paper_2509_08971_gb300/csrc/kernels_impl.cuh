@@ -3,6 +3,7 @@
 // HH_T defined (float or double) and HH_SUFFIX (f32 or f64).
 #pragma once
 #include <cstdlib>
+#include <cstring>
 
 #include "adjoint.cuh"
 #include "batched.cuh"
@@ -55,6 +56,8 @@ StageArgs<T> make_args(const MeshDesc& m, const TileDesc& td, const StageCall& c
     A.status = c.status;
     A.tmap = nullptr;
     A.starve_tma = false;
+    A.zg[0] = static_cast<const T*>(c.zg[0]);
+    A.zg[1] = static_cast<const T*>(c.zg[1]);
     return A;
 }
 
@@ -113,6 +116,44 @@ bool encode_state_map(CUtensorMap* map, const void* base, const MeshDesc& m, int
     return r == CUDA_SUCCESS;
 }
 
+// Tensor map of a ghost-plane buffer [5][2][ny][nx] (x, y, plane, field) with
+// box (bx, by, 1, 5).
+bool encode_ghost_map(CUtensorMap* map, const void* base, const MeshDesc& m, int bx, int by) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t es = sizeof(T);
+    const cuuint64_t dims[4] = {(cuuint64_t)m.n[0], (cuuint64_t)m.n[1], 2, 5};
+    const cuuint64_t strides[3] = {m.n[0] * es, (cuuint64_t)m.n[0] * m.n[1] * es,
+                                   2 * (cuuint64_t)m.n[0] * m.n[1] * es};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 5};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                          4, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Ghost-plane maps of the BC_HALO z faces (boxes of the main box and the two
+// strips); faces of other kinds keep zeroed maps that no load uses.
+template <class Maps>
+bool encode_ghost_maps(Maps& maps, const MeshDesc& m, const StageCall& c, int bx, int by) {
+    for (int s = 0; s < 2; ++s) {
+        std::memset(&maps.gmain[s], 0, sizeof(CUtensorMap));
+        std::memset(&maps.gxstrip[s], 0, sizeof(CUtensorMap));
+        std::memset(&maps.gystrip[s], 0, sizeof(CUtensorMap));
+        const bool halo = (s == 0 ? m.bc_lo[2] : m.bc_hi[2]) == BC_HALO;
+        if (!halo) continue;
+        if (!c.zg[s] || (reinterpret_cast<uintptr_t>(c.zg[s]) & 15u) != 0) return false;
+        if (!encode_ghost_map(&maps.gmain[s], c.zg[s], m, bx, by) ||
+            !encode_ghost_map(&maps.gxstrip[s], c.zg[s], m, 4, by) ||
+            !encode_ghost_map(&maps.gystrip[s], c.zg[s], m, bx, 2))
+            return false;
+    }
+    return true;
+}
+
 // The TMA kernel needs 3 active axes, rows (and so every stride) a multiple of
 // 16 bytes, at least 4 cells along x (the periodic x strip), a 16-byte
 // aligned base and element indices of all five fields below 2^32; otherwise
@@ -137,7 +178,8 @@ cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall
         if (!encode_state_map(&maps.main, c.Uc, m, TX + 8, TY + 4) ||
             !encode_state_map(&maps.xstrip, c.Uc, m, 4, TY + 4) ||
             !encode_state_map(&maps.ystrip, c.Uc, m, TX + 8, 2) ||
-            !encode_state_map(&maps.u0, c.stage == 2 ? c.U0 : c.Uc, m, TX, TY))
+            !encode_state_map(&maps.u0, c.stage == 2 ? c.U0 : c.Uc, m, TX, TY) ||
+            !encode_ghost_maps(maps, m, c, TX + 8, TY + 4))
             return cudaSuccess;
         StageArgs<T> A = make_args(m, td, c);
         // failure-path test: HARD_HYDRO_STARVE_TMA=1 makes the ring's waits
@@ -185,7 +227,8 @@ cudaError_t run_stage_ws(const MeshDesc& m, const TileDesc& td, const StageCall&
             !encode_state_map(&maps.xstrip, c.Uc, m, 4, L1::HYC) ||
             !encode_state_map(&maps.ystrip, c.Uc, m, L1::HXC, 2) ||
             !encode_state_map(&maps.u0, c.stage == 2 ? c.U0 : c.Uc, m, 32, TY) ||
-            !encode_state_map(&maps.out, c.Uo, m, 32, TY))
+            !encode_state_map(&maps.out, c.Uo, m, 32, TY) ||
+            !encode_ghost_maps(maps, m, c, L1::HXC, L1::HYC))
             return cudaSuccess;
         StageArgs<T> A = make_args(m, td, c);
         // failure-path test: HARD_HYDRO_STARVE_TMA=1 makes the ring's waits

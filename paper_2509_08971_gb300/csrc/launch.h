@@ -36,6 +36,8 @@ struct StageCall {
     int* status;
     int zlo = 0, zhi = -1;         // 3D: the kernel-z cells [zlo, zhi) to update (-1: to nz);
                                    // zlo a multiple of the tile's z-chunk
+    const void* zg[2] = {nullptr, nullptr};  // ghost planes of BC_HALO z faces (below, above),
+                                             // each [5][2][ny][nx]
 };
 
 // Tile configurations per number of active axes (the autotuner's space).

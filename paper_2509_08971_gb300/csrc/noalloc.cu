@@ -19,8 +19,10 @@
 //
 // Every call shares the one array, which keeps the last call's contents.  The
 // first stage overwrites every scratch cell before the second stage reads it,
-// so only the status word is cleared per call.  Calls whose work overlaps on
-// the GPU (different streams, or different host threads) race on the array.
+// so only the status word is cleared per call; hard_hydro_noalloc_get_error
+// reads it (after the device has finished the call).  Calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on
+// the array.
 #include <cmath>
 #include <mutex>
 
@@ -81,6 +83,9 @@ extern "C" int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U
     if (!hh::handle_view(h, &mesh, &dtype, &kernel, &tile)) return HARD_EINVAL;
     if (!U_in || !U_out || !aligned16(U_in) || !aligned16(U_out)) return HARD_EINVAL;
     if (!(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    // ghost planes of a decomposed mesh change between the stages
+    if (mesh->dim == 3 && (mesh->bc_lo[2] == HARD_BC_HALO || mesh->bc_hi[2] == HARD_BC_HALO))
+        return HARD_EUNSUPPORTED;
     const size_t need = 5 * (size_t)mesh->N * (dtype == HARD_F64 ? 8 : 4);
     if (need > SCRATCH_BYTES) return HARD_EUNSUPPORTED;       // mesh too large for the array
     DeviceScratch d;
@@ -103,4 +108,24 @@ extern "C" int hard_hydro_step_noalloc(hard_hydro_t h, const void* U_in, void* U
     const hh::StageCall c2{2, U_in, d.scratch, U_out, dt, nullptr, nullptr, nullptr, d.status};
     e = launch(c2);
     return e == cudaSuccess ? HARD_OK : HARD_ECUDA;
+}
+
+extern "C" int hard_hydro_noalloc_get_error(void) {
+    DeviceScratch d;
+    int rc = scratch_for_current_device(&d);
+    if (rc) return rc;
+    int st = 0;
+    // the status word of the last hard_hydro_step_noalloc call on this device
+    cudaError_t e = cudaMemcpy(&st, d.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HARD_ECUDA;
+    }
+    if (!st) return HARD_OK;
+    e = cudaMemset(d.status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HARD_ECUDA;
+    }
+    return (st & 4) ? HARD_ETIMEOUT : HARD_ENONPHYS;
 }

@@ -45,7 +45,15 @@ struct StageArgs {
     int* status;                      // non-physical flag
     const CUtensorMap* tmap;          // TMA descriptor of Uc (fused variant)
     bool starve_tma;                  // test switch: arm the ring's barriers, issue no copies
+    // z faces of kind BC_HALO: the two ghost planes below z = 0 (zg[0]) and
+    // above z = nz - 1 (zg[1]), each [5][2][ny][nx] (plane 0 of zg[0] is
+    // z = -2, plane 0 of zg[1] is z = nz)
+    const T* zg[2];
 };
+
+// Boundary kind of a z face whose ghost planes come from a caller buffer
+// (a neighbouring z slab of a decomposed mesh).
+constexpr int BC_HALO = 3;
 
 // Boundary map of one kernel axis: m in [-2, n+1] -> interior index, flip set
 // for a reflecting wall.  Indices beyond the ghost layers (ragged tiles only)
@@ -89,11 +97,25 @@ __device__ __forceinline__ void load_prim(const StageArgs<T>& A, int gx, int gy,
     int sx = bc_map(gx, A.n[0], A.bc_lo[0], A.bc_hi[0], fx);
     int sy = 0, sz = 0;
     if (DIM >= 2) sy = bc_map(gy, A.n[1], A.bc_lo[1], A.bc_hi[1], fy);
-    if (DIM >= 3) sz = bc_map(gz, A.n[2], A.bc_lo[2], A.bc_hi[2], fz);
+    const T* src = A.Uc;
+    long long fstride = A.N;
+    if (DIM >= 3) {
+        const bool hlo = gz < 0 && A.bc_lo[2] == BC_HALO;
+        const bool hhi = gz >= A.n[2] && A.bc_hi[2] == BC_HALO;
+        if (hlo || hhi) {
+            // ghost plane from the neighbouring slab (planes -2, -1 / nz, nz+1)
+            const int k = hlo ? gz + 2 : gz - A.n[2];
+            sz = k < 0 ? 0 : (k > 1 ? 1 : k);
+            src = A.zg[hlo ? 0 : 1];
+            fstride = 2ll * A.n[1] * A.n[0];
+        } else {
+            sz = bc_map(gz, A.n[2], A.bc_lo[2], A.bc_hi[2], fz);
+        }
+    }
     long long c = ((long long)sz * A.n[1] + sy) * A.n[0] + sx;
     T U[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) U[f] = NC ? __ldg(A.Uc + f * A.N + c) : A.Uc[f * A.N + c];
+    for (int f = 0; f < NF; ++f) U[f] = NC ? __ldg(src + f * fstride + c) : src[f * fstride + c];
     if (fx) U[1 + PX] = -U[1 + PX];
     if (DIM >= 2 && fy) U[1 + PY] = -U[1 + PY];
     if (DIM >= 3 && fz) U[3] = -U[3];

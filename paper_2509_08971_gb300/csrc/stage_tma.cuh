@@ -1,4 +1,5 @@
-// TMA-fed fused stage kernel for 3D meshes (the bench path).
+// TMA-fed fused stage kernel for FP64 3D meshes (the FP32 path is the
+// warp-specialised kernel of stage_ws.cuh).
 //
 // Same arithmetic as stage_kernel (each face flux evaluated once, in the same
 // operation order), different data movement:
@@ -24,6 +25,9 @@ struct TmaMaps {
     CUtensorMap xstrip;  // box (4, TY+4, 1, 5) of Uc
     CUtensorMap ystrip;  // box (TX+8, 2, 1, 5) of Uc
     CUtensorMap u0;      // box (TX, TY, 1, 5) of U0 (stage 2)
+    // the ghost planes of BC_HALO z faces ([0] below z = 0, [1] above z = nz-1,
+    // each [5][2][ny][nx]), with the boxes of main / xstrip / ystrip
+    CUtensorMap gmain[2], gxstrip[2], gystrip[2];
 };
 
 template <typename T, int TX, int TY, int STAGE = 1>
@@ -143,7 +147,13 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         T* s = slot_main(it);
         uint64_t* bar = bars + (it % D);
         bool fz;
-        const int jj = bc_map(jbeg + it, nz, A.bc_lo[2], A.bc_hi[2], fz);
+        const int pz = jbeg + it;
+        const bool hlo = pz < 0 && A.bc_lo[2] == BC_HALO, hhi = pz >= nz && A.bc_hi[2] == BC_HALO;
+        const int side = hlo ? 0 : 1;
+        const int jj = hlo ? pz + 2 : (hhi ? pz - nz : bc_map(pz, nz, A.bc_lo[2], A.bc_hi[2], fz));
+        const CUtensorMap* mm = hlo || hhi ? &M.gmain[side] : &M.main;
+        const CUtensorMap* mx = hlo || hhi ? &M.gxstrip[side] : &M.xstrip;
+        const CUtensorMap* my = hlo || hhi ? &M.gystrip[side] : &M.ystrip;
         // stage 2, update iterations: the U0 plane of the cell completed then
         const bool with_u0 = STAGE == 2 && it >= 4;
         mbar_arrive_expect_tx(bar, tx_bytes + (with_u0 ? L::U0_BYTES : 0u));
@@ -151,11 +161,11 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
         // wait on it runs to its limit (no copy is ever in flight)
         if (A.starve_tma) return;
         if (with_u0) tma_load_4d(u0s + (it & 1) * L::U0S, &M.u0, x0, y0, jbeg + it - 2, 0, bar);
-        tma_load_4d(s, &M.main, x0 - 4, y0 - 2, jj, 0, bar);
-        if (px_lo) tma_load_4d(s + L::XLO, &M.xstrip, nx - 4, y0 - 2, jj, 0, bar);
-        if (px_hi) tma_load_4d(s + L::XHI, &M.xstrip, 0, y0 - 2, jj, 0, bar);
-        if (py_lo) tma_load_4d(s + L::YLO, &M.ystrip, x0 - 4, ny - 2, jj, 0, bar);
-        if (py_hi) tma_load_4d(s + L::YHI, &M.ystrip, x0 - 4, 0, jj, 0, bar);
+        tma_load_4d(s, mm, x0 - 4, y0 - 2, jj, 0, bar);
+        if (px_lo) tma_load_4d(s + L::XLO, mx, nx - 4, y0 - 2, jj, 0, bar);
+        if (px_hi) tma_load_4d(s + L::XHI, mx, 0, y0 - 2, jj, 0, bar);
+        if (py_lo) tma_load_4d(s + L::YLO, my, x0 - 4, ny - 2, jj, 0, bar);
+        if (py_hi) tma_load_4d(s + L::YHI, my, x0 - 4, 0, jj, 0, bar);
     };
 
     if (tid == 0) {
@@ -365,8 +375,9 @@ stage_tma_kernel(const __grid_constant__ StageArgs<T> A, const __grid_constant__
             T U[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) U[f] = S[(f * HYC + ty + 2) * HXC + tx + 4];
-            bool fz;
-            bc_map(j, nz, A.bc_lo[2], A.bc_hi[2], fz);
+            bool fz = false;
+            if (!((j < 0 && A.bc_lo[2] == BC_HALO) || (j >= nz && A.bc_hi[2] == BC_HALO)))
+                bc_map(j, nz, A.bc_lo[2], A.bc_hi[2], fz);
             if (fz) U[3] = -U[3];
             cons_to_prim(U, gm1, qj);
 #pragma unroll

@@ -42,6 +42,9 @@ struct WsMaps {
     CUtensorMap ystrip;  // box (TX+8, 2, 1, 5) of Uc
     CUtensorMap u0;      // box (TX, TY, 1, 5) of U0 (stage 2)
     CUtensorMap out;     // box (TX, TY, 1, 5) of Uo (TMA store)
+    // the ghost planes of BC_HALO z faces ([0] below z = 0, [1] above z = nz-1,
+    // each [5][2][ny][nx]), with the boxes of main / xstrip / ystrip
+    CUtensorMap gmain[2], gxstrip[2], gystrip[2];
 };
 
 template <int TX, int TY, int NCW, int STAGE>
@@ -232,7 +235,13 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     auto issue = [&](int q) {
         uint64_t* bar = bars + (q % D);
         bool fz;
-        const int jj = bc_map(jbeg + q, nz, A.bc_lo[2], A.bc_hi[2], fz);
+        const int pz = jbeg + q;
+        const bool hlo = pz < 0 && A.bc_lo[2] == BC_HALO, hhi = pz >= nz && A.bc_hi[2] == BC_HALO;
+        const int side = hlo ? 0 : 1;
+        const int jj = hlo ? pz + 2 : (hhi ? pz - nz : bc_map(pz, nz, A.bc_lo[2], A.bc_hi[2], fz));
+        const CUtensorMap* mm = hlo || hhi ? &M.gmain[side] : &M.main;
+        const CUtensorMap* mx = hlo || hhi ? &M.gxstrip[side] : &M.xstrip;
+        const CUtensorMap* my = hlo || hhi ? &M.gystrip[side] : &M.ystrip;
         const int pu = jbeg + q - 2;
         const bool with_u0 = STAGE == 2 && pu >= z0 && pu < z1;
         mbar_arrive_expect_tx(bar, tx_bytes + (with_u0 ? L::U0_BYTES : 0u));
@@ -240,11 +249,11 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
         float* s = ring + (q % D) * L::MAIN;
         float* st = strips + (q & 1) * L::STRIP;
         if (with_u0) tma_load_4d(u0s + (q & 1) * L::U0S, &M.u0, x0, y0, pu, 0, bar);
-        tma_load_4d(s, &M.main, x0 - 4, y0 - 2, jj, 0, bar);
-        if (px_lo) tma_load_4d(st + L::XLO, &M.xstrip, nx - 4, y0 - 2, jj, 0, bar);
-        if (px_hi) tma_load_4d(st + L::XHI, &M.xstrip, 0, y0 - 2, jj, 0, bar);
-        if (py_lo) tma_load_4d(st + L::YLO, &M.ystrip, x0 - 4, ny - 2, jj, 0, bar);
-        if (py_hi) tma_load_4d(st + L::YHI, &M.ystrip, x0 - 4, 0, jj, 0, bar);
+        tma_load_4d(s, mm, x0 - 4, y0 - 2, jj, 0, bar);
+        if (px_lo) tma_load_4d(st + L::XLO, mx, nx - 4, y0 - 2, jj, 0, bar);
+        if (px_hi) tma_load_4d(st + L::XHI, mx, 0, y0 - 2, jj, 0, bar);
+        if (py_lo) tma_load_4d(st + L::YLO, my, x0 - 4, ny - 2, jj, 0, bar);
+        if (py_hi) tma_load_4d(st + L::YHI, my, x0 - 4, 0, jj, 0, bar);
     };
     // reflecting wall across z: the ghost plane's rho*w changes sign
     auto zflip = [&](int pz) { return (pz < 0 && zr_lo) || (pz >= nz && zr_hi); };
