@@ -103,17 +103,6 @@ int hard_hydro_set_kernel(hard_hydro_t h, int kernel, int tile);
 int hard_hydro_tile_count(hard_hydro_t h);
 int hard_hydro_tile_info(hard_hydro_t h, int tile, int out4[4]);
 
-/* Schedule of the two stages of hard_hydro_step and hard_hydro_advance on 3D
- * meshes (the two stages blocked in time through L2): slab_planes = 0 runs
- * each stage over the whole mesh (the default); slab_planes >= 2, a multiple
- * of the z-chunk of the chosen tile, runs the stages slab by slab along z so
- * that stage 2 of a slab follows stage 1 of the slab above it while U1 of the
- * slab is still in L2.  Results are bit-identical to the whole-mesh schedule.
- * A mesh with at most 2 slabs, a tile whose z-chunk does not divide
- * slab_planes, the WENO5-Z scheme, or a 1D/2D mesh runs the whole-mesh
- * schedule.  HARD_EINVAL for slab_planes < 0 or == 1. */
-int hard_hydro_set_schedule(hard_hydro_t h, int slab_planes);
-
 /* Choose the scheme of every later stage, step and advance call:
  * HARD_SCHEME_PLM_HLLC (default) or HARD_SCHEME_WENO5Z_HLL.  The WENO5-Z
  * scheme needs at least three cells along every active axis (else

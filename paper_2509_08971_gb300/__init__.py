@@ -44,7 +44,6 @@ def _declare(lib):
                                           ctypes.c_double, _ip]),
         "hard_hydro_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
         "hard_hydro_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int]),
-        "hard_hydro_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int]),
         "hard_hydro_rad_exchange": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double,
                                                    ctypes.POINTER(ctypes.c_double), _vp]),
         "hard_hydro_advect_E": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
@@ -126,10 +125,6 @@ def hard_hydro_set_kernel(h, kernel, tile):
 
 def hard_hydro_set_scheme(h, scheme):
     return lib().hard_hydro_set_scheme(h, int(scheme))
-
-
-def hard_hydro_set_schedule(h, slab_planes):
-    return lib().hard_hydro_set_schedule(h, int(slab_planes))
 
 
 def hard_hydro_set_cells(h, dx, dy, dz):
@@ -329,9 +324,6 @@ class HardHydro:
     def set_scheme(self, scheme):
         check(hard_hydro_set_scheme(self.h, scheme), "hard_hydro_set_scheme")
         self.scheme = int(scheme)
-
-    def set_schedule(self, slab_planes):
-        check(hard_hydro_set_schedule(self.h, slab_planes), "hard_hydro_set_schedule")
 
     def advect_E(self, U, Er, dt):
         """In place on Er: one Heun step of the radiation energy advection."""

@@ -27,7 +27,6 @@ struct hard_hydro_s {
     int kernel = HARD_KERNEL_FUSED;
     int tile = -1;
     int scheme = HARD_SCHEME_PLM_HLLC;
-    int slab = 0;                    // z-slab planes of the two-stage schedule (0: whole mesh)
     MeshDesc mesh;
     // device scratch, allocated on first use
     void* U1 = nullptr;              // intermediate stage
@@ -193,35 +192,10 @@ cudaError_t stage_launch(hard_hydro_s* h, const StageCall& call, cudaStream_t s)
     return hh::launch_stage_f32(h->mesh, h->kernel, tile_of(h), c, s);
 }
 
-// Both stages of one step.  Whole-mesh launches, or (hard_hydro_set_schedule)
-// z-slabs in the order S1(0), S1(1), then S1(b+1), S2(b) for b = 1 .. S-2,
-// then S2(S-1), S2(0): stage 2 of a slab runs right after stage 1 of the slab
-// above it, while U1 of its slab and the one below are still in L2.  Stage 1
-// of a slab reads U^n two planes into each neighbour, so the stage 2 that
-// overwrites a slab in place comes after stage 1 of both of its neighbours
-// (slab 0 last: stage 1 of the top slab reads it across a periodic wrap).
+// Both stages of one step, each over the whole mesh.
 cudaError_t two_stages(hard_hydro_s* h, StageCall c1, StageCall c2, cudaStream_t s) {
-    const int nz = h->mesh.n[2], Z = h->slab;
-    const int zc = hh::tile_desc(3, tile_of(h)).zc;
-    if (Z <= 0 || h->mesh.dim != 3 || weno(h) || nz <= 2 * Z || zc <= 0 || Z % zc != 0) {
-        cudaError_t e = stage_launch(h, c1, s);
-        return e == cudaSuccess ? stage_launch(h, c2, s) : e;
-    }
-    const int S = (nz + Z - 1) / Z;
-    auto run = [&](StageCall c, int b) {
-        c.zlo = b * Z;
-        c.zhi = std::min(nz, (b + 1) * Z);
-        return stage_launch(h, c, s);
-    };
-    cudaError_t e = run(c1, 0);
-    if (e == cudaSuccess) e = run(c1, 1);
-    for (int b = 1; b + 1 < S && e == cudaSuccess; ++b) {
-        e = run(c1, b + 1);
-        if (e == cudaSuccess) e = run(c2, b);
-    }
-    if (e == cudaSuccess) e = run(c2, S - 1);
-    if (e == cudaSuccess) e = run(c2, 0);
-    return e;
+    cudaError_t e = stage_launch(h, c1, s);
+    return e == cudaSuccess ? stage_launch(h, c2, s) : e;
 }
 
 cudaError_t rate_launch(hard_hydro_s* h, const void* U, cudaStream_t s) {
@@ -408,12 +382,6 @@ int hard_hydro_set_scheme(hard_hydro_t h, int scheme) {
         for (int a = 0; a < 3; ++a)
             if (h->n[a] > 1 && h->n[a] < 3) return HARD_EINVAL;
     h->scheme = scheme;
-    return HARD_OK;
-}
-
-int hard_hydro_set_schedule(hard_hydro_t h, int slab_planes) {
-    if (!h || slab_planes < 0 || slab_planes == 1) return HARD_EINVAL;
-    h->slab = slab_planes;
     return HARD_OK;
 }
 

@@ -9,10 +9,19 @@
 
 namespace hh {
 
-// Iteration limit of one bounded mbarrier wait.  try_wait itself suspends the
-// thread for a hardware-defined window, so this is of the order of a second of
-// wall time: only a lost transfer ever reaches it.
-constexpr int MBAR_SPIN_LIMIT = 1 << 20;
+// Limits of one bounded mbarrier wait.  A plane's bulk load lands within a
+// few microseconds; a wait gives up after MBAR_WAIT_NS of wall time (the
+// GPU's global nanosecond timer), about 10^4 times that, or after
+// MBAR_SPIN_LIMIT tries, whichever comes first.  Only a lost transfer ever
+// reaches either.
+constexpr int MBAR_SPIN_LIMIT = 1 << 22;
+constexpr unsigned long long MBAR_WAIT_NS = 50ull * 1000ull * 1000ull;   // 50 ms
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -48,10 +57,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on a phase; false when the limit ran out.
+// Bounded wait on a phase; false when a limit ran out.  The first try needs
+// no timer: most waits end there.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < MBAR_SPIN_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (int i = 0; i < MBAR_SPIN_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > MBAR_WAIT_NS) return false;
+    }
     return false;
 }
 

@@ -62,3 +62,27 @@ def test_noalloc_step_in_place_and_limits():
     assert hh.hard_hydro_step_noalloc(m.h, None, V.data_ptr(), dt, _stream()) == hh.HARD_EINVAL
     assert hh.hard_hydro_step_noalloc(m.h, V.data_ptr(), V.data_ptr(), -1.0, _stream()) == \
         hh.HARD_EINVAL
+
+
+def test_noalloc_status_word():
+    """The status word of the no-allocation step is the call's own (the
+    handle's flag does not see these calls): clean after a physical step,
+    HARD_ENONPHYS after a step met a negative density, clean again once
+    read."""
+    shape = (8, 8, 32)
+    gam = 1.4
+    U = torch.tensor(H.smooth_3d(0, seed=2, gamma=gam, shape=shape), dtype=torch.float32,
+                     device="cuda")
+    m = hh.HardHydro(shape, gam, 0)
+    dt = m.cfl_dt(U, 0.4)
+    out = torch.empty_like(U)
+    assert hh.hard_hydro_step_noalloc(m.h, U.data_ptr(), out.data_ptr(), dt, _stream()) == hh.HARD_OK
+    torch.cuda.synchronize()
+    assert hh.hard_hydro_noalloc_get_error() == hh.HARD_OK
+    V = U.clone()
+    V[0, 3, 4, 5] = -1.0
+    assert hh.hard_hydro_step_noalloc(m.h, V.data_ptr(), out.data_ptr(), dt, _stream()) == hh.HARD_OK
+    torch.cuda.synchronize()
+    assert hh.hard_hydro_noalloc_get_error() == hh.HARD_ENONPHYS
+    assert hh.hard_hydro_noalloc_get_error() == hh.HARD_OK
+    assert m.get_error() == hh.HARD_OK
