@@ -218,3 +218,25 @@ class CudaSlabBackend:
     def finalize(self, cfl, t_end):
         check(hard_hydro_finalize_dt(self.m.h, self.rate.data_ptr(), cfl, t_end, self.t.data_ptr(),
                                      self.dt.data_ptr(), self._stream()), "hard_hydro_finalize_dt")
+
+
+# ---- independent problems (the batched configuration) ----
+
+def lpt_partition(costs, world: int) -> list[list[int]]:
+    """Split independent problems over `world` ranks with no exchange between
+    them: longest processing time first (problems in decreasing cost, each to
+    the rank with the least load so far; ties to the lower problem index and
+    the lower rank), so that the most loaded rank carries at most the mean
+    load plus one problem's cost.  Returns each rank's problem indices in
+    increasing order."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    costs = [float(c) for c in costs]
+    order = sorted(range(len(costs)), key=lambda p: (-costs[p], p))
+    load = [0.0] * world
+    parts: list[list[int]] = [[] for _ in range(world)]
+    for p in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(p)
+        load[r] += costs[p]
+    return [sorted(q) for q in parts]

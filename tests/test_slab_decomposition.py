@@ -169,3 +169,19 @@ def test_the_exchange_matters():
         parts.append(g.run_fixed(U0[:, z0:z1], dts))
     alone = np.concatenate(parts, axis=1)
     assert np.max(np.abs(alone - ref)) > 1e-6 * np.max(np.abs(ref))
+
+
+def test_lpt_partition_of_independent_problems():
+    """The batched configuration shards without an exchange: every problem on
+    exactly one rank, the largest load within one problem of the mean, and
+    the split deterministic."""
+    spec = H.batch_spec(4096, seed=0)
+    cost = [int(c) for c in spec.cells]
+    for world in (1, 2, 3, 8):
+        parts = slab.lpt_partition(cost, world)
+        flat = sorted(p for q in parts for p in q)
+        assert flat == list(range(len(cost)))
+        loads = [sum(cost[p] for p in q) for q in parts]
+        assert max(loads) <= sum(loads) / world + max(cost)
+        assert parts == slab.lpt_partition(cost, world)
+    assert slab.lpt_partition([5, 1, 4, 2, 3], 2) == [[0, 1, 3], [2, 4]]
