@@ -20,6 +20,7 @@
 #include <cmath>
 #include <new>
 
+#include "devattr.h"
 #include "fld_launch.h"
 #include "hard_hydro.h"
 
@@ -27,7 +28,6 @@ namespace hh {
 
 constexpr int FLD_MAX_LEVELS = 16;
 constexpr int FLD_PRE = 2, FLD_POST = 2, FLD_COARSE = 50;
-constexpr int FLD_COARSE_SMEM = 1024;       // coarsest levels up to this size: one block, in smem
 
 struct FldLevel {
     int n[3];
@@ -231,39 +231,58 @@ __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T>
 }
 
 // Convergence check of the fine level: sum r^2 and sum b^2 (r = b - A x) into
-// norms[0..1], without storing r.  Blocks take rows (j, k) in a grid-stride
-// loop, one pair of atomics per block.  FP32: sums over runs of 32 cells in
-// FP32, each run added in FP64 (the FP64 pipe of this GPU is a small
-// fraction of its FP32 rate; a run of 32 positive FP32 terms is exact to
-// ~2e-6 relative, far inside what a convergence test of the residual needs).
-// FP64: every term added in FP64.
+// norms[0..1], without storing r.  A work item is SMOOTH_ROWS consecutive
+// rows of one 128-cell x segment of a plane; each thread takes its x cell in
+// those rows with every load issued before the arithmetic (one cell at a time
+// left each thread waiting on load latency), and blocks take items in a
+// grid-stride loop, one pair of atomics per block.  Each thread sums its
+// rows' terms in the element type and adds them to FP64 per item (at most
+// SMOOTH_ROWS FP32 terms: exact to ~1e-7 relative, far inside what a
+// convergence test of the residual needs); FP64 sums every term in FP64.
 template <typename T>
 __global__ void __launch_bounds__(128) residual_norms_kernel(const LvlArgs<T> a, double* norms) {
     __shared__ double sr[4], sb[4];
     double rr = 0.0, bb = 0.0;
-    T pr = T(0), pb = T(0);
-    int run = 0;
-    const int rows = a.n[1] * a.n[2];
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int j = row % a.n[1], k = row / a.n[1];
-        for (int i = threadIdx.x; i < a.n[0]; i += blockDim.x) {
-            const int q = (k * a.n[1] + j) * a.n[0] + i;
+    const int segs = (a.n[0] + 127) / 128;
+    const int groups = (a.n[1] + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
+    const long long items = (long long)segs * groups * a.n[2];
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int seg = (int)(it % segs);
+        const long long t = it / segs;
+        const int grp = (int)(t % groups), k = (int)(t / groups);
+        const int i = seg * 128 + threadIdx.x;
+        StencilVals<T> v[SMOOTH_ROWS];
+        T bq[SMOOTH_ROWS], xq[SMOOTH_ROWS];
+        bool on[SMOOTH_ROWS];
+#pragma unroll
+        for (int r = 0; r < SMOOTH_ROWS; ++r) {
+            const int j = grp * SMOOTH_ROWS + r;
+            on[r] = j < a.n[1] && i < a.n[0];
+            const int ii = on[r] ? i : 0, jj = on[r] ? j : 0;
+            const int q = (k * a.n[1] + jj) * a.n[0] + ii;
+            stencil_load(a, ii, jj, k, q, v[r]);
+            bq[r] = a.b[q];
+            xq[r] = a.x[q];
+        }
+        T pr = T(0), pb = T(0);
+#pragma unroll
+        for (int r = 0; r < SMOOTH_ROWS; ++r) {
             T diag, off;
-            stencil(a, i, j, k, q, diag, off);
-            const T bq = a.b[q];
-            const T r = bq - (diag * a.x[q] - off);
-            pr = fma(r, r, pr);
-            pb = fma(bq, bq, pb);
-            if (sizeof(T) == 8 || ++run == 32) {
-                rr += (double)pr;
-                bb += (double)pb;
-                pr = pb = T(0);
-                run = 0;
+            stencil_eval(a, v[r], diag, off);
+            const T res = bq[r] - (diag * xq[r] - off);
+            if (on[r]) {
+                if (sizeof(T) == 8) {
+                    rr += (double)res * (double)res;
+                    bb += (double)bq[r] * (double)bq[r];
+                } else {
+                    pr = fma(res, res, pr);
+                    pb = fma(bq[r], bq[r], pb);
+                }
             }
         }
+        rr += (double)pr;
+        bb += (double)pb;
     }
-    rr += (double)pr;
-    bb += (double)pb;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         rr += __shfl_xor_sync(0xffffffffu, rr, o);
@@ -286,49 +305,134 @@ __global__ void __launch_bounds__(128) residual_norms_kernel(const LvlArgs<T> a,
     }
 }
 
-// The coarsest level: `sweeps` red-black Gauss-Seidel sweeps by one block
-// (the level has at most a few thousand cells), so one launch instead of
-// 2 x sweeps.
+// The small levels of the V-cycle (each at most FLD_SMALL_CELLS cells, at
+// most FLD_SMALL_MAX of them: the bottom of the hierarchy) in one block, in
+// shared memory: the same smoothing, residual restriction, coarsest-level
+// sweeps and prolongation as the level kernels, with block barriers between
+// them instead of launches.  In: level 0 of the set's x and b (global: its
+// x is the current iterate or the zeroed correction, its b the restricted
+// residual or the right-hand side) and every level's D.  Out: level 0's x.
+constexpr int FLD_SMALL_CELLS = 4096;
+constexpr int FLD_SMALL_MAX = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(1024) coarse_solve_kernel(const LvlArgs<T> a, int sweeps) {
-    // the level fits in shared memory (at most FLD_COARSE_SMEM cells)
-    __shared__ T sx[FLD_COARSE_SMEM], sb[FLD_COARSE_SMEM], sD[FLD_COARSE_SMEM];
-    // changed[it & 1]: sweep it altered some x.  A sweep that alters nothing
-    // has reached a fixed point: every later sweep would return the same
-    // values, so the loop stops there with the result of all `sweeps`.  The
-    // slot of sweep it+1 is cleared after the first barrier of sweep it,
-    // when every thread has read sweep it-1's flag and none writes it yet.
-    __shared__ int changed[2];
-    const int N = (int)a.N;
-    if (threadIdx.x == 0) changed[0] = 0;
+struct SmallLevels {
+    int count;                       // levels of the set, finest first
+    LvlArgs<T> lv[FLD_SMALL_MAX];    // global arrays (x, b of the first; D of all), extents, weights
+    int h[FLD_SMALL_MAX][3];         // coarsening factors of level i into level i+1
+    int off[FLD_SMALL_MAX];          // element offset of level i's x, b, D in shared memory
+    int pre, post, coarse;           // sweeps
+};
+
+// One red-black half-sweep of a level held in shared memory.
+template <typename T>
+__device__ __forceinline__ void small_half_sweep(const LvlArgs<T>& s, int color) {
+    const int N = (int)s.N;
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
-        sx[q] = a.x[q];
-        sb[q] = a.b[q];
-        sD[q] = a.D[q];
+        const int i = q % s.n[0], t = q / s.n[0];
+        const int j = t % s.n[1], k = t / s.n[1];
+        if (((i + j + k) & 1) != color) continue;
+        T diag, off;
+        stencil(s, i, j, k, q, diag, off);
+        s.x[q] = (s.b[q] + off) / diag;
     }
     __syncthreads();
-    LvlArgs<T> s = a;
-    s.x = sx;
-    s.b = sb;
-    s.D = sD;
-    for (int it = 0; it < sweeps; ++it) {
-        for (int color = 0; color < 2; ++color) {
-            if (color == 1 && threadIdx.x == 0) changed[(it + 1) & 1] = 0;
-            for (int q = threadIdx.x; q < N; q += blockDim.x) {
-                const int i = q % a.n[0], t = q / a.n[0];
-                const int j = t % a.n[1], k = t / a.n[1];
-                if (((i + j + k) & 1) != color) continue;
-                T diag, off;
-                stencil(s, i, j, k, q, diag, off);
-                const T nx = (sb[q] + off) / diag;
-                if (!(nx == sx[q])) changed[it & 1] = 1;    // also NaN: keep sweeping
-                sx[q] = nx;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) small_vcycle_kernel(const SmallLevels<T> S) {
+    extern __shared__ __align__(16) unsigned char fld_smem[];
+    T* sm = reinterpret_cast<T*>(fld_smem);
+    LvlArgs<T> L[FLD_SMALL_MAX];
+    for (int l = 0; l < S.count; ++l) {
+        L[l] = S.lv[l];
+        T* base = sm + S.off[l];
+        const int N = (int)L[l].N;
+        L[l].x = base;
+        L[l].b = base + N;
+        L[l].D = base + 2 * N;
+        T* bb = base + N;
+        T* DD = base + 2 * N;
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+            DD[q] = S.lv[l].D[q];
+            if (l == 0) {
+                base[q] = S.lv[0].x[q];
+                bb[q] = S.lv[0].b[q];
             }
-            __syncthreads();
         }
-        if (!changed[it & 1]) break;              // the same value in every thread
     }
-    for (int q = threadIdx.x; q < N; q += blockDim.x) a.x[q] = sx[q];
+    __syncthreads();
+    // down: smooth, then the children's mean residual as the next b, x = 0
+    for (int l = 0; l + 1 < S.count; ++l) {
+        for (int it = 0; it < S.pre; ++it) {
+            small_half_sweep(L[l], 0);
+            small_half_sweep(L[l], 1);
+        }
+        const LvlArgs<T>& F = L[l];
+        const LvlArgs<T>& C = L[l + 1];
+        const int h0 = S.h[l][0], h1 = S.h[l][1], h2 = S.h[l][2];
+        T* cb = const_cast<T*>(C.b);
+        for (int Q = threadIdx.x; Q < (int)C.N; Q += blockDim.x) {
+            const int I = Q % C.n[0], t = Q / C.n[0];
+            const int J = t % C.n[1], K = t / C.n[1];
+            T sum = T(0);
+            for (int cz = 0; cz < h2; ++cz)
+                for (int cy = 0; cy < h1; ++cy)
+                    for (int cx = 0; cx < h0; ++cx) {
+                        const int i = I * h0 + cx, j = J * h1 + cy, k = K * h2 + cz;
+                        const int q = (k * F.n[1] + j) * F.n[0] + i;
+                        T diag, off;
+                        stencil(F, i, j, k, q, diag, off);
+                        sum += F.b[q] - (diag * F.x[q] - off);
+                    }
+            cb[Q] = sum / T(h0 * h1 * h2);
+            C.x[Q] = T(0);
+        }
+        __syncthreads();
+    }
+    // the coarsest level: red-black sweeps until a sweep changes nothing
+    // (every later sweep would return the same values) or `coarse` sweeps
+    {
+        __shared__ int changed[2];
+        const LvlArgs<T>& s = L[S.count - 1];
+        const int N = (int)s.N;
+        if (threadIdx.x == 0) changed[0] = 0;
+        __syncthreads();
+        for (int it = 0; it < S.coarse; ++it) {
+            for (int color = 0; color < 2; ++color) {
+                if (color == 1 && threadIdx.x == 0) changed[(it + 1) & 1] = 0;
+                for (int q = threadIdx.x; q < N; q += blockDim.x) {
+                    const int i = q % s.n[0], t = q / s.n[0];
+                    const int j = t % s.n[1], k = t / s.n[1];
+                    if (((i + j + k) & 1) != color) continue;
+                    T diag, off;
+                    stencil(s, i, j, k, q, diag, off);
+                    const T nx = (s.b[q] + off) / diag;
+                    if (!(nx == s.x[q])) changed[it & 1] = 1;    // also NaN: keep sweeping
+                    s.x[q] = nx;
+                }
+                __syncthreads();
+            }
+            if (!changed[it & 1]) break;          // the same value in every thread
+        }
+    }
+    // up: add the coarse correction to the children, smooth
+    for (int l = S.count - 2; l >= 0; --l) {
+        const LvlArgs<T>& F = L[l];
+        const LvlArgs<T>& C = L[l + 1];
+        const int h0 = S.h[l][0], h1 = S.h[l][1], h2 = S.h[l][2];
+        for (int q = threadIdx.x; q < (int)F.N; q += blockDim.x) {
+            const int i = q % F.n[0], t = q / F.n[0];
+            const int j = t % F.n[1], k = t / F.n[1];
+            F.x[q] += C.x[((k / h2) * C.n[1] + j / h1) * C.n[0] + i / h0];
+        }
+        __syncthreads();
+        for (int it = 0; it < S.post; ++it) {
+            small_half_sweep(F, 0);
+            small_half_sweep(F, 1);
+        }
+    }
+    for (int q = threadIdx.x; q < (int)L[0].N; q += blockDim.x) S.lv[0].x[q] = L[0].x[q];
 }
 
 // coarse[I] = mean of the children fine[...] (restriction of r, and of D)
@@ -478,11 +582,35 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
     for (int l = 0; l + 1 < H->nl; ++l) restrict_to<T>(H, l, H->L[l].D, H->L[l + 1].D, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
+    // the small levels at the bottom run in one block per cycle
+    int ls = H->nl;
+    while (ls > 0 && H->L[ls - 1].N <= FLD_SMALL_CELLS && H->nl - (ls - 1) <= FLD_SMALL_MAX) --ls;
+    SmallLevels<T> S;
+    size_t small_bytes = 0;
+    if (ls < H->nl) {
+        S.count = H->nl - ls;
+        S.pre = FLD_PRE;
+        S.post = FLD_POST;
+        S.coarse = FLD_COARSE;
+        int off = 0;
+        for (int i = 0; i < S.count; ++i) {
+            const FldLevel& F = H->L[ls + i];
+            S.lv[i] = level_args<T>(H, ls + i, dt);
+            for (int a = 0; a < 3; ++a) S.h[i][a] = F.coarsened[a] ? 2 : 1;
+            S.off[i] = off;
+            off += 3 * (int)F.N;
+        }
+        small_bytes = sizeof(T) * (size_t)off;
+        static std::atomic<unsigned long long> attr{0};
+        if ((e = smem_attr_once(small_vcycle_kernel<T>, small_bytes, attr)) != cudaSuccess) return e;
+    }
+
     int done = 0;
     double rel = -1.0;
     for (int cyc = 0; cyc < max_cycles; ++cyc) {
-        // down: smooth, residual, restrict
-        for (int l = 0; l + 1 < H->nl; ++l) {
+        // down: smooth, residual, restrict (the large levels)
+        for (int l = 0; l < ls; ++l) {
+            if (l + 1 >= H->nl) break;
             if ((e = smooth<T>(H, l, dt, FLD_PRE, s)) != cudaSuccess) return e;
             const FldLevel& F = H->L[l];
             const FldLevel& C = H->L[l + 1];
@@ -492,17 +620,15 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
                 level_args<T>(H, l, dt), static_cast<T*>(C.b), static_cast<T*>(C.x), C.n[0],
                 C.n[1], F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
         }
-        {
-            const LvlArgs<T> a = level_args<T>(H, H->nl - 1, dt);
-            if (a.N <= FLD_COARSE_SMEM) {
-                coarse_solve_kernel<T><<<1, 1024, 0, s>>>(a, FLD_COARSE);
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            } else if ((e = smooth<T>(H, H->nl - 1, dt, FLD_COARSE, s)) != cudaSuccess) {
-                return e;
-            }
+        if (ls < H->nl) {
+            small_vcycle_kernel<T><<<1, 1024, small_bytes, s>>>(S);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        } else if ((e = smooth<T>(H, H->nl - 1, dt, FLD_COARSE, s)) != cudaSuccess) {
+            return e;                                // a coarsest level too large for one block
         }
-        // up: prolong the correction, smooth
-        for (int l = H->nl - 2; l >= 0; --l) {
+        // up: prolong the correction, smooth (the large levels)
+        for (int l = ls - 1; l >= 0; --l) {
+            if (l + 1 >= H->nl) continue;
             const FldLevel& F = H->L[l];
             const FldLevel& C = H->L[l + 1];
             dim3 gp = rows_grid(F, 1);
@@ -515,8 +641,9 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
         done = cyc + 1;
         if (rtol > 0.0) {
             if ((e = cudaMemsetAsync(H->norms, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
-            const int rows = L0.n[1] * L0.n[2];
-            residual_norms_kernel<T><<<rows < 152 * 16 ? rows : 152 * 16, 128, 0, s>>>(
+            const long long items = (long long)((L0.n[0] + 127) / 128) *
+                                    ((L0.n[1] + SMOOTH_ROWS - 1) / SMOOTH_ROWS) * L0.n[2];
+            residual_norms_kernel<T><<<(int)(items < 152 * 16 ? items : 152 * 16), 128, 0, s>>>(
                 level_args<T>(H, 0, dt), H->norms);
             double nr[2];
             if ((e = cudaMemcpyAsync(nr, H->norms, sizeof(nr), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
