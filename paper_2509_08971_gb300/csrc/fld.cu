@@ -601,8 +601,13 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             off += 3 * (int)F.N;
         }
         small_bytes = sizeof(T) * (size_t)off;
+        // the limit is raised once per device to the largest set there can
+        // be: levels of at most FLD_SMALL_CELLS cells, each at most half the
+        // one above, three arrays each
         static std::atomic<unsigned long long> attr{0};
-        if ((e = smem_attr_once(small_vcycle_kernel<T>, small_bytes, attr)) != cudaSuccess) return e;
+        if ((e = smem_attr_once(small_vcycle_kernel<T>, sizeof(T) * 3 * 2 * FLD_SMALL_CELLS,
+                                attr)) != cudaSuccess)
+            return e;
     }
 
     int done = 0;
