@@ -25,6 +25,18 @@
 
 namespace hh {
 
+// Programmatic dependent launch: the adjoint's kernels are launched while the
+// kernel before them in the stream still runs (cudaLaunchKernelEx with
+// programmatic stream serialization), so that launch latency overlaps the
+// tail of the previous kernel.  Each waits here, before its first read of
+// memory the previous kernel writes, for that kernel to complete (a hardware
+// wait of the grid dependency, not a spin), and lets its own dependent start
+// once it has issued all its work.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // The primitive cotangent accumulator holds one 8-slot record per cell (5
 // used), so that FP32 contributions land with one 16-byte vector reduction
 // plus one scalar reduction.
@@ -310,6 +322,7 @@ __device__ __forceinline__ void face_vjp_one(const AdjArgs<T>& A, const int c3[3
 constexpr int FACES_VJP_THREADS = 128;
 template <typename T, int DIM, int PX, int PY>
 __global__ void __launch_bounds__(FACES_VJP_THREADS, 7) faces_vjp_kernel(const AdjArgs<T> A) {
+    griddep_wait();
     // 32-bit index arithmetic (the launcher keeps DIM * total below 2^31)
     const unsigned e0 = A.n[0] + 1, e1 = DIM >= 2 ? A.n[1] + 1 : 1, e2 = DIM >= 3 ? A.n[2] + 1 : 1;
     const unsigned total = e0 * e1 * e2;
@@ -330,6 +343,7 @@ __global__ void __launch_bounds__(FACES_VJP_THREADS, 7) faces_vjp_kernel(const A
             if (DIM >= 3 && in0 && in1) face_vjp_one<T, 2, 2>(A, c3, gacc);
         }
     }
+    griddep_launch_dependents();
     // block sum of the explicit d/dgamma, one atomic per block
     __shared__ double red[8];
 #pragma unroll
@@ -353,6 +367,7 @@ __global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, T* gW, const
                                                        T* out_c, bool accumulate, T* out0,
                                                        long long N, T gamma, double* g_gamma,
                                                        bool clear_gW) {
+    griddep_wait();
     double gacc = 0.0;
     const T g1 = gamma - T(1);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
@@ -388,6 +403,7 @@ __global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, T* gW, const
             if (out0) out0[f * N + c] = a * Gc[f];
         }
     }
+    griddep_launch_dependents();
     __shared__ double red[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(0xffffffffu, gacc, o);
