@@ -21,22 +21,14 @@
 // E = p/(gamma-1) + rho|v|^2/2.
 #pragma once
 #include "hydro_math.cuh"
+#include "pdl.h"
 #include "stage_kernel.cuh"
 
 namespace hh {
 
-// Programmatic dependent launch: the adjoint's kernels are launched while the
-// kernel before them in the stream still runs (cudaLaunchKernelEx with
-// programmatic stream serialization), so that launch latency overlaps the
-// tail of the previous kernel.  Each waits here, before its first read of
-// memory the previous kernel writes, for that kernel to complete (a hardware
-// wait of the grid dependency, not a spin), and lets its own dependent start
-// once it has issued all its work.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
+// The face and cell passes are launched as programmatic dependents (pdl.h):
+// each waits for the pass before it on the device and triggers the next one
+// when its loop is done.
 // The primitive cotangent accumulator holds one 8-slot record per cell (5
 // used), so that FP32 contributions land with one 16-byte vector reduction
 // plus one scalar reduction.

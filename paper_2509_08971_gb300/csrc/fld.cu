@@ -22,6 +22,7 @@
 
 #include "devattr.h"
 #include "fld_launch.h"
+#include "pdl.h"
 #include "hard_hydro.h"
 
 namespace hh {
@@ -147,6 +148,7 @@ constexpr int SMOOTH_ROWS = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int color) {
+    griddep_wait();
     const int k = blockIdx.z;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     StencilVals<T> v[SMOOTH_ROWS];
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int col
 #pragma unroll
     for (int r = 0; r < SMOOTH_ROWS; ++r)
         if (on[r]) a.x[qs[r]] = bq[r];
+    griddep_launch_dependents();
 }
 
 // Residual of level l restricted to level l+1 in one pass: one thread per
@@ -188,6 +191,7 @@ template <typename T, bool H2>
 __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T> a, T* bc, T* xc,
                                                                 int nc0, int nc1, int h0, int h1,
                                                                 int h2) {
+    griddep_wait();
     const int J = blockIdx.y, K = blockIdx.z;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc0) return;
@@ -228,6 +232,7 @@ __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T>
     const int Q = (K * nc1 + J) * nc0 + I;
     bc[Q] = sum / T(h0 * h1 * h2);
     xc[Q] = T(0);
+    griddep_launch_dependents();
 }
 
 // Convergence check of the fine level: sum r^2 and sum b^2 (r = b - A x) into
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T>
 // convergence test of the residual needs); FP64 sums every term in FP64.
 template <typename T>
 __global__ void __launch_bounds__(128) residual_norms_kernel(const LvlArgs<T> a, double* norms) {
+    griddep_wait();
     __shared__ double sr[4], sb[4];
     double rr = 0.0, bb = 0.0;
     const int segs = (a.n[0] + 127) / 128;
@@ -303,6 +309,7 @@ __global__ void __launch_bounds__(128) residual_norms_kernel(const LvlArgs<T> a,
         atomicAdd(norms, tr);
         atomicAdd(norms + 1, tb);
     }
+    griddep_launch_dependents();
 }
 
 // The small levels of the V-cycle (each at most FLD_SMALL_CELLS cells, at
@@ -341,6 +348,7 @@ __device__ __forceinline__ void small_half_sweep(const LvlArgs<T>& s, int color)
 
 template <typename T>
 __global__ void __launch_bounds__(1024) small_vcycle_kernel(const SmallLevels<T> S) {
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char fld_smem[];
     T* sm = reinterpret_cast<T*>(fld_smem);
     LvlArgs<T> L[FLD_SMALL_MAX];
@@ -433,6 +441,7 @@ __global__ void __launch_bounds__(1024) small_vcycle_kernel(const SmallLevels<T>
         }
     }
     for (int q = threadIdx.x; q < (int)L[0].N; q += blockDim.x) S.lv[0].x[q] = L[0].x[q];
+    griddep_launch_dependents();
 }
 
 // coarse[I] = mean of the children fine[...] (restriction of r, and of D)
@@ -462,6 +471,7 @@ __global__ void __launch_bounds__(256) restrict_kernel(const T* fine, T* coarse,
 template <typename T>
 __global__ void __launch_bounds__(128) prolong_kernel(T* fine, const T* coarse, int nf0, int nf1,
                                                       int nc0, int nc1, int h0, int h1, int h2) {
+    griddep_wait();
     const int k = blockIdx.z;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf0) return;
@@ -482,6 +492,7 @@ __global__ void __launch_bounds__(128) prolong_kernel(T* fine, const T* coarse, 
 #pragma unroll
     for (int r = 0; r < SMOOTH_ROWS; ++r)
         if (on[r]) fine[qs[r]] = f[r] + c[r];
+    griddep_launch_dependents();
 }
 
 // D = c lambda(R) / (kappa rho), R = |grad E| / (rho kappa E), on level 0
@@ -552,8 +563,11 @@ cudaError_t smooth(const FldHierarchy* H, int l, double dt, int sweeps, cudaStre
     dim3 g = rows_grid(H->L[l], 2);
     g.y = (g.y + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
     for (int it = 0; it < sweeps; ++it)
-        for (int color = 0; color < 2; ++color) smooth_kernel<T><<<g, 128, 0, s>>>(a, color);
-    return cudaGetLastError();
+        for (int color = 0; color < 2; ++color) {
+            const cudaError_t e = launch_pdl(smooth_kernel<T>, g, dim3(128), 0, s, a, color);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -621,13 +635,15 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             const FldLevel& C = H->L[l + 1];
             const bool h2 = F.coarsened[0] && F.coarsened[1] && F.coarsened[2];
             auto rr = h2 ? residual_restrict_kernel<T, true> : residual_restrict_kernel<T, false>;
-            rr<<<rows_grid(C, 1), 128, 0, s>>>(
-                level_args<T>(H, l, dt), static_cast<T*>(C.b), static_cast<T*>(C.x), C.n[0],
-                C.n[1], F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
+            e = launch_pdl(rr, rows_grid(C, 1), dim3(128), 0, s, level_args<T>(H, l, dt),
+                           static_cast<T*>(C.b), static_cast<T*>(C.x), C.n[0], C.n[1],
+                           F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1,
+                           F.coarsened[2] ? 2 : 1);
+            if (e != cudaSuccess) return e;
         }
         if (ls < H->nl) {
-            small_vcycle_kernel<T><<<1, 1024, small_bytes, s>>>(S);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            e = launch_pdl(small_vcycle_kernel<T>, dim3(1), dim3(1024), small_bytes, s, S);
+            if (e != cudaSuccess) return e;
         } else if ((e = smooth<T>(H, H->nl - 1, dt, FLD_COARSE, s)) != cudaSuccess) {
             return e;                                // a coarsest level too large for one block
         }
@@ -638,9 +654,11 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             const FldLevel& C = H->L[l + 1];
             dim3 gp = rows_grid(F, 1);
             gp.y = (gp.y + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
-            prolong_kernel<T><<<gp, 128, 0, s>>>(
-                static_cast<T*>(F.x), static_cast<const T*>(C.x), F.n[0], F.n[1], C.n[0], C.n[1],
-                F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
+            e = launch_pdl(prolong_kernel<T>, gp, dim3(128), 0, s, static_cast<T*>(F.x),
+                           static_cast<const T*>(C.x), F.n[0], F.n[1], C.n[0], C.n[1],
+                           F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1,
+                           F.coarsened[2] ? 2 : 1);
+            if (e != cudaSuccess) return e;
             if ((e = smooth<T>(H, l, dt, FLD_POST, s)) != cudaSuccess) return e;
         }
         done = cyc + 1;
@@ -648,8 +666,10 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             if ((e = cudaMemsetAsync(H->norms, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
             const long long items = (long long)((L0.n[0] + 127) / 128) *
                                     ((L0.n[1] + SMOOTH_ROWS - 1) / SMOOTH_ROWS) * L0.n[2];
-            residual_norms_kernel<T><<<(int)(items < 152 * 16 ? items : 152 * 16), 128, 0, s>>>(
-                level_args<T>(H, 0, dt), H->norms);
+            e = launch_pdl(residual_norms_kernel<T>,
+                           dim3((unsigned)(items < 152 * 16 ? items : 152 * 16)), dim3(128), 0, s,
+                           level_args<T>(H, 0, dt), H->norms);
+            if (e != cudaSuccess) return e;
             double nr[2];
             if ((e = cudaMemcpyAsync(nr, H->norms, sizeof(nr), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
                 return e;

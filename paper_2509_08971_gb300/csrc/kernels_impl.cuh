@@ -417,25 +417,6 @@ cudaError_t run_batched(const BatchCall& c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Launch with programmatic stream serialization: the kernel may begin while
-// the previous kernel in the stream finishes; it waits for it on the device
-// (griddep_wait) before touching its results.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
-                       Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
 AdjArgs<T> make_adj(const MeshDesc& m, const AdjointCall& c) {
     AdjArgs<T> A;
     A.Uc = static_cast<const T*>(c.Uc);
@@ -463,7 +444,7 @@ cudaError_t run_faces_vjp(const AdjArgs<T>& A, int dim, cudaStream_t s) {
     long long blocks = (total + FACES_VJP_THREADS - 1) / FACES_VJP_THREADS;
     if (blocks > 152 * 32) blocks = 152 * 32;
     return launch_pdl(faces_vjp_kernel<T, DIM, PX, PY>, dim3((unsigned)blocks),
-                      dim3(FACES_VJP_THREADS), s, A);
+                      dim3(FACES_VJP_THREADS), 0, s, A);
 }
 
 }  // namespace
@@ -539,7 +520,7 @@ cudaError_t HH_CAT(launch_adjoint_stage_, HH_SUFFIX)(const MeshDesc& m, const Ad
     if (e != cudaSuccess) return e;
     long long blocks = (m.N + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    return launch_pdl(cell_vjp_kernel<T>, dim3((unsigned)blocks), dim3(256), s,
+    return launch_pdl(cell_vjp_kernel<T>, dim3((unsigned)blocks), dim3(256), 0, s,
                       static_cast<const T*>(c.Uc), static_cast<T*>(c.gW),
                       static_cast<const T*>(c.G), (T)c.b, (T)c.a, static_cast<T*>(c.out_c),
                       c.accumulate, static_cast<T*>(c.out0), m.N, (T)m.gamma, c.g_gamma,
