@@ -7,14 +7,14 @@
 //
 //   * face warps, one per tile row: lane = x.  In the iteration of plane p a
 //     face warp evaluates the x face left of its cell (the left state of the
-//     face comes from the neighbouring lane by a shuffle, the right flux
-//     likewise) and the y face below it, then converts its own cell of plane
-//     p+1, then closes cell p-1: the z face p-1/2 from the column's register
-//     stencil and the RK combine.
+//     face comes from the neighbouring lane by a shuffle) and the y face
+//     below it, then converts its own cell of plane p+1, then closes cell
+//     p-1: the z face p-1/2 from the column's register stencil and the RK
+//     combine with the x and y fluxes of plane p-1 read from shared memory.
 //   * converter warps: they issue the TMA loads, convert the halo ring of
 //     plane p+1 and evaluate the tile's edge faces of plane p (the y faces
-//     above the top row, the x faces right of the last column), whose fluxes
-//     the face warps read one plane later.
+//     above the top row, the x faces left of the first and right of the last
+//     column), whose fluxes the face warps read one plane later.
 //
 // The finished plane of the tile is staged in shared memory and written by
 // one TMA tile store.  Primitive planes, y-face fluxes, edge fluxes and the
@@ -50,10 +50,11 @@ struct WsMaps {
 template <int TX, int TY, int NCW, int STAGE>
 struct WsLayout {
     static_assert(TX == 32, "one face warp per tile row, lane = x");
+    static_assert(2 * TY <= 32, "one converter lane per x edge face");
     static constexpr int NFW = TY;                      // face warps
     static constexpr int NW = TY + NCW;
     static constexpr int NT = 32 * NW;
-    static constexpr int D = 4;                         // conserved ring slots
+    static constexpr int D = 4;                         // conserved ring slots (a power of 2)
     static constexpr int HXC = TX + 8, HYC = TY + 4;    // conserved box
     static constexpr int HXP = TX + 4, HYP = TY + 4;    // primitive plane
     static constexpr int NPC = HXP * HYP;               // cells of a primitive plane
@@ -68,15 +69,16 @@ struct WsLayout {
     static constexpr int PQ = pad32(5 * NPC);           // float4 part, then p
     static constexpr int FYR = TY + 1;                  // y-face rows
     static constexpr int FQ = pad32(5 * FYR * TX);      // float4 part, then the energy flux
-    static constexpr int FXE = pad32(NF * TY);          // right-edge x fluxes [TY][5]
+    static constexpr int FXR = TX + 1;                  // x faces per tile row
+    static constexpr int FX = pad32(5 * TY * FXR);      // x-face fluxes: float4 part, then energy
     static constexpr int OST = pad32(NF * TY * TX);     // output plane staged for the TMA store
     // offsets in floats from the end of the barrier block
     static constexpr int O_STRIP = D * MAIN;
     static constexpr int O_U0 = O_STRIP + 2 * STRIP;
     static constexpr int O_P = O_U0 + NU0 * U0S;
     static constexpr int O_FY = O_P + 2 * PQ;
-    static constexpr int O_FXE = O_FY + 2 * FQ;
-    static constexpr int O_OST = O_FXE + 2 * FXE;
+    static constexpr int O_FX = O_FY + 2 * FQ;
+    static constexpr int O_OST = O_FX + 2 * FX;
     static constexpr int O_MAP = O_OST + 2 * OST;       // halo conversion map (ints)
     static constexpr int O_END = O_MAP + pad32(4 * TX + 4 * TY);
     static constexpr size_t BAR_BYTES = 128;            // D mbarriers, abort flags
@@ -189,6 +191,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     constexpr int D = L::D, HXC = L::HXC, HYC = L::HYC, HXP = L::HXP, NPC = L::NPC;
     constexpr int FYR = L::FYR, NCT = 32 * NCW;
     constexpr bool EPI = STAGE == 2;
+    static_assert(D == 4, "the wait parity below divides by 4");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the base stays a pointer into the shared array (not an integer round
     // trip), so every access below compiles to a shared-memory instruction
@@ -203,7 +206,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     float* u0s = sm + L::O_U0;
     float* Pbase = sm + L::O_P;
     float* Fybase = sm + L::O_FY;
-    float* Fxebase = sm + L::O_FXE;
+    float* Fxbase = sm + L::O_FX;
     float* Ost = sm + L::O_OST;
     int* hmap = reinterpret_cast<int*>(sm + L::O_MAP);
     double (*red_tot)[NF] = reinterpret_cast<double (*)[NF]>(sm + L::O_END);
@@ -233,7 +236,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     // stage 2 also the U^n plane jbeg + q - 2 that the RK combine of
     // iteration q - 1 needs (it completes on the same barrier).
     auto issue = [&](int q) {
-        uint64_t* bar = bars + (q % D);
+        uint64_t* bar = bars + (q & (D - 1));
         bool fz;
         const int pz = jbeg + q;
         const bool hlo = pz < 0 && A.bc_lo[2] == BC_HALO, hhi = pz >= nz && A.bc_hi[2] == BC_HALO;
@@ -246,7 +249,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
         const bool with_u0 = STAGE == 2 && pu >= z0 && pu < z1;
         mbar_arrive_expect_tx(bar, tx_bytes + (with_u0 ? L::U0_BYTES : 0u));
         if (A.starve_tma) return;          // test switch: the waits run out, no copy in flight
-        float* s = ring + (q % D) * L::MAIN;
+        float* s = ring + (q & (D - 1)) * L::MAIN;
         float* st = strips + (q & 1) * L::STRIP;
         if (with_u0) tma_load_4d(u0s + (q & 1) * L::U0S, &M.u0, x0, y0, pu, 0, bar);
         tma_load_4d(s, mm, x0 - 4, y0 - 2, jj, 0, bar);
@@ -299,7 +302,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     // conserved -> primitive of the own cell of the plane of iteration index q
     auto convert_own = [&](int q, float W[NF]) {
         float U[NF];
-        const float* slot = ring + (q % D) * L::MAIN;
+        const float* slot = ring + (q & (D - 1)) * L::MAIN;
         if (!edge) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) U[f] = slot[rown + f * (HYC * HXC)];
@@ -313,9 +316,9 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     };
 
     // z-column register stencil of the face warps
-    float qn[NF], dn[NF], qLz[NF], Fzb[NF], Xc[NF];
+    float qn[NF], dn[NF], qLz[NF], Fzb[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) qn[f] = dn[f] = qLz[f] = Fzb[f] = Xc[f] = 0.f;
+    for (int f = 0; f < NF; ++f) qn[f] = dn[f] = qLz[f] = Fzb[f] = 0.f;
     bool bad = false;
     float rate_max = 0.f;
     float tot[NF] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -327,10 +330,9 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
         const bool XY = p >= z0 && p < z1;               // faces of plane p wanted
         const bool FIN = p - 1 >= z0 && p - 1 < z1;      // cell p-1 completes
         const int cb = it & 1, pb = cb ^ 1;              // buffers of plane p and of plane p+-1
-        const uint32_t wpar = (uint32_t)(((it + 1) / D) & 1);
-        uint64_t* wbar = bars + ((it + 1) % D);
+        const uint32_t wpar = (uint32_t)((it + 1) >> 2) & 1u;      // D = 4
+        uint64_t* wbar = bars + ((it + 1) & (D - 1));
         if (facew) {
-            float Xn[NF];                                // x part of the divergence of plane p
             if (XY) {
                 const float4* P4 = reinterpret_cast<const float4*>(Pbase + cb * L::PQ);
                 const float* Pp = Pbase + cb * L::PQ + 4 * NPC;
@@ -338,7 +340,10 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
                 ws_get(P4, Pp, pown, q);
                 ws_get(P4, Pp, pown - 1, qm);
                 ws_get(P4, Pp, pown + 1, qp);
-                // x: slope of the own cell; its right state goes to the next lane
+                // x: slope of the own cell; its right state goes to the next
+                // lane, which evaluates the face between them.  Lane 0's left
+                // face is the tile's edge face (a converter warp's), so its
+                // result is not stored.
                 float qRx[NF], qLl[NF];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -346,21 +351,12 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
                     qRx[f] = fmaf(-0.5f, s, q[f]);
                     qLl[f] = __shfl_up_sync(0xffffffffu, fmaf(0.5f, s, q[f]), 1);
                 }
-                if (lane == 0) {
-                    // right state of the halo cell left of the tile
-                    float qmm[NF];
-                    ws_get(P4, Pp, pown - 2, qmm);
-#pragma unroll
-                    for (int f = 0; f < NF; ++f)
-                        qLl[f] = fmaf(0.5f, vminmod(qm[f] - qmm[f], q[f] - qm[f]), qm[f]);
-                }
                 float Fl[NF];
                 hllc_axis<0>(qLl, qRx, gamma, gm1, igm1, Fl);
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const float Fr = __shfl_down_sync(0xffffffffu, Fl[f], 1);
-                    // lane 31: the right flux is the tile's edge face, read next plane
-                    Xn[f] = lane == 31 ? Fl[f] : (Fl[f] - Fr) * idx;
+                if (lane != 0) {
+                    float* Fx = Fxbase + cb * L::FX;
+                    ws_put(reinterpret_cast<float4*>(Fx), Fx + 4 * TY * L::FXR,
+                           warp * L::FXR + lane, Fl);
                 }
                 // y: the face below the cell, from the four rows around it
                 float r0[NF], r1[NF], r3[NF], Fb[NF];
@@ -406,19 +402,20 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
                                warp * TX + lane, yb);
                         ws_get(reinterpret_cast<const float4*>(Fq), Fq + 4 * FYR * TX,
                                (warp + 1) * TX + lane, yt);
-                        if (lane == 31) {
-                            const float* Fe = Fxebase + pb * L::FXE + warp * NF;
-#pragma unroll
-                            for (int f = 0; f < NF; ++f) Xc[f] = (Xc[f] - Fe[f]) * idx;
-                        }
-                        const float* Sk = ring + ((it - 1) % D) * L::MAIN + rown;
+                        const float* Fx = Fxbase + pb * L::FX;
+                        float xl[NF], xr[NF];
+                        ws_get(reinterpret_cast<const float4*>(Fx), Fx + 4 * TY * L::FXR,
+                               warp * L::FXR + lane, xl);
+                        ws_get(reinterpret_cast<const float4*>(Fx), Fx + 4 * TY * L::FXR,
+                               warp * L::FXR + lane + 1, xr);
+                        const float* Sk = ring + ((it - 1) & (D - 1)) * L::MAIN + rown;
                         const float* U0k = u0s + pb * L::U0S + warp * TX + lane;
                         float* Ok = Ost + cb * L::OST + warp * TX + lane;
                         float Uo[NF];
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
-                            const float Lf =
-                                fmaf(Fzb[f] - Fz[f], idz, fmaf(yb[f] - yt[f], idy, Xc[f]));
+                            const float Lf = fmaf(Fzb[f] - Fz[f], idz,
+                                                  fmaf(yb[f] - yt[f], idy, (xl[f] - xr[f]) * idx));
                             const float uc = Sk[f * (HYC * HXC)];
                             if constexpr (STAGE == 1) {
                                 Uo[f] = fmaf(dt, Lf, uc);
@@ -450,7 +447,6 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
             for (int f = 0; f < NF; ++f) {
                 dn[f] = d1[f];
                 qn[f] = q1[f];
-                if (XY) Xc[f] = Xn[f];
             }
         } else {
             // ---- converter warps ----
@@ -481,17 +477,20 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
                     float* Fq = Fybase + cb * L::FQ;
                     ws_put(reinterpret_cast<float4*>(Fq), Fq + 4 * FYR * TX, TY * TX + lane, F);
                 }
-                if (cw == NCW - 1 && lane < TY) {
-                    // x faces right of the last column (one per row)
-                    const int c = (lane + 2) * HXP + TX + 2;   // plane column TX
+                if (cw == NCW - 1 && lane < 2 * TY) {
+                    // the x faces at the tile's left and right edges (one per
+                    // row and side): lanes 0 .. TY-1 left, TY .. 2TY-1 right
+                    const int row = lane < TY ? lane : lane - TY;
+                    const int col = lane < TY ? 0 : TX;
+                    const int c = (row + 2) * HXP + col + 2;
                     ws_get(P4, Pp, c - 2, q0);
                     ws_get(P4, Pp, c - 1, q1);
                     ws_get(P4, Pp, c, q2);
                     ws_get(P4, Pp, c + 1, q3);
                     face_flux4<0>(q0, q1, q2, q3, gamma, gm1, igm1, F);
-                    float* Fe = Fxebase + cb * L::FXE + lane * NF;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) Fe[f] = F[f];
+                    float* Fx = Fxbase + cb * L::FX;
+                    ws_put(reinterpret_cast<float4*>(Fx), Fx + 4 * TY * L::FXR, row * L::FXR + col,
+                           F);
                 }
             }
             if (!mbar_wait(wbar, wpar)) {
@@ -500,7 +499,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
             } else if (p + 1 >= z0 && p + 1 < z1) {
                 // halo ring of plane p+1
                 const int q = it + 1;
-                const float* slot = ring + (q % D) * L::MAIN;
+                const float* slot = ring + (q & (D - 1)) * L::MAIN;
                 const float* strip = strips + pb * L::STRIP;
                 float* Pq = Pbase + pb * L::PQ;
                 const bool fz = zflip(p + 1);
