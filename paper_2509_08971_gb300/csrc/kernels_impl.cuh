@@ -202,20 +202,25 @@ cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall
 
 #ifdef HH_WS
 // Warp-specialised FP32 kernel (stage_ws.cuh): tiles 32 x TY with NCW
-// converter warps; blocks per SM by tile height.
+// converter warps and RPW tile rows per face warp; blocks per SM by tile
+// height.
 #ifndef HH_WS_NCW8
 #define HH_WS_NCW8 2
 #endif
+#ifndef HH_WS_RPW8
+#define HH_WS_RPW8 1
+#endif
 template <int TY> struct WsConf {
     static constexpr int NCW = TY >= 8 ? HH_WS_NCW8 : 1;
+    static constexpr int RPW = TY == 8 ? HH_WS_RPW8 : 1;
 };
 
 template <int TY>
 cudaError_t run_stage_ws(const MeshDesc& m, const TileDesc& td, const StageCall& c,
                          cudaStream_t s, bool& used) {
-    constexpr int NCW = WsConf<TY>::NCW;
-    using L1 = WsLayout<32, TY, NCW, 1>;
-    using L2 = WsLayout<32, TY, NCW, 2>;
+    constexpr int NCW = WsConf<TY>::NCW, RPW = WsConf<TY>::RPW;
+    using L1 = WsLayout<32, TY, NCW, 1, RPW>;
+    using L2 = WsLayout<32, TY, NCW, 2, RPW>;
     used = false;
     if constexpr (L2::bytes > SMEM_LIMIT) {
         return cudaSuccess;
@@ -240,13 +245,13 @@ cudaError_t run_stage_ws(const MeshDesc& m, const TileDesc& td, const StageCall&
         static std::atomic<unsigned long long> attr1{0}, attr2{0};
         cudaError_t e;
         if (c.stage == 1) {
-            e = smem_attr_once(stage_ws_kernel<32, TY, NCW, 1>, L1::bytes, attr1);
+            e = smem_attr_once(stage_ws_kernel<32, TY, NCW, 1, RPW>, L1::bytes, attr1);
             if (e != cudaSuccess) return e;
-            stage_ws_kernel<32, TY, NCW, 1><<<grid, L1::NT, L1::bytes, s>>>(A, maps);
+            stage_ws_kernel<32, TY, NCW, 1, RPW><<<grid, L1::NT, L1::bytes, s>>>(A, maps);
         } else {
-            e = smem_attr_once(stage_ws_kernel<32, TY, NCW, 2>, L2::bytes, attr2);
+            e = smem_attr_once(stage_ws_kernel<32, TY, NCW, 2, RPW>, L2::bytes, attr2);
             if (e != cudaSuccess) return e;
-            stage_ws_kernel<32, TY, NCW, 2><<<grid, L2::NT, L2::bytes, s>>>(A, maps);
+            stage_ws_kernel<32, TY, NCW, 2, RPW><<<grid, L2::NT, L2::bytes, s>>>(A, maps);
         }
         used = true;
         return cudaGetLastError();

@@ -47,12 +47,13 @@ struct WsMaps {
     CUtensorMap gmain[2], gxstrip[2], gystrip[2];
 };
 
-template <int TX, int TY, int NCW, int STAGE>
+template <int TX, int TY, int NCW, int STAGE, int RPW>
 struct WsLayout {
-    static_assert(TX == 32, "one face warp per tile row, lane = x");
+    static_assert(TX == 32, "lane = x in the face warps");
     static_assert(2 * TY <= 32, "one converter lane per x edge face");
-    static constexpr int NFW = TY;                      // face warps
-    static constexpr int NW = TY + NCW;
+    static_assert(TY % RPW == 0, "whole tile rows per face warp");
+    static constexpr int NFW = TY / RPW;                // face warps, RPW tile rows each
+    static constexpr int NW = NFW + NCW;
     static constexpr int NT = 32 * NW;
     static constexpr int D = 4;                         // conserved ring slots (a power of 2)
     static constexpr int HXC = TX + 8, HYC = TY + 4;    // conserved box
@@ -178,18 +179,36 @@ __device__ __forceinline__ void ws_get(const float4* P4, const float* Pp, int i,
 }
 
 
+// Signal rate of a conserved state on a 3D mesh: cons_to_prim followed by
+// cell_rate with every axis active, the density's reciprocal taken once (the
+// same operations, so the same value).
+__device__ __forceinline__ float ws_rate(const float U[NF], float gamma, float gm1,
+                                         const float rdx[3]) {
+    const float ir = vrcp(U[0]);
+    const float u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+    const float kin = 0.5f * fmaf(U[1], u, fmaf(U[2], v, U[3] * w));
+    const float p = gm1 * (U[4] - kin);
+    const float cs = vsqrt(gamma * p * ir);
+    float r = fmaf(fabsf(u) + cs, rdx[0], 0.0f);
+    r = fmaf(fabsf(v) + cs, rdx[1], r);
+    return fmaf(fabsf(w) + cs, rdx[2], r);
+}
+
 // Iteration schedule of a block's z chunk [z0, z1): the iteration of plane
 // p = z0 - 2 + it converts plane p+1, evaluates the x/y faces of plane p when
 // z0 <= p < z1, and closes cell p-1 when z0 <= p-1 < z1.  The z stencil takes
 // its first slope in iteration 1 and its first face in iteration 2.  One copy
 // of the iteration body: copies specialised per iteration kind (measured)
-// ran slower, from instruction-cache misses.
-template <int TX, int TY, int NCW, int STAGE>
-__global__ void __launch_bounds__(32 * (TY + NCW), TY >= 16 ? 1 : (TY >= 8 ? 2 : 3))
+// ran slower, from instruction-cache misses.  A face warp owns RPW
+// consecutive tile rows: with two, the y slope of a row is shared by the two
+// y faces around it and the iteration's control work is spread over two
+// cells per thread.
+template <int TX, int TY, int NCW, int STAGE, int RPW>
+__global__ void __launch_bounds__(32 * (TY / RPW + NCW), TY >= 16 ? 1 : (TY >= 8 ? 2 : 3))
 stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constant__ WsMaps M) {
-    using L = WsLayout<TX, TY, NCW, STAGE>;
+    using L = WsLayout<TX, TY, NCW, STAGE, RPW>;
     constexpr int D = L::D, HXC = L::HXC, HYC = L::HYC, HXP = L::HXP, NPC = L::NPC;
-    constexpr int FYR = L::FYR, NCT = 32 * NCW;
+    constexpr int FYR = L::FYR, NCT = 32 * NCW, NFW = L::NFW;
     constexpr bool EPI = STAGE == 2;
     static_assert(D == 4, "the wait parity below divides by 4");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -214,7 +233,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
         reinterpret_cast<unsigned long long*>(reinterpret_cast<double*>(red_tot) + L::NFW * NF);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool facew = warp < TY;                       // warp-uniform
+    const bool facew = warp < NFW;                      // warp-uniform
     const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = A.zlo + blockIdx.z * A.zchunk;
@@ -230,7 +249,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     const uint32_t tx_bytes = L::MAIN_BYTES + (px_lo ? L::XS_BYTES : 0) +
                               (px_hi ? L::XS_BYTES : 0) + (py_lo ? L::YS_BYTES : 0) +
                               (py_hi ? L::YS_BYTES : 0);
-    const int issuer = 32 * TY;                         // lane 0 of the first converter warp
+    const int issuer = 32 * NFW;                        // lane 0 of the first converter warp
 
     // Ring plane of iteration index q (plane jbeg + q) with its strips; in
     // stage 2 also the U^n plane jbeg + q - 2 that the RK combine of
@@ -261,16 +280,21 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     // reflecting wall across z: the ghost plane's rho*w changes sign
     auto zflip = [&](int pz) { return (pz < 0 && zr_lo) || (pz >= nz && zr_hi); };
 
-    // conversion maps of edge tiles: the face warps' own cell in a register,
+    // conversion maps of edge tiles: the face warps' own cells in registers,
     // the halo ring in shared memory (written by the converter lanes, read
     // after the barrier); interior tiles read the main box at fixed offsets
-    int cv_own = 0;
+    const int yr0 = warp * RPW;                         // first tile row of a face warp
+    int cv_own[RPW];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) cv_own[r] = 0;
     if (edge) {
         if (facew) {
-            cv_own = ws_source<TX, TY, HXC, HYC, L::XLO, L::XHI, L::YLO, L::YHI>(
-                lane, warp, x0, y0, nx, ny, A.bc_lo, A.bc_hi);
+#pragma unroll
+            for (int r = 0; r < RPW; ++r)
+                cv_own[r] = ws_source<TX, TY, HXC, HYC, L::XLO, L::XHI, L::YLO, L::YHI>(
+                    lane, yr0 + r, x0, y0, nx, ny, A.bc_lo, A.bc_hi);
         } else {
-            for (int e = tid - 32 * TY; e < L::NHALO; e += NCT) {
+            for (int e = tid - 32 * NFW; e < L::NHALO; e += NCT) {
                 int cx, cy;
                 halo_cell<TX, TY>(e, cx, cy);
                 hmap[e] = ws_source<TX, TY, HXC, HYC, L::XLO, L::XHI, L::YLO, L::YHI>(
@@ -295,30 +319,39 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     const float gamma = A.gamma, gm1 = A.gm1, igm1 = A.igm1;
     const float idx = A.dxk[0], idy = A.dxk[1], idz = A.dxk[2];
     const float dt = (float)(A.dt_dev ? *A.dt_dev : A.dt);
-    const bool own = facew && x0 + lane < nx && y0 + warp < ny;
-    const int pown = (warp + 2) * HXP + lane + 2;       // own cell in a primitive plane
-    const int rown = (warp + 2) * HXC + lane + 4;       // own cell in a ring slot
-
-    // conserved -> primitive of the own cell of the plane of iteration index q
-    auto convert_own = [&](int q, float W[NF]) {
-        float U[NF];
-        const float* slot = ring + (q & (D - 1)) * L::MAIN;
-        if (!edge) {
+    // the face warps' cells: tile row yr0 + r, column lane
+    bool own[RPW];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) U[f] = slot[rown + f * (HYC * HXC)];
-        } else {
-            ws_gather(cv_own, slot, strips + (q & 1) * L::STRIP, U);
-        }
-        if (zflip(jbeg + q)) U[3] = -U[3];
-        cons_to_prim(U, gm1, W);
+    for (int r = 0; r < RPW; ++r) own[r] = facew && x0 + lane < nx && y0 + yr0 + r < ny;
+    const int pown0 = (yr0 + 2) * HXP + lane + 2;       // row yr0 in a primitive plane
+    const int rown0 = (yr0 + 2) * HXC + lane + 4;       // row yr0 in a ring slot
+
+    // conserved -> primitive of the own cells of the plane of iteration index q
+    auto convert_own = [&](int q, float (&W)[RPW][NF]) {
+        const float* slot = ring + (q & (D - 1)) * L::MAIN;
+        const bool fz = zflip(jbeg + q);
         float* Pq = Pbase + (q & 1) * L::PQ;
-        ws_put(reinterpret_cast<float4*>(Pq), Pq + 4 * NPC, pown, W);
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+            float U[NF];
+            if (!edge) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) U[f] = slot[rown0 + r * HXC + f * (HYC * HXC)];
+            } else {
+                ws_gather(cv_own[r], slot, strips + (q & 1) * L::STRIP, U);
+            }
+            if (fz) U[3] = -U[3];
+            cons_to_prim(U, gm1, W[r]);
+            ws_put(reinterpret_cast<float4*>(Pq), Pq + 4 * NPC, pown0 + r * HXP, W[r]);
+        }
     };
 
-    // z-column register stencil of the face warps
-    float qn[NF], dn[NF], qLz[NF], Fzb[NF];
+    // z-column register stencil of the face warps, per own row
+    float qn[RPW][NF], dn[RPW][NF], qLz[RPW][NF], Fzb[RPW][NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) qn[f] = dn[f] = qLz[f] = Fzb[f] = 0.f;
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) qn[r][f] = dn[r][f] = qLz[r][f] = Fzb[r][f] = 0.f;
     bool bad = false;
     float rate_max = 0.f;
     float tot[NF] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -328,7 +361,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
     auto body = [&](int it) -> bool {
         const int p = jbeg + it;
         const bool XY = p >= z0 && p < z1;               // faces of plane p wanted
-        const bool FIN = p - 1 >= z0 && p - 1 < z1;      // cell p-1 completes
+        const bool FIN = p - 1 >= z0 && p - 1 < z1;      // cells p-1 complete
         const int cb = it & 1, pb = cb ^ 1;              // buffers of plane p and of plane p+-1
         const uint32_t wpar = (uint32_t)((it + 1) >> 2) & 1u;      // D = 4
         uint64_t* wbar = bars + ((it + 1) & (D - 1));
@@ -336,118 +369,153 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
             if (XY) {
                 const float4* P4 = reinterpret_cast<const float4*>(Pbase + cb * L::PQ);
                 const float* Pp = Pbase + cb * L::PQ + 4 * NPC;
-                float q[NF], qm[NF], qp[NF];
-                ws_get(P4, Pp, pown, q);
-                ws_get(P4, Pp, pown - 1, qm);
-                ws_get(P4, Pp, pown + 1, qp);
-                // x: slope of the own cell; its right state goes to the next
-                // lane, which evaluates the face between them.  Lane 0's left
-                // face is the tile's edge face (a converter warp's), so its
-                // result is not stored.
-                float qRx[NF], qLl[NF];
+                // the column's rows yr0 - 2 .. yr0 + RPW: Y[k] is row yr0 - 2 + k
+                float Y[RPW + 3][NF];
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const float s = vminmod(q[f] - qm[f], qp[f] - q[f]);
-                    qRx[f] = fmaf(-0.5f, s, q[f]);
-                    qLl[f] = __shfl_up_sync(0xffffffffu, fmaf(0.5f, s, q[f]), 1);
+                for (int r = 0; r < RPW; ++r) {
+                    float* q = Y[2 + r];
+                    float qm[NF], qp[NF];
+                    ws_get(P4, Pp, pown0 + r * HXP, q);
+                    ws_get(P4, Pp, pown0 + r * HXP - 1, qm);
+                    ws_get(P4, Pp, pown0 + r * HXP + 1, qp);
+                    // x: slope of the own cell; its right state goes to the
+                    // next lane, which evaluates the face between them.  Lane
+                    // 0's left face is the tile's edge face (a converter
+                    // warp's), so its result is not stored.
+                    float qRx[NF], qLl[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const float s = vminmod(q[f] - qm[f], qp[f] - q[f]);
+                        qRx[f] = fmaf(-0.5f, s, q[f]);
+                        qLl[f] = __shfl_up_sync(0xffffffffu, fmaf(0.5f, s, q[f]), 1);
+                    }
+                    float Fl[NF];
+                    hllc_axis<0>(qLl, qRx, gamma, gm1, igm1, Fl);
+                    if (lane != 0) {
+                        float* Fx = Fxbase + cb * L::FX;
+                        ws_put(reinterpret_cast<float4*>(Fx), Fx + 4 * TY * L::FXR,
+                               (yr0 + r) * L::FXR + lane, Fl);
+                    }
                 }
-                float Fl[NF];
-                hllc_axis<0>(qLl, qRx, gamma, gm1, igm1, Fl);
-                if (lane != 0) {
-                    float* Fx = Fxbase + cb * L::FX;
-                    ws_put(reinterpret_cast<float4*>(Fx), Fx + 4 * TY * L::FXR,
-                           warp * L::FXR + lane, Fl);
-                }
-                // y: the face below the cell, from the four rows around it
-                float r0[NF], r1[NF], r3[NF], Fb[NF];
-                ws_get(P4, Pp, pown - 2 * HXP, r0);
-                ws_get(P4, Pp, pown - HXP, r1);
-                ws_get(P4, Pp, pown + HXP, r3);
-                face_flux4<1>(r0, r1, q, r3, gamma, gm1, igm1, Fb);
+                // y: the face below each own row.  The slope of row k, from
+                // rows k-1, k, k+1, serves the faces below and above it.
+                ws_get(P4, Pp, pown0 - 2 * HXP, Y[0]);
+                ws_get(P4, Pp, pown0 - HXP, Y[1]);
+                ws_get(P4, Pp, pown0 + RPW * HXP, Y[RPW + 2]);
+                float sl[RPW + 1][NF];                   // slope of row yr0 - 1 + j
+#pragma unroll
+                for (int j = 0; j <= RPW; ++j)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        sl[j][f] = vminmod(Y[1 + j][f] - Y[j][f], Y[2 + j][f] - Y[1 + j][f]);
                 float* Fq = Fybase + cb * L::FQ;
-                ws_put(reinterpret_cast<float4*>(Fq), Fq + 4 * FYR * TX, warp * TX + lane, Fb);
+#pragma unroll
+                for (int r = 0; r < RPW; ++r) {
+                    float qLy[NF], qRy[NF], Fb[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        qLy[f] = fmaf(0.5f, sl[r][f], Y[1 + r][f]);
+                        qRy[f] = fmaf(-0.5f, sl[r + 1][f], Y[2 + r][f]);
+                    }
+                    hllc_axis<1>(qLy, qRy, gamma, gm1, igm1, Fb);
+                    ws_put(reinterpret_cast<float4*>(Fq), Fq + 4 * FYR * TX, (yr0 + r) * TX + lane,
+                           Fb);
+                }
             }
-            // own cell of plane p+1
-            float q1[NF];
+            // own cells of plane p+1
+            float q1[RPW][NF];
             if (!mbar_wait(wbar, wpar)) {
                 atomicOr(A.status, 4);
                 s_abort[cb] = 1;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) q1[f] = qn[f];
+                for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) q1[r][f] = qn[r][f];
             } else {
                 convert_own(it + 1, q1);
             }
-            if (own && p + 1 >= z0 && p + 1 < z1) bad |= nonphys(q1);
-            // z: slope of plane p, face p-1/2, then cell p-1
-            float d1[NF];
+            if (p + 1 >= z0 && p + 1 < z1) {
 #pragma unroll
-            for (int f = 0; f < NF; ++f) d1[f] = q1[f] - qn[f];
+                for (int r = 0; r < RPW; ++r)
+                    if (own[r]) bad |= nonphys(q1[r]);
+            }
+            // z, per own row: slope of plane p, face p-1/2, then cell p-1
             if (it >= 1) {
-                float qRz[NF], qLn[NF];
+                const float* Fq = Fybase + pb * L::FQ;
+                const float* Fx = Fxbase + pb * L::FX;
+                float yb[NF];                             // y flux below the row
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const float s = vminmod(dn[f], d1[f]);
-                    qRz[f] = fmaf(-0.5f, s, qn[f]);
-                    qLn[f] = fmaf(0.5f, s, qn[f]);
-                }
-                if (it >= 2) {
-                    float Fz[NF];
-                    hllc_axis<2>(qLz, qRz, gamma, gm1, igm1, Fz);
-                    if (FIN) {
-                        // finish the x/y divergence of plane p-1 with the fluxes
-                        // written in the last iteration
-                        const float* Fq = Fybase + pb * L::FQ;
-                        float yb[NF], yt[NF];
-                        ws_get(reinterpret_cast<const float4*>(Fq), Fq + 4 * FYR * TX,
-                               warp * TX + lane, yb);
-                        ws_get(reinterpret_cast<const float4*>(Fq), Fq + 4 * FYR * TX,
-                               (warp + 1) * TX + lane, yt);
-                        const float* Fx = Fxbase + pb * L::FX;
-                        float xl[NF], xr[NF];
-                        ws_get(reinterpret_cast<const float4*>(Fx), Fx + 4 * TY * L::FXR,
-                               warp * L::FXR + lane, xl);
-                        ws_get(reinterpret_cast<const float4*>(Fx), Fx + 4 * TY * L::FXR,
-                               warp * L::FXR + lane + 1, xr);
-                        const float* Sk = ring + ((it - 1) & (D - 1)) * L::MAIN + rown;
-                        const float* U0k = u0s + pb * L::U0S + warp * TX + lane;
-                        float* Ok = Ost + cb * L::OST + warp * TX + lane;
-                        float Uo[NF];
+                for (int r = 0; r < RPW; ++r) {
+                    float qRz[NF], qLn[NF];
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) {
-                            const float Lf = fmaf(Fzb[f] - Fz[f], idz,
-                                                  fmaf(yb[f] - yt[f], idy, (xl[f] - xr[f]) * idx));
-                            const float uc = Sk[f * (HYC * HXC)];
-                            if constexpr (STAGE == 1) {
-                                Uo[f] = fmaf(dt, Lf, uc);
-                            } else {
-                                Uo[f] = fmaf(0.5f, U0k[f * (TY * TX)], 0.5f * fmaf(dt, Lf, uc));
+                    for (int f = 0; f < NF; ++f) {
+                        const float d1 = q1[r][f] - qn[r][f];
+                        const float s = vminmod(dn[r][f], d1);
+                        qRz[f] = fmaf(-0.5f, s, qn[r][f]);
+                        qLn[f] = fmaf(0.5f, s, qn[r][f]);
+                        dn[r][f] = d1;
+                    }
+                    if (it >= 2) {
+                        float Fz[NF];
+                        hllc_axis<2>(qLz[r], qRz, gamma, gm1, igm1, Fz);
+                        if (FIN) {
+                            // the x/y divergence of plane p-1 from the fluxes
+                            // written in the last iteration
+                            float yt[NF], xl[NF], xr[NF];
+                            if (r == 0)
+                                ws_get(reinterpret_cast<const float4*>(Fq), Fq + 4 * FYR * TX,
+                                       yr0 * TX + lane, yb);
+                            ws_get(reinterpret_cast<const float4*>(Fq), Fq + 4 * FYR * TX,
+                                   (yr0 + r + 1) * TX + lane, yt);
+                            ws_get(reinterpret_cast<const float4*>(Fx), Fx + 4 * TY * L::FXR,
+                                   (yr0 + r) * L::FXR + lane, xl);
+                            ws_get(reinterpret_cast<const float4*>(Fx), Fx + 4 * TY * L::FXR,
+                                   (yr0 + r) * L::FXR + lane + 1, xr);
+                            const float* Sk =
+                                ring + ((it - 1) & (D - 1)) * L::MAIN + rown0 + r * HXC;
+                            const float* U0k = u0s + pb * L::U0S + (yr0 + r) * TX + lane;
+                            float* Ok = Ost + cb * L::OST + (yr0 + r) * TX + lane;
+                            float Uo[NF];
+#pragma unroll
+                            for (int f = 0; f < NF; ++f) {
+                                const float Lf = fmaf(Fzb[r][f] - Fz[f], idz,
+                                                      fmaf(yb[f] - yt[f], idy, (xl[f] - xr[f]) * idx));
+                                const float uc = Sk[f * (HYC * HXC)];
+                                if constexpr (STAGE == 1) {
+                                    Uo[f] = fmaf(dt, Lf, uc);
+                                } else {
+                                    Uo[f] = fmaf(0.5f, U0k[f * (TY * TX)], 0.5f * fmaf(dt, Lf, uc));
+                                }
+                                Ok[f * (TY * TX)] = Uo[f];
+                                yb[f] = yt[f];
                             }
-                            Ok[f * (TY * TX)] = Uo[f];
-                        }
-                        fence_proxy_async_smem();        // the staged plane is read by TMA
-                        if (EPI && A.rate_slot) {
-                            float W[NF];
-                            cons_to_prim(Uo, gm1, W);
-                            const float r = cell_rate(W, gamma, A.act, A.rdx);
-                            const bool up = own && (r > rate_max || r != r);
-                            rate_max = up ? r : rate_max;
-                        }
-                        if (EPI && A.tot_partial) {
+                            if (EPI && A.rate_slot) {
+                                const float rr = ws_rate(Uo, gamma, gm1, A.rdx);
+                                const bool up = own[r] && (rr > rate_max || rr != rr);
+                                rate_max = up ? rr : rate_max;
+                            }
+                            if (EPI && A.tot_partial) {
 #pragma unroll
-                            for (int f = 0; f < NF; ++f) tot[f] += own ? Uo[f] : 0.f;
+                                for (int f = 0; f < NF; ++f) tot[f] += own[r] ? Uo[f] : 0.f;
+                            }
                         }
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) Fzb[r][f] = Fz[f];
                     }
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) Fzb[f] = Fz[f];
+                    for (int f = 0; f < NF; ++f) qLz[r][f] = qLn[f];
                 }
+                if (FIN && it >= 2) fence_proxy_async_smem();   // the staged plane is read by TMA
+            } else {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) qLz[f] = qLn[f];
+                for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) dn[r][f] = q1[r][f] - qn[r][f];
             }
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                dn[f] = d1[f];
-                qn[f] = q1[f];
-            }
+            for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) qn[r][f] = q1[r][f];
         } else {
             // ---- converter warps ----
             if (tid == issuer) {
@@ -464,7 +532,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
             if (XY) {
                 const float4* P4 = reinterpret_cast<const float4*>(Pbase + cb * L::PQ);
                 const float* Pp = Pbase + cb * L::PQ + 4 * NPC;
-                const int cw = warp - TY;                // converter warp index
+                const int cw = warp - NFW;               // converter warp index
                 float q0[NF], q1[NF], q2[NF], q3[NF], F[NF];
                 if (cw == 0) {
                     // y faces above the top row (one per column)
@@ -503,7 +571,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
                 const float* strip = strips + pb * L::STRIP;
                 float* Pq = Pbase + pb * L::PQ;
                 const bool fz = zflip(p + 1);
-                for (int e = tid - 32 * TY; e < L::NHALO; e += NCT) {
+                for (int e = tid - 32 * NFW; e < L::NHALO; e += NCT) {
                     int cx, cy;
                     halo_cell<TX, TY>(e, cx, cy);
                     float U[NF], W[NF];
@@ -589,7 +657,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
         if (any_bad) atomicOr(A.status, 1);
         if (EPI && A.rate_slot) {
             unsigned long long b = 0;
-            for (int w = 0; w < TY; ++w) b = red_rate[w] > b ? red_rate[w] : b;
+            for (int w = 0; w < NFW; ++w) b = red_rate[w] > b ? red_rate[w] : b;
             atomicMax(A.rate_slot, b);
         }
     }
@@ -597,7 +665,7 @@ stage_ws_kernel(const __grid_constant__ StageArgs<float> A, const __grid_constan
         const long long bz = A.zlo / A.zchunk + blockIdx.z;
         const long long blk = (bz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         double s = 0.0;
-        for (int w = 0; w < TY; ++w) s += red_tot[w][tid];
+        for (int w = 0; w < NFW; ++w) s += red_tot[w][tid];
         A.tot_partial[blk * NF + tid] = s;
     }
 }

@@ -75,7 +75,9 @@ __device__ __forceinline__ void plm_faces(const V q0[5], const V q1[5], const V 
 //   S*  = [p_R - p_L + m_L u_L - m_R u_R] / (m_L - m_R),    m_K = rho_K (S_K - u_K),
 //   f   = m_K / (S_K - S*)                                  (rho* of the star state),
 //   f e* = [(S_K - u_K) E_K + (S* - u_K)(m_K S* + p_K)] / (S_K - S*),
-// the last being the star energy rho_K (S_K-u_K)/(S_K-S*) [E_K/rho_K +
+//   F_t = F_rho t_K for both tangential components (the tangential velocity
+//         is t_K on the whole K side of the contact, star state included),
+// the energy term being the star energy rho_K (S_K-u_K)/(S_K-S*) [E_K/rho_K +
 // (S*-u_K)(S* + p_K/(rho_K (S_K-u_K)))] with m_K / rho_K = S_K - u_K taken out.
 // The root's argument is kept at or above the smallest normal number, so a
 // zero pressure gives c = 0 rather than 0 * inf.
@@ -109,8 +111,8 @@ __device__ __forceinline__ void hllc_core(const V WL[5], const V WR[5], V gamma,
     const V dr = vsub(fac, r);
     F[0] = vfma(s, dr, mu);
     F[1] = vfma(s, vsub(vmul(fac, Sstar), mu), vfma(mu, u, p));
-    F[2] = vfma(s, vmul(dr, t1), vmul(mu, t1));
-    F[3] = vfma(s, vmul(dr, t2), vmul(mu, t2));
+    F[2] = vmul(F[0], t1);                              // tangential momentum moves with the mass
+    F[3] = vmul(F[0], t2);
     F[4] = vfma(s, vsub(fes, E), vmul(vadd(E, p), u));
 }
 
