@@ -764,7 +764,8 @@ def main():
             "ms_per_step": msw / kw, "status": hh.hard_hydro_strerror(mw.get_error()),
             "roofline": {"bound": "hbm", "achieved": w_achieved, "peak": hbm, "unit": "GB/s",
                          "frac": w_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "weno_stage_kernel<float,32,8,3> z-chunk 32 "
+                         "kernel": "weno_x_kernel + weno_march_kernel (y') + weno_march_kernel "
+                                   "(z', combine): one stage's three sweeps, z/y chunks of 64 "
                                    "(mean of stage 1 and stage 2)",
                          "algorithmic_bytes_per_launch": alg_bytes2, "launch_ms": wstage_ms}}
     del mw, Uw, W1, W2

@@ -36,6 +36,8 @@ struct hard_hydro_s {
     unsigned char* slots = nullptr;  // rate | dt | t | status | totals[5]
     double* tot_partial = nullptr;
     long long tot_rows = 0;
+    void* wL = nullptr;              // flux difference between the WENO sweeps (3D meshes)
+    size_t wL_bytes = 0;
     void* adj = nullptr;             // adjoint scratch: primitive cotangent | stage-1 cotangent
     size_t adj_bytes = 0;
     hh::FldHierarchy* fld = nullptr; // radiation diffusion multigrid levels, on first use
@@ -111,6 +113,9 @@ void free_scratch(hard_hydro_s* h) {
     h->adj = nullptr;
     h->adj_bytes = 0;
     if (h->U1) cudaFree(h->U1);
+    if (h->wL) cudaFree(h->wL);
+    h->wL = nullptr;
+    h->wL_bytes = 0;
     if (h->Udev) cudaFree(h->Udev);
     if (h->tot_partial) cudaFree(h->tot_partial);
     h->U1 = h->Udev = nullptr;
@@ -126,8 +131,25 @@ int ensure_slots(hard_hydro_s* h) {
     return from_cuda(cudaMemset(h->slots, 0, SLOT_BYTES));
 }
 
+// The WENO scheme on a 3D mesh runs as directional sweeps that pass the
+// flux difference through a state-sized buffer.
+int ensure_weno_scratch(hard_hydro_s* h) {
+    if (!(h->scheme == HARD_SCHEME_WENO5Z_HLL && h->mesh.dim == 3)) return HARD_OK;
+    const size_t need = state_bytes(h);
+    if (h->wL && h->wL_bytes >= need) return HARD_OK;
+    if (h->wL) cudaFree(h->wL);
+    h->wL = nullptr;
+    h->wL_bytes = 0;
+    int rc = dev_alloc(&h->wL, need);
+    if (rc) return rc;
+    h->wL_bytes = need;
+    return HARD_OK;
+}
+
 int ensure_U1(hard_hydro_s* h) {
     int rc = ensure_slots(h);
+    if (rc) return rc;
+    rc = ensure_weno_scratch(h);
     if (rc) return rc;
     size_t need = state_bytes(h);
     if (h->U1 && h->U1_bytes >= need) return HARD_OK;
@@ -178,16 +200,20 @@ bool halo_ready(const hard_hydro_s* h) {
 
 // blocks of one stage launch (rows of the totals partial array)
 long long launch_blocks(const hard_hydro_s* h) {
-    return hh::stage_blocks(h->mesh, weno(h) ? 0 : tile_of(h));
+    if (weno(h)) return hh::weno_stage_blocks(h->mesh, h->mesh.dim == 3);
+    return hh::stage_blocks(h->mesh, tile_of(h));
 }
 
 cudaError_t stage_launch(hard_hydro_s* h, const StageCall& call, cudaStream_t s) {
     StageCall c = call;
     c.zg[0] = h->zg[0];
     c.zg[1] = h->zg[1];
-    if (weno(h))
+    if (weno(h)) {
+        c.scratch = h->wL;           // set by ensure_weno_scratch before any 3D launch
+        if (h->mesh.dim == 3 && !c.scratch) return cudaErrorInvalidValue;
         return h->dtype == HARD_F64 ? hh::launch_weno_stage_f64(h->mesh, c, s)
                                     : hh::launch_weno_stage_f32(h->mesh, c, s);
+    }
     if (h->dtype == HARD_F64) return hh::launch_stage_f64(h->mesh, h->kernel, tile_of(h), c, s);
     return hh::launch_stage_f32(h->mesh, h->kernel, tile_of(h), c, s);
 }
@@ -416,6 +442,8 @@ int hard_hydro_stage_ex(hard_hydro_t h, int stage, const void* U0, const void* U
     if (Uout == Ucur) return HARD_EINVAL;
     if (!dt_dev && (!(dt > 0.0) || !std::isfinite(dt))) return HARD_EINVAL;
     int rc = ensure_slots(h);
+    if (rc) return rc;
+    rc = ensure_weno_scratch(h);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->last = s;

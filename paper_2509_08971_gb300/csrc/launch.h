@@ -38,6 +38,8 @@ struct StageCall {
                                    // zlo a multiple of the tile's z-chunk
     const void* zg[2] = {nullptr, nullptr};  // ghost planes of BC_HALO z faces (below, above),
                                              // each [5][2][ny][nx]
+    void* scratch = nullptr;       // WENO on 3D meshes: [5][N] flux-difference buffer of the
+                                   // sweeps (nullptr: the fused kernel)
 };
 
 // Tile configurations per number of active axes (the autotuner's space).

@@ -172,10 +172,14 @@ __device__ __forceinline__ void weno5z_pair(float v0, float v1, float v2, float 
     // mirrored stencil has s' = (s2, s1, s0) and t' = (t2, -t1, t0), so the
     // left value's are v2 + (u2 + w2), v2 + (u1 + w1), v2 + (u0 - w0).  Each
     // value is then v2 + sum a_k (p_k - v2) / sum a_k.
+    // The indicators' differences from the four first differences d_k of
+    // the stencil: s0 = d01 - d12, t0 = d01 - 3 d12, s1 = d12 - d23,
+    // t1 = d12 + d23, s2 = d23 - d34, t2 = 3 d23 - d34 (d_ab = v_a - v_b).
     const float c = 13.0f / 12.0f, twelfth = 1.0f / 12.0f;
-    const float s0 = v0 - 2.0f * v1 + v2, t0 = v0 - 4.0f * v1 + 3.0f * v2;
-    const float s1 = v1 - 2.0f * v2 + v3, t1 = v1 - v3;
-    const float s2 = v2 - 2.0f * v3 + v4, t2 = 3.0f * v2 - 4.0f * v3 + v4;
+    const float d01 = v0 - v1, d12 = v1 - v2, d23 = v2 - v3, d34 = v3 - v4;
+    const float s0 = d01 - d12, t0 = fmaf(-3.0f, d12, d01);
+    const float s1 = d12 - d23, t1 = d12 + d23;
+    const float s2 = d23 - d34, t2 = fmaf(3.0f, d23, -d34);
     const float w0 = 0.25f * t0, w1 = 0.25f * t1, w2 = 0.25f * t2;    // exact
     const float b0 = fmaf(c * s0, s0, w0 * t0);
     const float b1 = fmaf(c * s1, s1, w1 * t1);
@@ -183,11 +187,14 @@ __device__ __forceinline__ void weno5z_pair(float v0, float v1, float v2, float 
     const float tau = fabsf(b0 - b2);
     const float r0 = tau * vrcp(b0 + 1e-30f), r1 = tau * vrcp(b1 + 1e-30f),
                 r2 = tau * vrcp(b2 + 1e-30f);
-    const float u0 = s0 * twelfth, u1 = s1 * twelfth, u2 = s2 * twelfth;
     const float a0 = fmaf(0.1f, r0, 0.1f), a1 = fmaf(0.6f, r1, 0.6f), a2 = fmaf(0.3f, r2, 0.3f);
     const float l0 = fmaf(0.1f, r2, 0.1f), l2 = fmaf(0.3f, r0, 0.3f);
-    right = fmaf(fmaf(a0, u0 + w0, fmaf(a1, u1 - w1, a2 * (u2 - w2))), vrcp(a0 + a1 + a2), v2);
-    left = fmaf(fmaf(l0, u2 + w2, fmaf(a1, u1 + w1, l2 * (u0 - w0))), vrcp(l0 + a1 + l2), v2);
+    // candidate offsets u_k +- w_k with u_k = s_k / 12
+    const float e0p = fmaf(s0, twelfth, w0), e0m = fmaf(s0, twelfth, -w0);
+    const float e1p = fmaf(s1, twelfth, w1), e1m = fmaf(s1, twelfth, -w1);
+    const float e2p = fmaf(s2, twelfth, w2), e2m = fmaf(s2, twelfth, -w2);
+    right = fmaf(fmaf(a0, e0p, fmaf(a1, e1m, a2 * e2m)), vrcp(a0 + a1 + a2), v2);
+    left = fmaf(fmaf(l0, e2p, fmaf(a1, e1p, l2 * e0m)), vrcp(l0 + a1 + l2), v2);
 }
 
 // HLL flux along physical axis AX from the face states (primitives).

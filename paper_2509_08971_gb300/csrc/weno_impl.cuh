@@ -5,6 +5,7 @@
 #include "devattr.h"
 #include "weno.cuh"
 #include "weno_launch.h"
+#include "weno_sweep.cuh"
 
 #define HH_WCAT2(a, b) a##b
 #define HH_WCAT(a, b) HH_WCAT2(a, b)
@@ -60,6 +61,25 @@ cudaError_t run_weno(const MeshDesc& m, const StageCall& c, cudaStream_t s) {
     const cudaError_t e = smem_attr_once(kern, smem, attr);
     if (e != cudaSuccess) return e;
     kern<<<grid, TX * TY, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+// The three sweeps of one stage on a 3D mesh (weno_sweep.cuh).
+cudaError_t run_weno_sweeps(const MeshDesc& m, const StageCall& c, cudaStream_t s) {
+    const StageArgs<T> A = weno_args(m, WENO_SWEEP_CHUNK, c);
+    T* L = static_cast<T*>(c.scratch);
+    const long long items = (long long)m.n[1] * m.n[2] * wcdiv(m.n[0], SWEEP_SEG);
+    const long long xblocks = wcdiv(items, (long long)(SWEEP_THREADS / 32));
+    if (xblocks > 0x7fffffffLL || m.n[1] > 65535 || m.n[2] > 65535) return cudaErrorInvalidValue;
+    weno_x_kernel<T, 0><<<(unsigned)xblocks, SWEEP_THREADS, 0, s>>>(A, L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 gy(wcdiv(m.n[0], SWEEP_THREADS), m.n[2], wcdiv(m.n[1], WENO_SWEEP_CHUNK));
+    weno_march_kernel<T, 1, 1, false><<<gy, SWEEP_THREADS, 0, s>>>(A, L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 gz(wcdiv(m.n[0], SWEEP_THREADS), m.n[1], wcdiv(m.n[2], WENO_SWEEP_CHUNK));
+    weno_march_kernel<T, 2, 2, true><<<gz, SWEEP_THREADS, 0, s>>>(A, L);
     return cudaGetLastError();
 }
 
@@ -120,7 +140,7 @@ cudaError_t HH_WCAT(launch_weno_stage_, HH_SUFFIX)(const MeshDesc& m, const Stag
                   "the WENO launcher runs tile 0 of each table");
     for (int a = 0; a < 3; ++a)
         if (m.n[a] > 1 && m.n[a] < WENO_G) return cudaErrorInvalidValue;
-    if (m.dim == 3) return run_weno<32, 8, 3, 0, 1>(m, c, s);
+    if (m.dim == 3) return c.scratch ? run_weno_sweeps(m, c, s) : run_weno<32, 8, 3, 0, 1>(m, c, s);
     if (m.dim == 2) {
         if (m.px == 0 && m.py == 1) return run_weno<32, 8, 2, 0, 1>(m, c, s);
         if (m.px == 0 && m.py == 2) return run_weno<32, 8, 2, 0, 2>(m, c, s);
