@@ -641,8 +641,11 @@ int hard_hydro_advect_E(hard_hydro_t h, const void* U, void* Er, double dt, void
     h->last = s;
     const bool f64 = h->dtype == HARD_F64;
     auto stage = f64 ? hh::launch_advect_E_stage_f64 : hh::launch_advect_E_stage_f32;
-    cudaError_t e = stage(h->mesh, 1, U, nullptr, Er, h->U1, dt, s);   // U1 holds E1
-    if (e == cudaSuccess) e = stage(h->mesh, 2, U, Er, h->U1, Er, dt, s);
+    // U1 holds E1 in its first field and, on 3D meshes, the sweeps' flux
+    // difference in its second
+    void* L = h->mesh.dim == 3 ? static_cast<char*>(h->U1) + h->mesh.N * elem_size(h) : nullptr;
+    cudaError_t e = stage(h->mesh, 1, U, nullptr, Er, h->U1, dt, L, s);
+    if (e == cudaSuccess) e = stage(h->mesh, 2, U, Er, h->U1, Er, dt, L, s);
     return from_cuda(e);
 }
 

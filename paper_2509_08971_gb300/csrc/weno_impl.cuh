@@ -68,10 +68,9 @@ cudaError_t run_weno(const MeshDesc& m, const StageCall& c, cudaStream_t s) {
 cudaError_t run_weno_sweeps(const MeshDesc& m, const StageCall& c, cudaStream_t s) {
     const StageArgs<T> A = weno_args(m, WENO_SWEEP_CHUNK, c);
     T* L = static_cast<T*>(c.scratch);
-    const long long items = (long long)m.n[1] * m.n[2] * wcdiv(m.n[0], SWEEP_SEG);
-    const long long xblocks = wcdiv(items, (long long)(SWEEP_THREADS / 32));
-    if (xblocks > 0x7fffffffLL || m.n[1] > 65535 || m.n[2] > 65535) return cudaErrorInvalidValue;
-    weno_x_kernel<T, 0><<<(unsigned)xblocks, SWEEP_THREADS, 0, s>>>(A, L);
+    if (m.n[1] > 65535 || m.n[2] > 65535) return cudaErrorInvalidValue;
+    const dim3 gx(wcdiv(m.n[0], SWEEP_SEG), wcdiv(m.n[1], SWEEP_THREADS / 32), m.n[2]);
+    weno_x_kernel<T, 0><<<gx, SWEEP_THREADS, 0, s>>>(A, L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 gy(wcdiv(m.n[0], SWEEP_THREADS), m.n[2], wcdiv(m.n[1], WENO_SWEEP_CHUNK));
@@ -96,11 +95,27 @@ cudaError_t run_advect(const MeshDesc& m, const AdvectArgs<T>& A, cudaStream_t s
     return cudaGetLastError();
 }
 
+// The three sweeps of one advection stage on a 3D mesh (weno_sweep.cuh).
+cudaError_t run_advect_sweeps(const MeshDesc& m, const AdvectArgs<T>& A, T* L, cudaStream_t s) {
+    if (m.n[1] > 65535 || m.n[2] > 65535) return cudaErrorInvalidValue;
+    const dim3 gx(wcdiv(m.n[0], SWEEP_SEG), wcdiv(m.n[1], SWEEP_THREADS / 32), m.n[2]);
+    advect_x_kernel<T, 0><<<gx, SWEEP_THREADS, 0, s>>>(A, L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 gy(wcdiv(m.n[0], SWEEP_THREADS), m.n[2], wcdiv(m.n[1], WENO_SWEEP_CHUNK));
+    advect_march_kernel<T, 1, 1, false><<<gy, SWEEP_THREADS, 0, s>>>(A, L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 gz(wcdiv(m.n[0], SWEEP_THREADS), m.n[1], wcdiv(m.n[2], WENO_SWEEP_CHUNK));
+    advect_march_kernel<T, 2, 2, true><<<gz, SWEEP_THREADS, 0, s>>>(A, L);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t HH_WCAT(launch_advect_E_stage_, HH_SUFFIX)(const MeshDesc& m, int stage, const void* U,
                                                        const void* E0, const void* Ec, void* Eo,
-                                                       double dt, cudaStream_t s) {
+                                                       double dt, void* scratch, cudaStream_t s) {
     for (int a = 0; a < 3; ++a)
         if (m.n[a] > 1 && m.n[a] < WENO_G) return cudaErrorInvalidValue;
     AdvectArgs<T> A{};
@@ -118,6 +133,10 @@ cudaError_t HH_WCAT(launch_advect_E_stage_, HH_SUFFIX)(const MeshDesc& m, int st
     A.dt = dt;
     A.stage = stage;
     A.zchunk = tile_desc(3, 0).zc;
+    if (m.dim == 3 && scratch) {
+        A.zchunk = WENO_SWEEP_CHUNK;
+        return run_advect_sweeps(m, A, static_cast<T*>(scratch), s);
+    }
     if (m.dim == 3) return run_advect<32, 8, 3, 0, 1>(m, A, s);
     if (m.dim == 2) {
         if (m.px == 0 && m.py == 1) return run_advect<32, 8, 2, 0, 1>(m, A, s);

@@ -36,11 +36,15 @@ cudaError_t launch_weno_stage_f64(const MeshDesc& m, const StageCall& c, cudaStr
 // One Heun stage of the radiation energy advection (WENO5-Z states, Rusanov
 // flux) with the fluid state U [5][N] held fixed: stage 1 writes
 // Eo = Ec + dt L(Ec), stage 2 Eo = E0/2 + (Ec + dt L(Ec))/2 (Eo may alias E0,
-// not Ec).  Every active axis needs at least three cells.
+// not Ec).  On a 3D mesh with `scratch` set (N elements aliasing none of the
+// other buffers) it runs as three directional sweeps, otherwise as the fused
+// kernel.  Every active axis needs at least three cells.
 cudaError_t launch_advect_E_stage_f32(const MeshDesc& m, int stage, const void* U, const void* E0,
-                                      const void* Ec, void* Eo, double dt, cudaStream_t s);
+                                      const void* Ec, void* Eo, double dt, void* scratch,
+                                      cudaStream_t s);
 cudaError_t launch_advect_E_stage_f64(const MeshDesc& m, int stage, const void* U, const void* E0,
-                                      const void* Ec, void* Eo, double dt, cudaStream_t s);
+                                      const void* Ec, void* Eo, double dt, void* scratch,
+                                      cudaStream_t s);
 
 // The scheme of a handle (hard_hydro.cu): HARD_SCHEME_PLM_HLLC or
 // HARD_SCHEME_WENO5Z_HLL.

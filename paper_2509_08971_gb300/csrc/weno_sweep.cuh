@@ -88,22 +88,19 @@ __device__ __forceinline__ void sweep_epilogue(const StageArgs<T>& A, bool bad, 
     }
 }
 
-// x sweep: one warp per 30-cell segment of a row (y', z' fixed); writes L.
+// x sweep: one warp per 30-cell segment of a row (y', z' fixed); a block
+// takes one segment of four consecutive rows.  Writes L.
 template <typename T, int PX>
 __global__ void __launch_bounds__(SWEEP_THREADS)
 weno_x_kernel(const StageArgs<T> A, T* __restrict__ L) {
     __shared__ T win[SWEEP_THREADS / 32][NF][SWEEP_WIN];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-    const int n0 = A.n[0], n1 = A.n[1], n2 = A.n[2];
-    const int nseg = (n0 + SWEEP_SEG - 1) / SWEEP_SEG;
-    const long long item = (long long)blockIdx.x * (SWEEP_THREADS / 32) + wq;
-    const long long items = (long long)n1 * n2 * nseg;
-    const bool active = item < items;                  // warp-uniform
-    const long long it = active ? item : 0;
-    const int seg = (int)(it % nseg);
-    const long long row = it / nseg;                   // z' * n1 + y'
-    const long long base = row * n0;
-    const int xs = seg * SWEEP_SEG;
+    const int n0 = A.n[0], n1 = A.n[1];
+    // segment blockIdx.x of rows y' = 4 blockIdx.y + warp, z' = blockIdx.z
+    const int yr = blockIdx.y * (SWEEP_THREADS / 32) + wq;
+    const bool active = yr < n1;                       // warp-uniform
+    const long long base = ((long long)blockIdx.z * n1 + (active ? yr : 0)) * n0;
+    const int xs = blockIdx.x * SWEEP_SEG;
     const T gamma = A.gamma;
     const T gx = sizeof(T) == 4 ? A.igm1 : A.gm1;     // the HLL energy closure
     bool bad = false;                                  // reported by the combining sweep
@@ -295,6 +292,147 @@ weno_march_kernel(const StageArgs<T> A, T* __restrict__ L) {
     if constexpr (LAST) {
         const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         sweep_epilogue(A, bad, rate_max, tot, blk);
+    }
+}
+
+// ---------------------------------------------------- radiation energy --
+// The advection of E (weno_advect_kernel's scheme: WENO5-Z states of E and of
+// the normal velocity, the Rusanov flux) as the same three sweeps on 3D
+// meshes: the x sweep writes L, the y' march adds to it, the z' march adds
+// its part and forms the Heun stage.  L is one field.
+
+// m / rho: IEEE division in FP64 (the oracle's rounding); FP32 multiplies by
+// the approximate reciprocal, as its conversion to primitives does.
+__device__ __forceinline__ double sweep_ratio(double m, double rho) { return m / rho; }
+__device__ __forceinline__ float sweep_ratio(float m, float rho) { return m * vrcp(rho); }
+
+// E and the velocity along kernel axis AX (momentum slot 1+PA) of cell m of
+// the line, through the axis' boundary map.
+template <typename T, int AX, int PA>
+__device__ __forceinline__ void sweep_ev(const AdvectArgs<T>& A, long long base, int m, int nA,
+                                         long long stride, T& e, T& u) {
+    bool flip;
+    const int sidx = bc_map3(m, nA, A.bc_lo[AX], A.bc_hi[AX], flip);
+    const long long c = base + (long long)sidx * stride;
+    const T rho = __ldg(A.U + c);
+    T mom = __ldg(A.U + (1 + PA) * A.N + c);
+    if (flip) mom = -mom;
+    e = __ldg(A.Ec + c);
+    u = sweep_ratio(mom, rho);
+}
+
+template <typename T, int PX>
+__global__ void __launch_bounds__(SWEEP_THREADS)
+advect_x_kernel(const AdvectArgs<T> A, T* __restrict__ L) {
+    __shared__ T win[SWEEP_THREADS / 32][2][SWEEP_WIN];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int n0 = A.n[0], n1 = A.n[1];
+    const int yr = blockIdx.y * (SWEEP_THREADS / 32) + wq;     // as in weno_x_kernel
+    const bool active = yr < n1;
+    const long long base = ((long long)blockIdx.z * n1 + (active ? yr : 0)) * n0;
+    const int xs = blockIdx.x * SWEEP_SEG;
+    {
+        T e, u;
+        sweep_ev<T, 0, PX>(A, base, xs - 3 + lane, n0, 1, e, u);
+        win[wq][0][lane] = e;
+        win[wq][1][lane] = u;
+        if (lane < SWEEP_WIN - 32) {
+            sweep_ev<T, 0, PX>(A, base, xs + 29 + lane, n0, 1, e, u);
+            win[wq][0][32 + lane] = e;
+            win[wq][1][32 + lane] = u;
+        }
+    }
+    __syncwarp();
+    const T* ve = &win[wq][0][lane];
+    const T* vu = &win[wq][1][lane];
+    T er, el, ur, ul;
+    weno5z_pair(ve[0], ve[1], ve[2], ve[3], ve[4], er, el);
+    weno5z_pair(vu[0], vu[1], vu[2], vu[3], vu[4], ur, ul);
+    const T eL = __shfl_up_sync(0xffffffffu, er, 1), uL = __shfl_up_sync(0xffffffffu, ur, 1);
+    const T Fl = rusanov_e(eL, el, uL, ul);
+    const T Fr = __shfl_down_sync(0xffffffffu, Fl, 1);
+    const int x = xs - 1 + lane;
+    if (active && lane >= 1 && lane <= SWEEP_SEG && x < n0)
+        L[base + x] = sub_over_dx(T(0), Fr - Fl, A.dxk[0]);
+}
+
+template <typename T, int AX, int PA, bool LAST>
+__global__ void __launch_bounds__(SWEEP_THREADS)
+advect_march_kernel(const AdvectArgs<T> A, T* __restrict__ L) {
+    static_assert(AX == 1 || AX == 2, "the x' axis is the x sweep's");
+    const int n0 = A.n[0], n1 = A.n[1];
+    const int nA = A.n[AX];
+    const int x = blockIdx.x * SWEEP_THREADS + threadIdx.x;
+    const bool xin = x < n0;
+    const int xl = xin ? x : n0 - 1;
+    const int o = blockIdx.y;
+    const long long stride = AX == 1 ? (long long)n0 : (long long)n0 * n1;
+    const long long base = (AX == 1 ? (long long)o * n1 * n0 : (long long)o * n0) + xl;
+    const int a0 = blockIdx.z * A.zchunk;
+    const int a1 = min(a0 + A.zchunk, nA);
+    const T dt = (T)A.dt;
+    const bool two = A.stage == 2;
+    // E and u of the last five cells, the upper values of the newest pair's
+    // lower neighbour, the last face flux; the next cell and the operands of
+    // the cell completing at the next step are fetched one step ahead
+    T we[5], wu[5], eUp = T(0), uUp = T(0), Fp = T(0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) we[q] = wu[q] = T(0);
+    // the next cell's raw values (density, normal momentum, E, wall flip):
+    // the velocity is formed when the cell enters the window, so the loads
+    // have a whole step to arrive
+    auto fetch = [&](int m, T& r, T& mo, T& e, bool& flip) {
+        const int sidx = bc_map3(m, nA, A.bc_lo[AX], A.bc_hi[AX], flip);
+        const long long c = base + (long long)sidx * stride;
+        r = __ldg(A.U + c);
+        mo = __ldg(A.U + (1 + PA) * A.N + c);
+        e = __ldg(A.Ec + c);
+    };
+    T rn, mn, en, Lk = T(0), E0k = T(0);
+    bool fn;
+    fetch(a0 - 3, rn, mn, en, fn);
+#pragma unroll 1
+    for (int j = a0 - 3; j <= a1 + 2; ++j) {
+        const int cnt = j - (a0 - 3);
+        const T rj = rn, ej = en;
+        const T mj = fn ? -mn : mn;
+        if (j < a1 + 2) fetch(j + 1, rn, mn, en, fn);
+        const T uj = sweep_ratio(mj, rj);
+        const T Lc = Lk, E0c = E0k;
+        if (cnt >= 5 && j < a1 + 2) {
+            const long long ck = base + (long long)(j - 2) * stride;
+            Lk = L[ck];
+            if (LAST && two) E0k = A.E0[ck];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            we[q] = we[q + 1];
+            wu[q] = wu[q + 1];
+        }
+        we[4] = ej;
+        wu[4] = uj;
+        if (cnt >= 4) {
+            T eu, el, uu, ul;
+            weno5z_pair(we[0], we[1], we[2], we[3], we[4], eu, el);
+            weno5z_pair(wu[0], wu[1], wu[2], wu[3], wu[4], uu, ul);
+            if (cnt >= 5) {
+                const T F = rusanov_e(eUp, el, uUp, ul);
+                if (cnt >= 6 && xin) {
+                    // cell j-3, whose E is we[1]
+                    const long long c = base + (long long)(j - 3) * stride;
+                    const T D = sub_over_dx(Lc, F - Fp, A.dxk[AX]);
+                    if constexpr (LAST) {
+                        const T ec = we[1];
+                        A.Eo[c] = two ? madd(T(0.5), E0c, T(0.5) * madd(dt, D, ec)) : madd(dt, D, ec);
+                    } else {
+                        L[c] = D;
+                    }
+                }
+                Fp = F;
+            }
+            eUp = eu;
+            uUp = uu;
+        }
     }
 }
 

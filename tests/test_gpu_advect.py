@@ -12,7 +12,7 @@ hh = pytest.importorskip("paper_2509_08971_gb300")
 from test_gpu_parity import F64_TOL, random_state  # noqa: E402
 
 SHAPES = [(1, 1, 300), (1, 37, 1), (29, 1, 1), (1, 19, 45), (13, 1, 40), (17, 21, 1),
-          (11, 13, 37), (70, 9, 8), (3, 3, 3)]
+          (11, 13, 37), (70, 9, 8), (20, 67, 61), (3, 3, 3)]
 BCS = [(0,) * 6, (1,) * 6, (2,) * 6, (2, 1, 0, 0, 1, 2)]
 
 
