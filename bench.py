@@ -823,7 +823,8 @@ def main():
               "ms_per_step": adv_ms,
               "roofline": {"bound": "hbm", "achieved": adv_achieved, "peak": hbm, "unit": "GB/s",
                            "frac": adv_achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                           "kernel": "weno_advect_kernel<float,32,8,3> (mean of the two stages)",
+                           "kernel": "advect_x_kernel + advect_march_kernel (y') + "
+                                     "advect_march_kernel (z', Heun stage): three sweeps per stage",
                            "algorithmic_bytes_per_step": adv_bytes}}
     del Ea, ms2, Us
 
