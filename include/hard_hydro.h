@@ -151,13 +151,53 @@ int hard_hydro_stage_ex(hard_hydro_t h, int stage, const void* U0, const void* U
  * device copies on `stream`, so the buffers can go straight to a
  * send/receive.  A step is then: exchange U^n, stage 1, exchange U1,
  * stage 2 with the rate, a max of the rates over the slabs, and
- * hard_hydro_finalize_dt.  hard_hydro_step, hard_hydro_advance(_host), the
- * adjoint, the radiation advection and diffusion and the no-allocation step
- * return HARD_EUNSUPPORTED on a handle with a halo face (the ghosts change
- * between the two stages of a step). */
+ * hard_hydro_finalize_dt.  hard_hydro_step, hard_hydro_advance(_host),
+ * hard_hydro_step_backward, the radiation advection and diffusion and the
+ * no-allocation step return HARD_EUNSUPPORTED on a handle with a halo face
+ * (the ghosts change between the two stages of a step); the adjoint of a
+ * slab runs through the split calls below. */
 int hard_hydro_set_zghost(hard_hydro_t h, const void* ghost_lo, const void* ghost_hi);
 int hard_hydro_pack_zhalo(hard_hydro_t h, const void* U, void* send_lo, void* send_hi,
                           void* stream);
+
+/* ---- the adjoint of a slab (the ghost exchange reversed) ----
+ * The paper has no counterpart (it computes no derivatives).  A stage's VJP
+ * (see hard_hydro_step_backward; lambda = b dt G with b = 1 in stage 1 and
+ * 1/2 in stage 2) is split around an exchange of cotangents:
+ *   hard_hydro_stage_vjp_faces  every face of the slab (the faces on its
+ *       z boundaries included, with the lambda of the neighbour's cells
+ *       taken as zero: the neighbour evaluates the same face with this
+ *       slab's lambda as zero, and the two halves sum to the face's VJP)
+ *       runs its flux backwards onto the primitive cotangents of its four
+ *       stencil cells: this slab's cells into the handle's accumulator, the
+ *       ghost cells into the caller's accumulators set by
+ *       hard_hydro_set_zghost_adjoint (gw_lo for the two planes below,
+ *       gw_hi above; each [2][ny][nx] records of 8 elements of the
+ *       handle's type, 16-byte aligned, zeroed by this call first).  Uc's
+ *       ghost planes come from hard_hydro_set_zghost.  Adds the faces'
+ *       d/dgamma to *g_gamma.
+ *   the caller sends gw_lo to the slab below and gw_hi to the slab above;
+ *   hard_hydro_add_zghost_cotangent adds what the slab below sent (its
+ *       gw_hi: this slab's planes 0, 1) and what the slab above sent (its
+ *       gw_lo: planes nz-2, nz-1) into the accumulator (either may be NULL);
+ *   hard_hydro_stage_vjp_cells  per cell, the transpose of the
+ *       conserved-to-primitive map of the accumulator (which it clears)
+ *       plus the combine: gUc (=|+=, accumulate) b G + J^T, and in stage 2
+ *       gU0 = G / 2 when gU0 is not NULL (stage 1: must be NULL); adds the
+ *       pressure's d/dgamma to *g_gamma.
+ * A backward step of a slab: exchange U^n, stage 1 (forward) to U1,
+ * exchange U1; stage 2: faces(U1, G), exchange, cells(U1, G, gU1, 0, gU);
+ * exchange U^n; stage 1: faces(U^n, gU1), exchange, cells(U^n, gU1, gU, 1,
+ * NULL); the *g_gamma of the slabs summed by the caller.  HARD_EUNSUPPORTED
+ * for the second scheme.  Asynchronous. */
+int hard_hydro_set_zghost_adjoint(hard_hydro_t h, void* gw_lo, void* gw_hi);
+int hard_hydro_stage_vjp_faces(hard_hydro_t h, int stage, const void* Uc, const void* G,
+                               double dt, double* g_gamma, void* stream);
+int hard_hydro_add_zghost_cotangent(hard_hydro_t h, const void* from_lo, const void* from_hi,
+                                    void* stream);
+int hard_hydro_stage_vjp_cells(hard_hydro_t h, int stage, const void* Uc, const void* G,
+                               void* gUc, int accumulate, void* gU0, double* g_gamma,
+                               void* stream);
 
 /* Largest signal rate of U over the handle's cells into the device double
  * *rate_dev (the reduction of hard_hydro_cfl_dt without the division).

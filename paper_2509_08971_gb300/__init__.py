@@ -74,6 +74,12 @@ def _declare(lib):
                                                _vp, _vp, _vp]),
         "hard_hydro_set_zghost": (ctypes.c_int, [_vp, _vp, _vp]),
         "hard_hydro_pack_zhalo": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "hard_hydro_set_zghost_adjoint": (ctypes.c_int, [_vp, _vp, _vp]),
+        "hard_hydro_stage_vjp_faces": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp,
+                                                      ctypes.c_double, _vp, _vp]),
+        "hard_hydro_add_zghost_cotangent": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "hard_hydro_stage_vjp_cells": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp,
+                                                      ctypes.c_int, _vp, _vp, _vp]),
         "hard_hydro_local_rate": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "hard_hydro_finalize_dt": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double,
                                                   _vp, _vp, _vp]),
@@ -142,6 +148,23 @@ def hard_hydro_set_zghost(h, ghost_lo, ghost_hi):
 
 def hard_hydro_pack_zhalo(h, U, send_lo, send_hi, stream):
     return lib().hard_hydro_pack_zhalo(h, U, send_lo, send_hi, stream)
+
+
+def hard_hydro_set_zghost_adjoint(h, gw_lo, gw_hi):
+    return lib().hard_hydro_set_zghost_adjoint(h, gw_lo, gw_hi)
+
+
+def hard_hydro_stage_vjp_faces(h, stage, Uc, G, dt, g_gamma, stream):
+    return lib().hard_hydro_stage_vjp_faces(h, int(stage), Uc, G, float(dt), g_gamma, stream)
+
+
+def hard_hydro_add_zghost_cotangent(h, from_lo, from_hi, stream):
+    return lib().hard_hydro_add_zghost_cotangent(h, from_lo, from_hi, stream)
+
+
+def hard_hydro_stage_vjp_cells(h, stage, Uc, G, gUc, accumulate, gU0, g_gamma, stream):
+    return lib().hard_hydro_stage_vjp_cells(h, int(stage), Uc, G, gUc, int(bool(accumulate)),
+                                            gU0, g_gamma, stream)
 
 
 def hard_hydro_local_rate(h, U, rate_dev, stream):

@@ -65,6 +65,12 @@ struct AdjArgs {
     int bc_lo[3], bc_hi[3];
     T gamma, gm1;
     T dxk[3];             // per kernel axis: dx (FP64) or 1/dx (FP32)
+    // z faces of kind BC_HALO (a slab of a decomposed mesh): the ghost planes
+    // of Uc below / above the slab ([5][2][ny][nx], z fastest-but-one) and the
+    // accumulators of the primitive cotangent the faces scatter onto them
+    // ([2][ny][nx] records of GW_STRIDE)
+    const T* zg[2];
+    T* gwg[2];
 };
 
 // Which argument minmod selected: 0 none, 1 a, 2 b (the forward rule).
@@ -272,11 +278,27 @@ __device__ __forceinline__ void face_vjp_one(const AdjArgs<T>& A, const int c3[3
     const int m = c3[KA];
     long long src[4];
     bool flip[4];
+    int side[4];                                       // -1: a cell of this mesh; 0 / 1: ghost plane
     T q[4][NF];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         int c[3] = {c3[0], c3[1], c3[2]};
-        c[KA] = bc_map(m - 2 + s, na, A.bc_lo[KA], A.bc_hi[KA], flip[s]);
+        const int cm = m - 2 + s;
+        side[s] = -1;
+        if (KA == 2 && ((cm < 0 && A.bc_lo[2] == BC_HALO) || (cm >= na && A.bc_hi[2] == BC_HALO))) {
+            // a neighbouring slab's cell: planes -2, -1 / na, na+1 of the ghost buffers
+            side[s] = cm < 0 ? 0 : 1;
+            const int k = cm < 0 ? cm + 2 : cm - na;
+            flip[s] = false;
+            src[s] = ((long long)k * A.n[1] + c[1]) * A.n[0] + c[0];
+            const long long gs = 2ll * A.n[1] * A.n[0];
+            T U[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) U[f] = A.zg[side[s]][f * gs + src[s]];
+            cons_to_prim(U, A.gm1, q[s]);
+            continue;
+        }
+        c[KA] = bc_map(cm, na, A.bc_lo[KA], A.bc_hi[KA], flip[s]);
         src[s] = ((long long)c[2] * A.n[1] + c[1]) * A.n[0] + c[0];
         T U[NF];
 #pragma unroll
@@ -298,7 +320,8 @@ __device__ __forceinline__ void face_vjp_one(const AdjArgs<T>& A, const int c3[3
         if (flip[s]) qb[s][R::n] = -qb[s][R::n];
         const bool any = qb[s][0] != T(0) || qb[s][1] != T(0) || qb[s][2] != T(0) ||
                          qb[s][3] != T(0) || qb[s][4] != T(0);
-        if (any) accumulate_cell(A.gW + src[s] * GW_STRIDE, qb[s]);
+        T* acc = side[s] < 0 ? A.gW : A.gwg[side[s]];
+        if (any) accumulate_cell(acc + src[s] * GW_STRIDE, qb[s]);
     }
 }
 
@@ -406,6 +429,18 @@ __global__ void __launch_bounds__(256) cell_vjp_kernel(const T* Uc, T* gW, const
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         if (s != 0.0) atomicAdd(g_gamma, s);
     }
+}
+
+// A neighbouring slab's ghost-plane accumulator added into this slab's
+// accumulator: `from` ([2][ny][nx] records) lands on planes k0, k0+1.
+template <typename T>
+__global__ void __launch_bounds__(256) add_ghost_cotangent_kernel(T* gW, const T* from,
+                                                                  long long plane_records, int k0) {
+    const long long n = 2 * plane_records * GW_STRIDE;
+    T* dst = gW + (long long)k0 * plane_records * GW_STRIDE;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] += from[i];
 }
 
 }  // namespace hh

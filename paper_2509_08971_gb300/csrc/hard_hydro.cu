@@ -23,6 +23,7 @@ struct hard_hydro_s {
     double ext[3];
     double cell[3];                  // cell widths (ext / n unless set directly)
     const void* zg[2] = {nullptr, nullptr};  // ghost planes of BC_HALO z faces (caller-owned)
+    void* zgw[2] = {nullptr, nullptr};       // their cotangent accumulators (caller-owned)
     int dtype = HARD_F32;
     int kernel = HARD_KERNEL_FUSED;
     int tile = -1;
@@ -160,6 +161,22 @@ int ensure_U1(hard_hydro_s* h) {
     if (rc) return rc;
     h->U1_bytes = need;
     return HARD_OK;
+}
+
+// Adjoint scratch: the primitive cotangent accumulator (8 slots per cell,
+// zero between calls: zeroed here once, cleared by each cell pass) and the
+// cotangent of the intermediate stage.
+int ensure_adj(hard_hydro_s* h) {
+    const size_t gw_bytes = 8 * (size_t)h->mesh.N * elem_size(h);
+    const size_t need = gw_bytes + state_bytes(h);
+    if (h->adj && h->adj_bytes >= need) return HARD_OK;
+    if (h->adj) cudaFree(h->adj);
+    h->adj = nullptr;
+    h->adj_bytes = 0;
+    int rc = dev_alloc(&h->adj, need);
+    if (rc) return rc;
+    h->adj_bytes = need;
+    return cudaMemset(h->adj, 0, gw_bytes) == cudaSuccess ? HARD_OK : HARD_ECUDA;
 }
 
 int ensure_partial(hard_hydro_s* h, long long rows) {
@@ -693,17 +710,9 @@ int hard_hydro_step_backward(hard_hydro_t h, const void* U_in, const void* gU_ou
     // adjoint scratch: the primitive cotangent accumulator (8 slots per cell,
     // zero between calls: zeroed here once, cleared by each cell pass) and
     // the cotangent of the intermediate stage
+    rc = ensure_adj(h);
+    if (rc) return rc;
     const size_t gw_bytes = 8 * (size_t)h->mesh.N * elem_size(h);
-    const size_t need = gw_bytes + state_bytes(h);
-    if (!h->adj || h->adj_bytes < need) {
-        if (h->adj) cudaFree(h->adj);
-        h->adj = nullptr;
-        h->adj_bytes = 0;
-        rc = dev_alloc(&h->adj, need);
-        if (rc) return rc;
-        h->adj_bytes = need;
-        if (cudaMemset(h->adj, 0, gw_bytes) != cudaSuccess) return HARD_ECUDA;
-    }
     void* gW = h->adj;
     void* gU1 = static_cast<unsigned char*>(h->adj) + gw_bytes;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -744,6 +753,91 @@ int hard_hydro_set_zghost(hard_hydro_t h, const void* ghost_lo, const void* ghos
     h->zg[0] = ghost_lo;
     h->zg[1] = ghost_hi;
     return HARD_OK;
+}
+
+int hard_hydro_set_zghost_adjoint(hard_hydro_t h, void* gw_lo, void* gw_hi) {
+    if (!h) return HARD_EINVAL;
+    if ((gw_lo && !aligned16(gw_lo)) || (gw_hi && !aligned16(gw_hi))) return HARD_EINVAL;
+    h->zgw[0] = gw_lo;
+    h->zgw[1] = gw_hi;
+    return HARD_OK;
+}
+
+namespace {
+
+// Checks shared by the two halves of a stage's decomposed VJP.
+int vjp_common(hard_hydro_t h, int stage, const void* Uc, const void* G) {
+    if (!h || (stage != 1 && stage != 2) || !Uc || !G) return HARD_EINVAL;
+    if (!aligned16(Uc) || !aligned16(G)) return HARD_EINVAL;
+    if (weno(h)) return HARD_EUNSUPPORTED;
+    long long faces = h->mesh.dim;        // the face VJP kernel indexes faces in 32 bits
+    for (int k = 0; k < 3; ++k) faces *= (long long)h->mesh.n[k] + (k < h->mesh.dim ? 1 : 0);
+    if (faces >= (1ll << 31)) return HARD_EUNSUPPORTED;
+    int rc = ensure_slots(h);
+    return rc ? rc : ensure_adj(h);
+}
+
+}  // namespace
+
+int hard_hydro_stage_vjp_faces(hard_hydro_t h, int stage, const void* Uc, const void* G,
+                               double dt, double* g_gamma, void* stream) {
+    int rc = vjp_common(h, stage, Uc, G);
+    if (rc) return rc;
+    if (!g_gamma || !(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
+    if (!halo_ready(h)) return HARD_EINVAL;
+    for (int side = 0; side < 2; ++side)
+        if (h->bc[4 + side] == HARD_BC_HALO && !h->zgw[side]) return HARD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    const size_t acc = 2 * (size_t)h->n[0] * h->n[1] * 8 * elem_size(h);
+    cudaError_t e = cudaSuccess;
+    for (int side = 0; side < 2 && e == cudaSuccess; ++side)
+        if (h->bc[4 + side] == HARD_BC_HALO) e = cudaMemsetAsync(h->zgw[side], 0, acc, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    const double b = stage == 1 ? 1.0 : 0.5;
+    hh::AdjointCall a{Uc, G, h->adj, nullptr, false, nullptr, b, 0.0, b * dt, g_gamma, false};
+    a.passes = 1;
+    for (int side = 0; side < 2; ++side) {
+        a.zg[side] = h->zg[side];
+        a.gwg[side] = h->zgw[side];
+    }
+    e = h->dtype == HARD_F64 ? hh::launch_adjoint_stage_f64(h->mesh, a, s)
+                             : hh::launch_adjoint_stage_f32(h->mesh, a, s);
+    return from_cuda(e);
+}
+
+int hard_hydro_add_zghost_cotangent(hard_hydro_t h, const void* from_lo, const void* from_hi,
+                                    void* stream) {
+    if (!h) return HARD_EINVAL;
+    if ((from_lo && !aligned16(from_lo)) || (from_hi && !aligned16(from_hi))) return HARD_EINVAL;
+    if (h->mesh.dim != 3 || h->n[2] < 2) return HARD_EINVAL;
+    int rc = ensure_adj(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    auto add = h->dtype == HARD_F64 ? hh::launch_add_ghost_cotangent_f64
+                                    : hh::launch_add_ghost_cotangent_f32;
+    cudaError_t e = cudaSuccess;
+    if (from_lo) e = add(h->mesh, h->adj, from_lo, 0, s);
+    if (e == cudaSuccess && from_hi) e = add(h->mesh, h->adj, from_hi, h->n[2] - 2, s);
+    return from_cuda(e);
+}
+
+int hard_hydro_stage_vjp_cells(hard_hydro_t h, int stage, const void* Uc, const void* G,
+                               void* gUc, int accumulate, void* gU0, double* g_gamma,
+                               void* stream) {
+    int rc = vjp_common(h, stage, Uc, G);
+    if (rc) return rc;
+    if (!gUc || !aligned16(gUc) || !g_gamma || (gU0 && !aligned16(gU0))) return HARD_EINVAL;
+    if (stage == 1 && gU0) return HARD_EINVAL;       // stage 1 does not depend on U^n separately
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last = s;
+    const double b = stage == 1 ? 1.0 : 0.5, a0 = stage == 1 ? 0.0 : 0.5;
+    hh::AdjointCall a{Uc, G, h->adj, gUc, accumulate != 0, gU0, b, a0, 0.0, g_gamma, true};
+    a.passes = 2;
+    const cudaError_t e = h->dtype == HARD_F64 ? hh::launch_adjoint_stage_f64(h->mesh, a, s)
+                                               : hh::launch_adjoint_stage_f32(h->mesh, a, s);
+    return from_cuda(e);
 }
 
 int hard_hydro_pack_zhalo(hard_hydro_t h, const void* U, void* send_lo, void* send_hi,

@@ -438,6 +438,10 @@ AdjArgs<T> make_adj(const MeshDesc& m, const AdjointCall& c) {
     }
     A.gamma = (T)m.gamma;
     A.gm1 = (T)(m.gamma - 1.0);
+    for (int k = 0; k < 2; ++k) {
+        A.zg[k] = static_cast<const T*>(c.zg[k]);
+        A.gwg[k] = static_cast<T*>(c.gwg[k]);
+    }
     return A;
 }
 
@@ -515,14 +519,19 @@ cudaError_t HH_CAT(launch_adjoint_stage_, HH_SUFFIX)(const MeshDesc& m, const Ad
                                                      cudaStream_t s) {
     const AdjArgs<T> A = make_adj(m, c);
     cudaError_t e = cudaSuccess;
-    if (m.dim == 3) e = run_faces_vjp<3, 0, 1>(A, 3, s);
-    else if (m.dim == 2)
-        e = m.px == 0 ? (m.py == 1 ? run_faces_vjp<2, 0, 1>(A, 2, s) : run_faces_vjp<2, 0, 2>(A, 2, s))
-                      : run_faces_vjp<2, 1, 2>(A, 2, s);
-    else if (m.dim == 1)
-        e = m.px == 0 ? run_faces_vjp<1, 0, 0>(A, 1, s)
-                      : (m.px == 1 ? run_faces_vjp<1, 1, 0>(A, 1, s) : run_faces_vjp<1, 2, 0>(A, 1, s));
-    if (e != cudaSuccess) return e;
+    if (c.passes & 1) {
+        if (m.dim == 3) e = run_faces_vjp<3, 0, 1>(A, 3, s);
+        else if (m.dim == 2)
+            e = m.px == 0 ? (m.py == 1 ? run_faces_vjp<2, 0, 1>(A, 2, s)
+                                       : run_faces_vjp<2, 0, 2>(A, 2, s))
+                          : run_faces_vjp<2, 1, 2>(A, 2, s);
+        else if (m.dim == 1)
+            e = m.px == 0 ? run_faces_vjp<1, 0, 0>(A, 1, s)
+                          : (m.px == 1 ? run_faces_vjp<1, 1, 0>(A, 1, s)
+                                       : run_faces_vjp<1, 2, 0>(A, 1, s));
+        if (e != cudaSuccess) return e;
+    }
+    if (!(c.passes & 2)) return cudaSuccess;
     long long blocks = (m.N + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     return launch_pdl(cell_vjp_kernel<T>, dim3((unsigned)blocks), dim3(256), 0, s,
@@ -530,5 +539,16 @@ cudaError_t HH_CAT(launch_adjoint_stage_, HH_SUFFIX)(const MeshDesc& m, const Ad
                       static_cast<const T*>(c.G), (T)c.b, (T)c.a, static_cast<T*>(c.out_c),
                       c.accumulate, static_cast<T*>(c.out0), m.N, (T)m.gamma, c.g_gamma,
                       c.clear_gW);
+}
+
+cudaError_t HH_CAT(launch_add_ghost_cotangent_, HH_SUFFIX)(const MeshDesc& m, void* gW,
+                                                           const void* from, int k0,
+                                                           cudaStream_t s) {
+    const long long plane = (long long)m.n[0] * m.n[1];
+    long long blocks = (2 * plane * GW_STRIDE + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    add_ghost_cotangent_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(
+        static_cast<T*>(gW), static_cast<const T*>(from), plane, k0);
+    return cudaGetLastError();
 }
 }  // namespace hh

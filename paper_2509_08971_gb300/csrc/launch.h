@@ -126,9 +126,18 @@ struct AdjointCall {
     double b, a, lam;
     double* g_gamma;
     bool clear_gW;
+    int passes = 3;                                // bit 0: the face pass, bit 1: the cell pass
+    const void* zg[2] = {nullptr, nullptr};        // BC_HALO z faces: ghost planes of Uc
+    void* gwg[2] = {nullptr, nullptr};             // and their cotangent accumulators
 };
 cudaError_t launch_adjoint_stage_f32(const MeshDesc& m, const AdjointCall& c, cudaStream_t s);
 cudaError_t launch_adjoint_stage_f64(const MeshDesc& m, const AdjointCall& c, cudaStream_t s);
+// A neighbouring slab's ghost accumulator ([2][ny][nx] records) added into
+// planes k0, k0+1 of the accumulator gW.
+cudaError_t launch_add_ghost_cotangent_f32(const MeshDesc& m, void* gW, const void* from, int k0,
+                                           cudaStream_t s);
+cudaError_t launch_add_ghost_cotangent_f64(const MeshDesc& m, void* gW, const void* from, int k0,
+                                           cudaStream_t s);
 
 // Read-only view of a handle (hard_hydro.cu); false for a NULL handle.
 }  // namespace hh

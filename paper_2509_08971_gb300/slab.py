@@ -23,9 +23,10 @@ oracle to check the partition and exchange logic against a single-rank run.
 """
 from __future__ import annotations
 
-from . import (HARD_BC_HALO, HARD_BC_PERIODIC, HardHydro, check, hard_hydro_finalize_dt,
-               hard_hydro_local_rate, hard_hydro_pack_zhalo, hard_hydro_set_cells,
-               hard_hydro_set_zghost, hard_hydro_stage_ex)
+from . import (HARD_BC_HALO, HARD_BC_PERIODIC, HardHydro, check, hard_hydro_add_zghost_cotangent,
+               hard_hydro_finalize_dt, hard_hydro_local_rate, hard_hydro_pack_zhalo,
+               hard_hydro_set_cells, hard_hydro_set_zghost, hard_hydro_set_zghost_adjoint,
+               hard_hydro_stage_ex, hard_hydro_stage_vjp_cells, hard_hydro_stage_vjp_faces)
 
 
 def partition(nz: int, world: int) -> list[tuple[int, int]]:
@@ -112,6 +113,13 @@ class HaloExchange:
             dist.all_reduce(t, op=dist.ReduceOp.MAX, group=self.group)
         return t
 
+    def sum(self, t):
+        """In place: the sum of t over the ranks."""
+        if self.layout.world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
+        return t
+
 
 class SlabStepper:
     """The time loop of one rank over its slab (see the module docstring).
@@ -149,6 +157,47 @@ class SlabStepper:
             self.x.max(b.rate)
             if step + 1 < nsteps:
                 b.finalize(cfl, t_end)
+
+
+class SlabAdjoint:
+    """The adjoint of a step on one rank's slab (dt held constant): the
+    forward ghost exchange, reversed for the cotangents.
+
+    Each stage's VJP is split around an exchange: the face pass leaves the
+    cotangent of the cells on the neighbours' planes in ``adj_send_lo`` /
+    ``adj_send_hi``, which go to the rank below / above; what they send back
+    arrives in ``adj_recv_lo`` / ``adj_recv_hi`` and is added before the cell
+    pass.  The backend provides, besides the forward stepper's interface,
+    ``set_dt(dt)``, ``vjp_faces(stage, Uc, G)``, ``vjp_add()``,
+    ``vjp_cells(stage, Uc, G, gUc, accumulate, gU0)`` and ``g_gamma`` (a
+    one-element float64 tensor the passes add to)."""
+
+    def __init__(self, backend, exchange: HaloExchange):
+        self.b = backend
+        self.x = exchange
+        self.fwd = SlabStepper(backend, exchange)
+
+    def _reverse(self):
+        b = self.b
+        self.x.run(b.adj_send_lo, b.adj_send_hi, b.adj_recv_lo, b.adj_recv_hi)
+        b.vjp_add()
+
+    def backward_step(self, U, U1, G, gU, gU1, dt):
+        """gU = (dU^{n+1}/dU^n)^T G for this slab's cells (U1, gU1: scratch of
+        U's shape); the slab's d/dgamma is added to the backend's g_gamma
+        (sum it over the ranks with ``exchange.sum``)."""
+        b = self.b
+        b.set_dt(dt)
+        self.fwd.exchange(U)
+        b.stage(1, U, U, U1, False)                    # recompute U1
+        self.fwd.exchange(U1)
+        b.vjp_faces(2, U1, G)
+        self._reverse()
+        b.vjp_cells(2, U1, G, gU1, False, gU)          # gU1 = G/2 + J^T, gU = G/2
+        self.fwd.exchange(U)
+        b.vjp_faces(1, U, gU1)
+        self._reverse()
+        b.vjp_cells(1, U, gU1, gU, True, None)         # gU += gU1 + J^T
 
 
 def slab_handle(shape, layout: SlabLayout, gamma, bc6, dtype=None, kernel=0, tile=-1,
@@ -218,6 +267,46 @@ class CudaSlabBackend:
     def finalize(self, cfl, t_end):
         check(hard_hydro_finalize_dt(self.m.h, self.rate.data_ptr(), cfl, t_end, self.t.data_ptr(),
                                      self.dt.data_ptr(), self._stream()), "hard_hydro_finalize_dt")
+
+    # ---- the adjoint (SlabAdjoint) ----
+
+    def set_dt(self, dt):
+        """Fix the step's dt (host value, also the forward stages' dt)."""
+        if not hasattr(self, "g_gamma"):
+            torch, m = self.torch, self.m
+            _, ny, nx = m.shape
+            dev = self.rate.device
+
+            def acc(on):
+                return torch.zeros((2, ny, nx, 8), dtype=m.dtype, device=dev) if on else None
+
+            lo, hi = self.send_lo is not None, self.send_hi is not None
+            self.adj_send_lo, self.adj_send_hi = acc(lo), acc(hi)
+            self.adj_recv_lo, self.adj_recv_hi = acc(lo), acc(hi)
+            check(hard_hydro_set_zghost_adjoint(m.h, self._p(self.adj_send_lo),
+                                                self._p(self.adj_send_hi)),
+                  "hard_hydro_set_zghost_adjoint")
+            self.g_gamma = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.dt_host = float(dt)
+        self.dt.fill_(self.dt_host)
+
+    def vjp_faces(self, stage, Uc, G):
+        m = self.m
+        check(hard_hydro_stage_vjp_faces(m.h, stage, m._check(Uc), m._check(G), self.dt_host,
+                                         self.g_gamma.data_ptr(), self._stream()),
+              "hard_hydro_stage_vjp_faces")
+
+    def vjp_add(self):
+        check(hard_hydro_add_zghost_cotangent(self.m.h, self._p(self.adj_recv_lo),
+                                              self._p(self.adj_recv_hi), self._stream()),
+              "hard_hydro_add_zghost_cotangent")
+
+    def vjp_cells(self, stage, Uc, G, gUc, accumulate, gU0):
+        m = self.m
+        check(hard_hydro_stage_vjp_cells(m.h, stage, m._check(Uc), m._check(G), m._check(gUc),
+                                         accumulate, None if gU0 is None else m._check(gU0),
+                                         self.g_gamma.data_ptr(), self._stream()),
+              "hard_hydro_stage_vjp_cells")
 
 
 # ---- independent problems (the batched configuration) ----

@@ -185,3 +185,139 @@ def test_lpt_partition_of_independent_problems():
         assert max(loads) <= sum(loads) / world + max(cost)
         assert parts == slab.lpt_partition(cost, world)
     assert slab.lpt_partition([5, 1, 4, 2, 3], 2) == [[0, 1, 3], [2, 4]]
+
+
+# ---- the adjoint of a decomposed step (the ghost exchange reversed) ----
+
+class TorchAdjointBackend:
+    """One rank's stages and stage VJPs by autograd of the PyTorch oracle
+    transcription on the rank's slab extended by its ghost planes: the VJP
+    with respect to the ghost planes is the cotangent the neighbours own,
+    sent back to them by the exchange (conserved variables here; the CUDA
+    backend sends primitive cotangents before its cell pass)."""
+
+    def __init__(self, layout, shape, bc6, gamma):
+        from oracle import oracle_torch as ot
+        self.ot = ot
+        nz, ny, nx = shape
+        self.L = layout
+        self.gamma = gamma
+        self.dxyz = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+        lo, hi = layout.lo is not None, layout.hi is not None
+
+        def buf(on):
+            return torch.zeros((5, 2, ny, nx), dtype=torch.float64) if on else None
+
+        self.send_lo, self.send_hi = buf(lo), buf(hi)
+        self.ghost_lo, self.ghost_hi = buf(lo), buf(hi)
+        self.adj_send_lo, self.adj_send_hi = buf(lo), buf(hi)
+        self.adj_recv_lo, self.adj_recv_hi = buf(lo), buf(hi)
+        self.g_gamma = torch.zeros(1, dtype=torch.float64)
+        bc = list(bc6)
+        bc[4] = oracle.BC_OUTFLOW if lo else layout.bc_z[0]   # the extension's own walls only
+        bc[5] = oracle.BC_OUTFLOW if hi else layout.bc_z[1]   # touch the dropped ghost cells
+        self.bc = bc
+
+    def pack(self, U):
+        if self.send_lo is not None:
+            self.send_lo.copy_(U[:, :2])
+        if self.send_hi is not None:
+            self.send_hi.copy_(U[:, -2:])
+
+    def _L(self, V, gl, gh, gam):
+        parts = ([gl] if gl is not None else []) + [V] + ([gh] if gh is not None else [])
+        k0 = 2 if gl is not None else 0
+        return self.ot.rhs(torch.cat(parts, dim=1), gam, self.dxyz, self.bc)[:, k0:k0 + V.shape[1]]
+
+    def set_dt(self, dt):
+        self.dt = float(dt)
+
+    def stage(self, stage, U0, Ucur, out, with_rate):
+        with torch.no_grad():
+            Ls = self._L(Ucur, self.ghost_lo, self.ghost_hi, self.gamma)
+            out.copy_(Ucur + self.dt * Ls if stage == 1 else 0.5 * U0 + 0.5 * (Ucur + self.dt * Ls))
+
+    def vjp_faces(self, stage, Uc, G):
+        b = 1.0 if stage == 1 else 0.5
+        V = Uc.clone().requires_grad_(True)
+        gl = None if self.ghost_lo is None else self.ghost_lo.clone().requires_grad_(True)
+        gh = None if self.ghost_hi is None else self.ghost_hi.clone().requires_grad_(True)
+        gam = torch.tensor(self.gamma, dtype=torch.float64, requires_grad=True)
+        out = b * (V + self.dt * self._L(V, gl, gh, gam))
+        ins = [V, gam] + [t for t in (gl, gh) if t is not None]
+        grads = torch.autograd.grad(out, ins, grad_outputs=G)
+        self.pending = grads[0]
+        self.g_gamma += grads[1]
+        k = 2
+        if gl is not None:
+            self.adj_send_lo.copy_(grads[k])
+            k += 1
+        if gh is not None:
+            self.adj_send_hi.copy_(grads[k])
+
+    def vjp_add(self):
+        if self.adj_recv_lo is not None:
+            self.pending[:, :2] += self.adj_recv_lo
+        if self.adj_recv_hi is not None:
+            self.pending[:, -2:] += self.adj_recv_hi
+
+    def vjp_cells(self, stage, Uc, G, gUc, accumulate, gU0):
+        if accumulate:
+            gUc += self.pending
+        else:
+            gUc.copy_(self.pending)
+        if gU0 is not None:
+            gU0.copy_(0.5 * G)
+
+
+def _adj_inputs(shape, bc6, seed):
+    U0 = H.smooth_3d(0, seed=seed, gamma=GAMMA, shape=shape) if bc6[4] == 0 else \
+        H.blast_3d(shape[0], seed=seed, gamma=GAMMA, p_amb=0.1)
+    G = np.random.default_rng(seed + 100).standard_normal((5,) + tuple(shape))
+    dt = 0.3 / oracle.Grid(shape, GAMMA, bc6).max_rate(U0)
+    return U0, G, dt
+
+
+def _adj_rank_main(rank, world, port, shape, bc6, seed, outdir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        L = slab.SlabLayout(shape[0], rank, world, bc_z=(bc6[4], bc6[5]))
+        U0, G0, dt = _adj_inputs(shape, bc6, seed)
+        U = torch.from_numpy(np.ascontiguousarray(U0[:, L.z0:L.z1]))
+        G = torch.from_numpy(np.ascontiguousarray(G0[:, L.z0:L.z1]))
+        gU, U1, gU1 = torch.empty_like(U), torch.empty_like(U), torch.empty_like(U)
+        backend = TorchAdjointBackend(L, shape, bc6, GAMMA)
+        x = slab.HaloExchange(L)
+        slab.SlabAdjoint(backend, x).backward_step(U, U1, G, gU, gU1, dt)
+        x.sum(backend.g_gamma)
+        np.save(os.path.join(outdir, f"g{rank}.npy"), gU.numpy())
+        np.save(os.path.join(outdir, f"gg{rank}.npy"), backend.g_gamma.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,shape,bc6", [
+    (2, (12, 6, 8), [0, 0, 0, 0, 0, 0]),              # periodic: the same peer above and below
+    (3, (13, 13, 13), [2, 2, 1, 1, 2, 2]),            # the blast, reflecting z ends, uneven slabs
+])
+def test_decomposed_adjoint_equals_whole_mesh_autograd(tmp_path, world, shape, bc6):
+    from oracle import oracle_torch as ot
+    seed = 6
+    mp.spawn(_adj_rank_main, args=(world, _free_port(), shape, bc6, seed, str(tmp_path)),
+             nprocs=world, join=True)
+    got = np.concatenate([np.load(tmp_path / f"g{r}.npy") for r in range(world)], axis=1)
+    ggs = [float(np.load(tmp_path / f"gg{r}.npy")[0]) for r in range(world)]
+    U0, G0, dt = _adj_inputs(shape, bc6, seed)
+    U = torch.tensor(U0, requires_grad=True)
+    gam = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+    nz, ny, nx = shape
+    out = ot.step(U, gam, dt, (1.0 / nx, 1.0 / ny, 1.0 / nz), bc6)
+    ref, ref_gg = torch.autograd.grad(out, [U, gam], grad_outputs=torch.tensor(G0))
+    ref = ref.numpy()
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * scale
+    assert all(abs(g - float(ref_gg)) <= 1e-10 * abs(float(ref_gg)) for g in ggs)
+    assert np.max(np.abs(got - ref)) < np.max(np.abs(ref))   # not trivially zero
