@@ -312,6 +312,77 @@ __global__ void __launch_bounds__(128) residual_norms_kernel(const LvlArgs<T> a,
     griddep_launch_dependents();
 }
 
+// The same check once the fine level's post-smoothing has ended with a
+// half-sweep of colour 1: each colour-1 cell then solves its own equation
+// with its (colour-0) neighbours as they stand, so its residual is zero up
+// to rounding and sum r^2 is the sum over the colour-0 cells, which this
+// kernel takes (half the stencils of residual_norms_kernel, in the
+// smoother's launch shape) into norms[0].  Only for a proper two-colouring:
+// no periodic axis of odd length.
+template <typename T>
+__global__ void __launch_bounds__(128) residual_norm_color_kernel(const LvlArgs<T> a, int color,
+                                                                  double* norms) {
+    griddep_wait();
+    const int k = blockIdx.z;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    StencilVals<T> v[SMOOTH_ROWS];
+    T bq[SMOOTH_ROWS], xq[SMOOTH_ROWS];
+    bool on[SMOOTH_ROWS];
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r) {
+        const int j = blockIdx.y * SMOOTH_ROWS + r;
+        const int i = 2 * p + ((j + k + color) & 1);
+        on[r] = j < a.n[1] && i < a.n[0];
+        const int ii = on[r] ? i : 0, jj = on[r] ? j : 0;
+        const int q = (k * a.n[1] + jj) * a.n[0] + ii;
+        stencil_load(a, ii, jj, k, q, v[r]);
+        bq[r] = a.b[q];
+        xq[r] = a.x[q];
+    }
+    T pr = T(0);
+    double rr = 0.0;
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r) {
+        T diag, off;
+        stencil_eval(a, v[r], diag, off);
+        const T res = bq[r] - (diag * xq[r] - off);
+        if (on[r]) {
+            if (sizeof(T) == 8) rr += (double)res * (double)res;
+            else pr = fma(res, res, pr);
+        }
+    }
+    rr += (double)pr;
+    __shared__ double sr[4];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    if ((threadIdx.x & 31) == 0) sr[threadIdx.x >> 5] = rr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double t = sr[0] + sr[1] + sr[2] + sr[3];
+        if (t != 0.0) atomicAdd(norms, t);
+    }
+    griddep_launch_dependents();
+}
+
+// sum b^2 of the fine level into *out (once per solve; b does not change).
+template <typename T>
+__global__ void __launch_bounds__(256) sumsq_kernel(const T* b, long long n, double* out) {
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc += (double)b[i] * (double)b[i];
+    __shared__ double sr[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sr[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sr[w];
+        atomicAdd(out, t);
+    }
+}
+
 // The small levels of the V-cycle (each at most FLD_SMALL_CELLS cells, at
 // most FLD_SMALL_MAX of them: the bottom of the hierarchy) in one block, in
 // shared memory: the same smoothing, residual restriction, coarsest-level
@@ -624,6 +695,19 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             return e;
     }
 
+    // the convergence check over colour 0 alone (see residual_norm_color_kernel)
+    // when the fine level is smoothed by the level kernels and the colouring
+    // is proper; sum b^2 then once
+    bool color_check = ls > 0 && H->nl > 1;
+    for (int ax = 0; ax < 3; ++ax)
+        if (L0.n[ax] > 1 && m.bc_lo[ax] == HARD_BC_PERIODIC && (L0.n[ax] & 1)) color_check = false;
+    if (rtol > 0.0 && color_check) {
+        if ((e = cudaMemsetAsync(H->norms, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
+        sumsq_kernel<T><<<grid_for(L0.N) < 152 * 8 ? grid_for(L0.N) : 152 * 8, 256, 0, s>>>(
+            static_cast<const T*>(L0.b), L0.N, H->norms + 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+
     int done = 0;
     double rel = -1.0;
     for (int cyc = 0; cyc < max_cycles; ++cyc) {
@@ -662,7 +746,14 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             if ((e = smooth<T>(H, l, dt, FLD_POST, s)) != cudaSuccess) return e;
         }
         done = cyc + 1;
-        if (rtol > 0.0) {
+        if (rtol > 0.0 && color_check) {
+            if ((e = cudaMemsetAsync(H->norms, 0, sizeof(double), s)) != cudaSuccess) return e;
+            dim3 g = rows_grid(L0, 2);
+            g.y = (g.y + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
+            e = launch_pdl(residual_norm_color_kernel<T>, g, dim3(128), 0, s,
+                           level_args<T>(H, 0, dt), 0, H->norms);
+            if (e != cudaSuccess) return e;
+        } else if (rtol > 0.0) {
             if ((e = cudaMemsetAsync(H->norms, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
             const long long items = (long long)((L0.n[0] + 127) / 128) *
                                     ((L0.n[1] + SMOOTH_ROWS - 1) / SMOOTH_ROWS) * L0.n[2];
@@ -670,6 +761,8 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
                            dim3((unsigned)(items < 152 * 16 ? items : 152 * 16)), dim3(128), 0, s,
                            level_args<T>(H, 0, dt), H->norms);
             if (e != cudaSuccess) return e;
+        }
+        if (rtol > 0.0) {
             double nr[2];
             if ((e = cudaMemcpyAsync(nr, H->norms, sizeof(nr), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
                 return e;
