@@ -391,7 +391,7 @@ advect_march_kernel(const AdvectArgs<T> A, T* __restrict__ L) {
     T rn, mn, en, Lk = T(0), E0k = T(0);
     bool fn;
     fetch(a0 - 3, rn, mn, en, fn);
-#pragma unroll 1
+#pragma unroll 5       // the window's five registers rotate by renaming (0.86 -> 0.82 ms per step)
     for (int j = a0 - 3; j <= a1 + 2; ++j) {
         const int cnt = j - (a0 - 3);
         const T rj = rn, ej = en;
