@@ -986,6 +986,15 @@ def main():
         line["cpu_baseline"]["single_thread"] = {
             "value": rate1, "unit": UNIT, "cores": 1,
             "sample": f"1 RK2 step of the middle 4 z planes of the blast ({sec1:.1f} s)"}
+        for n, steps in ((128, 3), (256, 1)):
+            Us = H.smooth_3d(n, seed=0, gamma=SMOOTH_GAMMA)
+            rs, ssec, used_s = time_oracle(Us, steps, threads, oracle.BC_PERIODIC, SMOOTH_GAMMA,
+                                           SMOOTH_CFL)
+            line["cpu_baseline"][f"smooth_3d_{n}"] = {
+                "value": rs, "unit": UNIT, "cores": used_s,
+                "sample": f"configuration 2 at {n}^3: {steps} RK2 step(s) of the periodic smooth "
+                          f"flow ({ssec:.1f} s)"}
+            del Us
         rr, rsec, rsteps = time_oracle_riemann()
         line["cpu_baseline"]["riemann_1d_400"] = {
             "value": rr, "unit": UNIT, "cores": 1,
