@@ -765,14 +765,18 @@ int hard_hydro_set_zghost_adjoint(hard_hydro_t h, void* gw_lo, void* gw_hi) {
 
 namespace {
 
-// Checks shared by the two halves of a stage's decomposed VJP.
-int vjp_common(hard_hydro_t h, int stage, const void* Uc, const void* G) {
+// Argument checks shared by the two halves of a stage's decomposed VJP (no
+// device work).
+int vjp_args(hard_hydro_t h, int stage, const void* Uc, const void* G) {
     if (!h || (stage != 1 && stage != 2) || !Uc || !G) return HARD_EINVAL;
     if (!aligned16(Uc) || !aligned16(G)) return HARD_EINVAL;
     if (weno(h)) return HARD_EUNSUPPORTED;
     long long faces = h->mesh.dim;        // the face VJP kernel indexes faces in 32 bits
     for (int k = 0; k < 3; ++k) faces *= (long long)h->mesh.n[k] + (k < h->mesh.dim ? 1 : 0);
-    if (faces >= (1ll << 31)) return HARD_EUNSUPPORTED;
+    return faces >= (1ll << 31) ? HARD_EUNSUPPORTED : HARD_OK;
+}
+
+int vjp_scratch(hard_hydro_t h) {
     int rc = ensure_slots(h);
     return rc ? rc : ensure_adj(h);
 }
@@ -781,12 +785,13 @@ int vjp_common(hard_hydro_t h, int stage, const void* Uc, const void* G) {
 
 int hard_hydro_stage_vjp_faces(hard_hydro_t h, int stage, const void* Uc, const void* G,
                                double dt, double* g_gamma, void* stream) {
-    int rc = vjp_common(h, stage, Uc, G);
+    int rc = vjp_args(h, stage, Uc, G);
     if (rc) return rc;
     if (!g_gamma || !(dt > 0.0) || !std::isfinite(dt)) return HARD_EINVAL;
     if (!halo_ready(h)) return HARD_EINVAL;
     for (int side = 0; side < 2; ++side)
         if (h->bc[4 + side] == HARD_BC_HALO && !h->zgw[side]) return HARD_EINVAL;
+    if ((rc = vjp_scratch(h)) != HARD_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->last = s;
     const size_t acc = 2 * (size_t)h->n[0] * h->n[1] * 8 * elem_size(h);
@@ -811,7 +816,7 @@ int hard_hydro_add_zghost_cotangent(hard_hydro_t h, const void* from_lo, const v
     if (!h) return HARD_EINVAL;
     if ((from_lo && !aligned16(from_lo)) || (from_hi && !aligned16(from_hi))) return HARD_EINVAL;
     if (h->mesh.dim != 3 || h->n[2] < 2) return HARD_EINVAL;
-    int rc = ensure_adj(h);
+    int rc = vjp_scratch(h);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->last = s;
@@ -826,10 +831,11 @@ int hard_hydro_add_zghost_cotangent(hard_hydro_t h, const void* from_lo, const v
 int hard_hydro_stage_vjp_cells(hard_hydro_t h, int stage, const void* Uc, const void* G,
                                void* gUc, int accumulate, void* gU0, double* g_gamma,
                                void* stream) {
-    int rc = vjp_common(h, stage, Uc, G);
+    int rc = vjp_args(h, stage, Uc, G);
     if (rc) return rc;
     if (!gUc || !aligned16(gUc) || !g_gamma || (gU0 && !aligned16(gU0))) return HARD_EINVAL;
     if (stage == 1 && gU0) return HARD_EINVAL;       // stage 1 does not depend on U^n separately
+    if ((rc = vjp_scratch(h)) != HARD_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     h->last = s;
     const double b = stage == 1 ? 1.0 : 0.5, a0 = stage == 1 ? 0.0 : 0.5;

@@ -67,6 +67,15 @@ def test_host_only_calls_without_gpu(libpath):
     assert hh.hard_hydro_fld_step(h, 16, 32, 1.0, 1.0, 1.0, 1e-6, 0, None)[0] == hh.HARD_EINVAL
     assert hh.hard_hydro_advect_E(h, None, None, 1.0, None) == hh.HARD_EINVAL
     assert hh.hard_hydro_advect_E(h, 16, 32, 0.0, None) == hh.HARD_EINVAL
+    # the split adjoint of a slab checks its arguments before touching the device
+    assert hh.hard_hydro_stage_vjp_faces(h, 3, 16, 32, 1e-3, 64, None) == hh.HARD_EINVAL
+    assert hh.hard_hydro_stage_vjp_faces(h, 1, None, 32, 1e-3, 64, None) == hh.HARD_EINVAL
+    assert hh.hard_hydro_stage_vjp_faces(h, 1, 16, 32, 0.0, 64, None) == hh.HARD_EINVAL
+    assert hh.hard_hydro_stage_vjp_cells(h, 1, 16, 32, 48, 0, 64, 80, None) == hh.HARD_EINVAL
+    assert hh.hard_hydro_stage_vjp_cells(h, 2, 16, 32, None, 0, None, 80, None) == hh.HARD_EINVAL
+    assert hh.hard_hydro_add_zghost_cotangent(h, None, None, None) == hh.HARD_EINVAL  # 2D mesh
+    assert hh.hard_hydro_set_zghost_adjoint(h, 17, None) == hh.HARD_EINVAL           # unaligned
+    assert hh.hard_hydro_set_zghost_adjoint(h, None, None) == hh.HARD_OK
     h2 = hh.hard_hydro_create(16, 2, 1, 1.4, 0)
     assert hh.hard_hydro_advect_E(h2, 16, 32, 1.0, None) == hh.HARD_EINVAL    # 2 cells along y
     assert hh.hard_hydro_set_scheme(h2, hh.HARD_SCHEME_WENO5Z_HLL) == hh.HARD_EINVAL
