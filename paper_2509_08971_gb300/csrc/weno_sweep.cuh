@@ -151,9 +151,11 @@ weno_x_kernel(const StageArgs<T> A, T* __restrict__ L) {
 // difference to L; LAST: then the combine.  Every global load is issued one
 // step before its value is used (the next cell's state; the flux difference,
 // state and U^n of the cell that completes at the next step), so a step's
-// arithmetic covers the memory latency.
+// arithmetic covers the memory latency.  At least four blocks per SM (at
+// most 128 registers a thread): 16 warps hide more latency than the 11 the
+// unbounded 138-168 registers allow.
 #ifndef HH_WENO_MINB
-#define HH_WENO_MINB 1
+#define HH_WENO_MINB 4
 #endif
 template <typename T, int AX, int PA, bool LAST>
 __global__ void __launch_bounds__(SWEEP_THREADS, HH_WENO_MINB)
