@@ -106,10 +106,14 @@ int hard_hydro_tile_info(hard_hydro_t h, int tile, int out4[4]);
 /* Choose the scheme of every later stage, step and advance call:
  * HARD_SCHEME_PLM_HLLC (default) or HARD_SCHEME_WENO5Z_HLL.  The WENO5-Z
  * scheme needs at least three cells along every active axis (else
- * HARD_EINVAL), runs one kernel variant (the kernel and tile choice of
- * hard_hydro_set_kernel apply to the default scheme only), and has no
- * adjoint: hard_hydro_step_backward returns HARD_EUNSUPPORTED for it.  The
- * CFL rate and the totals are the same for both schemes. */
+ * HARD_EINVAL), ignores the kernel and tile choice of hard_hydro_set_kernel
+ * (which apply to the default scheme only), and has no adjoint:
+ * hard_hydro_step_backward returns HARD_EUNSUPPORTED for it.  On a 3D mesh
+ * a stage runs as three directional sweeps that keep the flux difference in
+ * a state-sized buffer the handle allocates with its other scratch (the
+ * results equal the fused kernel's, which 1D and 2D meshes and
+ * hard_hydro_step_noalloc use).  The CFL rate and the totals are the same
+ * for both schemes. */
 int hard_hydro_set_scheme(hard_hydro_t h, int scheme);
 
 /* One Runge-Kutta stage (Sec. 2.2.2 flux difference, Heun tableau):
@@ -336,7 +340,8 @@ int hard_hydro_rad_exchange(hard_hydro_t h, void* U, void* Er, double dt, const 
  * and boundary kinds (E mirrors without a sign change at a reflecting wall).
  * U: the handle's state (read); Er: the radiation energy density
  * [nz][ny][nx], updated in place.  Device buffers of the handle's element
- * type, 16-byte aligned, caller-owned; the intermediate stage uses the
+ * type, 16-byte aligned, caller-owned; the intermediate stage (and, on a 3D
+ * mesh, the flux difference passed between the directional sweeps) uses the
  * handle's scratch.  Every active axis needs at least three cells
  * (HARD_EINVAL otherwise).  The caller chooses dt (a CFL limit is
  * max |v_d| dt / dx_d <= 1 summed over the axes).  Asynchronous. */
