@@ -654,6 +654,16 @@ def main():
     kname = "stage_ws_kernel<32,%d,*> z-chunk %d (mean of stage 1 and stage 2)" % (
         tuned["info"][1], tuned["info"][2])
     roofline = stage_roofline(m32, U, hbm, peak_kind, kname)
+    # the same bytes over half the whole step's time: a floor for the stage
+    # launches as they run in the step (stage 2 with its rate and totals
+    # epilogue, the finalize launch and the gaps between launches charged to
+    # them); launch_ms above times the stage launches alone
+    step_half = ms / args.steps / 2
+    roofline["in_step"] = {"ms_per_launch": step_half,
+                           "achieved": roofline["algorithmic_bytes_per_launch"] / (step_half * 1e-3)
+                           / 1e9,
+                           "frac": roofline["algorithmic_bytes_per_launch"] / (step_half * 1e-3)
+                           / 1e9 / hbm}
     issue = issue_roofline(cells, roofline["launch_ms"], clocks.get("sm_mhz"))
     if args.headline_only:
         if rank == 0:
