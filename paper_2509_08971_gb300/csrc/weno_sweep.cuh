@@ -219,7 +219,7 @@ weno_march_kernel(const StageArgs<T> A, T* __restrict__ L) {
     fetch(a0 - 3, Un, fn);
 #pragma unroll
     for (int f = 0; f < NF; ++f) Lk[f] = Uk[f] = U0k[f] = T(0);
-#pragma unroll 2       // by 2 (17.5 -> 17.7 G); by the window's 5 it spills the cap
+#pragma unroll 2       // by two: 17.5 -> 17.7 G; by five: 16.6 G under the register cap
     for (int j = a0 - 3; j <= a1 + 2; ++j) {
         const int cnt = j - (a0 - 3);
         T U[NF];
