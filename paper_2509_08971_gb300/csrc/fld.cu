@@ -187,7 +187,12 @@ __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int col
 // together, then evaluated, so their loads overlap); otherwise the factors
 // h0, h1, h2 are read at run time.  The children are summed in the same order
 // (z, then y, then x) either way.
-template <typename T, bool H2>
+// RED: only the colour-0 children are evaluated.  After a half-sweep of
+// colour 1 each colour-1 cell solves its own equation, so its residual is
+// zero up to rounding (see residual_norm_color_kernel) and it adds nothing to
+// the mean; used when the pre-smoothing ends with colour 1 and no periodic
+// axis of the level has odd length.
+template <typename T, bool H2, bool RED = false>
 __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T> a, T* bc, T* xc,
                                                                 int nc0, int nc1, int h0, int h1,
                                                                 int h2) {
@@ -201,21 +206,24 @@ __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T>
         // per child plane: the four children's loads, then their residuals
 #pragma unroll
         for (int cz = 0; cz < 2; ++cz) {
-            StencilVals<T> v[4];
-            T bq[4], xq[4];
+            // child c = cx + 2 cy of the plane; colour 0: cx + cy + cz even
+            constexpr int NC = RED ? 2 : 4;
+            StencilVals<T> v[NC];
+            T bq[NC], xq[NC];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int n = 0; n < NC; ++n) {
+                const int c = RED ? (cz == 0 ? 3 * n : 1 + n) : n;
                 const int i = 2 * I + (c & 1), j = 2 * J + (c >> 1), k = 2 * K + cz;
                 const int q = (k * a.n[1] + j) * a.n[0] + i;
-                stencil_load(a, i, j, k, q, v[c]);
-                bq[c] = a.b[q];
-                xq[c] = a.x[q];
+                stencil_load(a, i, j, k, q, v[n]);
+                bq[n] = a.b[q];
+                xq[n] = a.x[q];
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int n = 0; n < NC; ++n) {
                 T diag, off;
-                stencil_eval(a, v[c], diag, off);
-                sum += bq[c] - (diag * xq[c] - off);
+                stencil_eval(a, v[n], diag, off);
+                sum += bq[n] - (diag * xq[n] - off);
             }
         }
     } else {
@@ -718,7 +726,12 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             const FldLevel& F = H->L[l];
             const FldLevel& C = H->L[l + 1];
             const bool h2 = F.coarsened[0] && F.coarsened[1] && F.coarsened[2];
-            auto rr = h2 ? residual_restrict_kernel<T, true> : residual_restrict_kernel<T, false>;
+            bool proper = true;                      // red-black is a two-colouring of level l
+            for (int ax = 0; ax < 3; ++ax)
+                if (F.n[ax] > 1 && m.bc_lo[ax] == HARD_BC_PERIODIC && (F.n[ax] & 1)) proper = false;
+            auto rr = h2 ? (proper ? residual_restrict_kernel<T, true, true>
+                                   : residual_restrict_kernel<T, true, false>)
+                         : residual_restrict_kernel<T, false>;
             e = launch_pdl(rr, rows_grid(C, 1), dim3(128), 0, s, level_args<T>(H, l, dt),
                            static_cast<T*>(C.b), static_cast<T*>(C.x), C.n[0], C.n[1],
                            F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1,
