@@ -856,9 +856,10 @@ def main():
     fld_ms = e0.elapsed_time(e1)
     # bytes per V-cycle: per level, two pre- and two post-smoothing red-black
     # sweeps (24 B/cell each: x read twice, b and D, x written), the fused
-    # residual-restriction (13), prolongation (12): 121 B/cell, x 8/7 over
-    # the levels
-    fld_bytes = 121.0 * 8.0 / 7.0 * cells2 * cyc_f
+    # residual-restriction (11: x and D of every cell, b of the colour-0
+    # cells it evaluates, the coarse b and x), prolongation (12): 119 B/cell,
+    # x 8/7 over the levels (the per-cycle convergence check not counted)
+    fld_bytes = 119.0 * 8.0 / 7.0 * cells2 * cyc_f
     fld_achieved = fld_bytes / (fld_ms * 1e-3) / 1e9
     fld = {"workload": f"{n2}^3 periodic implicit flux-limited diffusion step, c = kappa = 1, "
                        "rho, E ~ 1 + 0.5 U[0,1) (seeded), diffusion number ~100, "
