@@ -207,11 +207,14 @@ cudaError_t run_stage_tma(const MeshDesc& m, const TileDesc& td, const StageCall
 #ifndef HH_WS_NCW8
 #define HH_WS_NCW8 2
 #endif
+#ifndef HH_WS_NCW16
+#define HH_WS_NCW16 3
+#endif
 #ifndef HH_WS_RPW8
 #define HH_WS_RPW8 1
 #endif
 template <int TY> struct WsConf {
-    static constexpr int NCW = TY >= 8 ? HH_WS_NCW8 : 1;
+    static constexpr int NCW = TY >= 16 ? HH_WS_NCW16 : (TY >= 8 ? HH_WS_NCW8 : 1);
     static constexpr int RPW = TY == 8 ? HH_WS_RPW8 : 1;
 };
 
