@@ -57,7 +57,9 @@ L2_BYTES = 129 * 2 ** 20
 STAGE_KERNEL_SOURCES = ("devattr.h", "hydro_math.cuh", "kernels_impl.cuh", "launch.h",
                         "stage_f32.cu", "stage_kernel.cuh", "stage_tma.cuh", "stage_ws.cuh",
                         "tma.cuh", "vec2.cuh")
-STAGE_PROFILE = os.path.join("profiles", "stage_ws_kernel_blast3d_256.md")
+# the committed ncu summaries of the stage kernel, by tile height
+STAGE_PROFILES = {8: os.path.join("profiles", "stage_ws_kernel_blast3d_256.md"),
+                  16: os.path.join("profiles", "stage_ws_kernel_ty16_blast3d_256.md")}
 
 
 def kernel_sources_digest():
@@ -72,13 +74,15 @@ def kernel_sources_digest():
     return h.hexdigest()
 
 
-def profiled(key):
-    """A figure of the committed ncu summary of the stage kernel
-    ("traffic-bytes-per-cell-stage": DRAM bytes read + written per cell, mean
-    of the two stage launches; "instructions-per-cell-stage": warp-instruction
-    issue slots x 32 per cell, mean of the two), or None when the kernel's
-    sources changed since the capture."""
-    path = os.path.join(ROOT, STAGE_PROFILE)
+def profiled(key, ty=8):
+    """A figure of the committed ncu summary of the stage kernel with tiles
+    of height ty ("traffic-bytes-per-cell-stage": DRAM bytes read + written
+    per cell, mean of the two stage launches; "instructions-per-cell-stage":
+    warp-instruction issue slots x 32 per cell, mean of the two), or None
+    when there is none or the kernel's sources changed since the capture."""
+    if ty not in STAGE_PROFILES:
+        return None
+    path = os.path.join(ROOT, STAGE_PROFILES[ty])
     try:
         rec = {}
         with open(path) as fh:
@@ -93,23 +97,23 @@ def profiled(key):
         return None
 
 
-def profiled_traffic(cells):
+def profiled_traffic(cells, ty=8):
     """DRAM bytes per stage launch on `cells` cells: the profiled per-cell
     figure (captured on a 256^3 case of the same kernel) times the cells; the
     kernel streams each plane once, so its traffic grows with the cells."""
-    b = profiled("traffic-bytes-per-cell-stage")
+    b = profiled("traffic-bytes-per-cell-stage", ty)
     return None if b is None else b * cells
 
 
 SCHEDULERS = 152 * 4       # GB300: 152 SMs, four warp schedulers each
 
 
-def issue_roofline(cells, stage_ms, sm_mhz):
+def issue_roofline(cells, stage_ms, sm_mhz, ty=8):
     """The stage kernel against the SMs' instruction issue rate: warp
     instructions per second (profiled thread instructions per cell-stage x
     cells / 32 / launch time) over one warp instruction per scheduler per
     clock at the median SM clock sampled during the timed steps."""
-    ipc = profiled("instructions-per-cell-stage")
+    ipc = profiled("instructions-per-cell-stage", ty)
     if ipc is None or not sm_mhz:
         return None
     achieved = ipc * cells / 32.0 / (stage_ms * 1e-3)
@@ -404,7 +408,7 @@ def precision_report():
     print(json.dumps(rep), flush=True)
 
 
-def stage_roofline(m, U, hbm, peak_kind, kernel_name, reps=20):
+def stage_roofline(m, U, hbm, peak_kind, kernel_name, reps=20, ty=8):
     """Mean CUDA-event time of the stage-1 and stage-2 launches of handle m on
     state U (inputs larger than L2), against the HBM roofline at the
     algorithmic 50 B per FP32 cell-stage."""
@@ -428,7 +432,7 @@ def stage_roofline(m, U, hbm, peak_kind, kernel_name, reps=20):
     alg = BYTES_PER_CELL_STAGE[4] * cells
     achieved = alg / (stage_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": profiled_traffic(cells), "peak_kind": peak_kind,
+            "frac": achieved / hbm, "traffic": profiled_traffic(cells, ty), "peak_kind": peak_kind,
             "kernel": kernel_name, "algorithmic_bytes_per_launch": alg, "launch_ms": stage_ms}
 
 
@@ -568,6 +572,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline workload only (profiling runs)")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="headline stage tile (default: the autotuner's choice)")
     ap.add_argument("--n", type=int, default=N_SIDE,
                     help="mesh side of the headline workload (profiling runs only)")
     ap.add_argument("--shard", action="store_true",
@@ -623,7 +629,11 @@ def main():
     m32 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_REFLECT, dtype=torch.float32,
                        kernel=hh.HARD_KERNEL_FUSED)
     U = U0.clone()
-    tuned = autotune.tune(m32, U, kernel=hh.HARD_KERNEL_FUSED, reps=5)   # outside the timed region
+    if args.tile >= 0:                                   # a fixed tile (profiling runs)
+        m32.set_kernel(hh.HARD_KERNEL_FUSED, args.tile)
+        tuned = {"tile": args.tile, "info": list(m32.tile_info(args.tile)), "ms": {}}
+    else:
+        tuned = autotune.tune(m32, U, kernel=hh.HARD_KERNEL_FUSED, reps=5)   # outside the timed region
     tot_log = torch.zeros((max(args.steps, args.warmup, 3), 5), dtype=torch.float64, device=dev)
     advance(m32, U, max(args.warmup, 3), tot_log)
     U.copy_(U0)                                          # the timed steps start at t = 0
@@ -653,7 +663,7 @@ def main():
     launches = 2 + 3 * args.steps
     kname = "stage_ws_kernel<32,%d,*> z-chunk %d (mean of stage 1 and stage 2)" % (
         tuned["info"][1], tuned["info"][2])
-    roofline = stage_roofline(m32, U, hbm, peak_kind, kname)
+    roofline = stage_roofline(m32, U, hbm, peak_kind, kname, ty=tuned["info"][1])
     # the same bytes over half the whole step's time: a floor for the stage
     # launches as they run in the step (stage 2 with its rate and totals
     # epilogue, the finalize launch and the gaps between launches charged to
@@ -664,7 +674,7 @@ def main():
                            / 1e9,
                            "frac": roofline["algorithmic_bytes_per_launch"] / (step_half * 1e-3)
                            / 1e9 / hbm}
-    issue = issue_roofline(cells, roofline["launch_ms"], clocks.get("sm_mhz"))
+    issue = issue_roofline(cells, roofline["launch_ms"], clocks.get("sm_mhz"), tuned["info"][1])
     if args.headline_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "ms_per_step": ms / args.steps,
@@ -738,9 +748,9 @@ def main():
               "tile": {"chosen": tuned2["info"], "ms_per_stage": tuned2["ms"]},
               "roofline": stage_roofline(ms2, Us, hbm, peak_kind,
                                          "stage_ws_kernel<32,%d,*> z-chunk %d" % (
-                                             tuned2["info"][1], tuned2["info"][2])),
+                                             tuned2["info"][1], tuned2["info"][2]),
+                                         ty=tuned2["info"][1]),
               "status": hh.hard_hydro_strerror(ms2.get_error())}
-    smooth["roofline"]["traffic"] = profiled_traffic(cells2)
     alg_bytes2 = BYTES_PER_CELL_STAGE[4] * cells2
 
     # ---------------- second scheme: WENO5-Z + HLL, FP32, 256^3 smooth flow ----------------
