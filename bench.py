@@ -686,15 +686,24 @@ def main():
     Uo = torch.empty_like(Uh).pin_memory()
     m32.advance_host(Uh, 1, CFL, out=Uo)                 # warm the handle's device buffer
     barrier()
-    t0 = time.perf_counter()
-    m32.advance_host(Uh, args.steps, CFL, out=Uo)
-    barrier()
-    e2e_s = rank_max(time.perf_counter() - t0)
+    e2e_runs = []                                        # three timed calls, the median reported
+    with ClockSampler(gpu_id) as clk_e2e:
+        time.sleep(0.3)                                  # the sampler is up before the first call
+        for _ in range(3):
+            barrier()
+            t0 = time.perf_counter()
+            m32.advance_host(Uh, args.steps, CFL, out=Uo)
+            barrier()
+            e2e_runs.append(rank_max(time.perf_counter() - t0))
+    e2e_s = sorted(e2e_runs)[1]
     e2e = {"value": whole_job_value(world, cells, 2 * args.steps, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": Uh.numel() * 4 / args.steps,
            "d2h_bytes_per_step": Uo.numel() * 4 / args.steps,
            "call": f"hard_hydro_advance_host: one call of {args.steps} steps of the blast from "
-                   "t = 0, pinned host buffers, both copies in the timed region"}
+                   "t = 0, pinned host buffers, both copies in the timed region; the median of "
+                   "three calls",
+           "seconds_per_call": e2e_runs,
+           "clocks": clk_e2e.summary()}
     del Uh, Uo, U, U0, m32
 
     # ---------------- FP64 plain on the same workload ----------------
