@@ -364,8 +364,8 @@ int hard_hydro_advect_E(hard_hydro_t h, const void* U, void* Er, double dt, void
  * relative residual (-1 when rtol <= 0).  The handle allocates its multigrid
  * levels on first use (freed by hard_hydro_set of another element type and by
  * hard_hydro_destroy).  With rtol > 0 the call synchronises `stream` once per
- * cycle.  A mesh with no active axis or with 2^31 cells or more returns
- * HARD_EUNSUPPORTED. */
+ * cycle.  A mesh with no active axis, with 2^31 cells or more, or with more
+ * than 65535 cells along y or z returns HARD_EUNSUPPORTED. */
 int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, double c,
                         double kappa, double rtol, int max_cycles, int* cycles_out,
                         double* resid_out, void* stream);

@@ -57,7 +57,7 @@ struct LvlArgs {
     const T* b;
     const T* D;
     int n[3];
-    T idx2[3];               // 1 / dx^2 per axis (0: inactive)
+    T wk[3];                 // dt / (2 dx^2) per axis (0: inactive): face weight (D_c + D_n) wk
     bool per[3];
     long long N;
     T dt;
@@ -119,7 +119,7 @@ __device__ __forceinline__ void stencil_eval(const LvlArgs<T>& a, const StencilV
         for (int s = -1; s <= 1; s += 2) {
             const bool use = (v.face >> (2 * ax + (s > 0))) & 1;
             const T Dn = v.Dn[2 * ax + (s > 0)], xn = v.xn[2 * ax + (s > 0)];
-            const T w = use ? a.dt * (T(0.5) * (v.Dc + Dn)) * a.idx2[ax] : T(0);
+            const T w = use ? (v.Dc + Dn) * a.wk[ax] : T(0);
             diag += w;
             off += w * xn;
         }
@@ -145,21 +145,31 @@ __device__ __forceinline__ void stencil(const LvlArgs<T>& a, int i, int j, int k
 // cells of its colour and reads only the other colour's x, so all of a
 // thread's stores can wait until its loads are done.
 constexpr int SMOOTH_ROWS = 4;
+#ifndef HH_FLD_COARSE_ROWS
+#define HH_FLD_COARSE_ROWS 2
+#endif
+constexpr int FLD_COARSE_ROWS = HH_FLD_COARSE_ROWS;   // the smoother's rows per thread below level 0
 
-template <typename T>
-__global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int color) {
+// SR rows per thread (SMOOTH_ROWS on the finest level; fewer on the coarser,
+// L2-resident levels, for more blocks).  lg: log2 of the threads per row.
+// Rows whose colour has at least 128 cells take whole blocks along x
+// (lg = 7); a shorter row takes 2^lg threads and a block serves 2^(7-lg)
+// groups of SR rows, so that the coarse levels keep every thread busy.
+template <typename T, int SR>
+__global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int color, int lg) {
     griddep_wait();
     const int k = blockIdx.z;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    StencilVals<T> v[SMOOTH_ROWS];
-    T bq[SMOOTH_ROWS];
-    int qs[SMOOTH_ROWS];
-    bool on[SMOOTH_ROWS];
+    const int p = blockIdx.x * (1 << lg) + (threadIdx.x & ((1 << lg) - 1));
+    const int j0 = (blockIdx.y * (128 >> lg) + (threadIdx.x >> lg)) * SR;
+    StencilVals<T> v[SR];
+    T bq[SR];
+    int qs[SR];
+    bool on[SR];
     // all rows' loads first (a row outside the level evaluates cell (0, 0, k)
     // and is not stored), then the arithmetic, then the stores
 #pragma unroll
-    for (int r = 0; r < SMOOTH_ROWS; ++r) {
-        const int j = blockIdx.y * SMOOTH_ROWS + r;
+    for (int r = 0; r < SR; ++r) {
+        const int j = j0 + r;
         // the cells of this colour in the row: i = 2p + ((j + k + color) & 1)
         const int i = 2 * p + ((j + k + color) & 1);
         on[r] = j < a.n[1] && i < a.n[0];
@@ -169,13 +179,13 @@ __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int col
         bq[r] = a.b[qs[r]];
     }
 #pragma unroll
-    for (int r = 0; r < SMOOTH_ROWS; ++r) {
+    for (int r = 0; r < SR; ++r) {
         T diag, off;
         stencil_eval(a, v[r], diag, off);
         bq[r] = (bq[r] + off) / diag;
     }
 #pragma unroll
-    for (int r = 0; r < SMOOTH_ROWS; ++r)
+    for (int r = 0; r < SR; ++r)
         if (on[r]) a.x[qs[r]] = bq[r];
     griddep_launch_dependents();
 }
@@ -359,10 +369,18 @@ __global__ void __launch_bounds__(128) residual_norm_color_kernel(const LvlArgs<
             else pr = fma(res, res, pr);
         }
     }
-    rr += (double)pr;
-    __shared__ double sr[4];
+    if (sizeof(T) == 8) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    } else {
+        // the warp's sum in FP32, then one conversion per warp (the FP64
+        // pipe is narrow; 128 terms in FP32 change the relative residual
+        // by ~1e-6 of itself)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        rr = (double)pr;
+    }
+    __shared__ double sr[4];
     if ((threadIdx.x & 31) == 0) sr[threadIdx.x >> 5] = rr;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -375,10 +393,24 @@ __global__ void __launch_bounds__(128) residual_norm_color_kernel(const LvlArgs<
 // sum b^2 of the fine level into *out (once per solve; b does not change).
 template <typename T>
 __global__ void __launch_bounds__(256) sumsq_kernel(const T* b, long long n, double* out) {
+    // a thread's values in grid-stride order, eight loads issued at a time
+    constexpr int UN = 8;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        acc += (double)b[i] * (double)b[i];
+    for (; i + (UN - 1) * stride < n; i += UN * stride) {
+        T v[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) v[u] = b[i + u * stride];
+        // the group's sum in the element type, then one FP64 addition (the
+        // FP64 pipe of this GPU is narrow; the sum normalises a convergence
+        // check, to which FP32 partial sums of eight terms add ~1e-7)
+        T part = T(0);
+#pragma unroll
+        for (int u = 0; u < UN; ++u) part = fma(v[u], v[u], part);
+        acc += (double)part;
+    }
+    for (; i < n; i += stride) acc += (double)b[i] * (double)b[i];
     __shared__ double sr[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -400,6 +432,10 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const T* b, long long n, dou
 // residual or the right-hand side) and every level's D.  Out: level 0's x.
 constexpr int FLD_SMALL_CELLS = 4096;
 constexpr int FLD_SMALL_MAX = 8;
+#ifndef HH_FLD_SMALL_THREADS
+#define HH_FLD_SMALL_THREADS 1024
+#endif
+constexpr int FLD_SMALL_THREADS = HH_FLD_SMALL_THREADS;   // the block of the small-level kernel
 
 template <typename T>
 struct SmallLevels {
@@ -407,61 +443,96 @@ struct SmallLevels {
     LvlArgs<T> lv[FLD_SMALL_MAX];    // global arrays (x, b of the first; D of all), extents, weights
     int h[FLD_SMALL_MAX][3];         // coarsening factors of level i into level i+1
     int off[FLD_SMALL_MAX];          // element offset of level i's x, b, D in shared memory
+    // division by n[0], n[1] and n[0] / 2 of level i as a multiply-high:
+    // q / d = umulhi(q, floor(2^32 / d) + 1), exact for q < 2^16 and d <= 2^16
+    // (the error q (m - 2^32/d) / 2^32 stays below 1/d); d = 1 passes q
+    unsigned mg[FLD_SMALL_MAX][3];
     int pre, post, coarse;           // sweeps
 };
 
-// One red-black half-sweep of a level held in shared memory.
+__device__ __forceinline__ int small_div(int q, unsigned m, int d) {
+    return d == 1 ? q : (int)__umulhi((unsigned)q, m);
+}
+
+// Level l of the set with its arrays in shared memory, built from the kernel
+// parameter (read in place) rather than kept in a local array.
 template <typename T>
-__device__ __forceinline__ void small_half_sweep(const LvlArgs<T>& s, int color) {
-    const int N = (int)s.N;
-    for (int q = threadIdx.x; q < N; q += blockDim.x) {
-        const int i = q % s.n[0], t = q / s.n[0];
-        const int j = t % s.n[1], k = t / s.n[1];
-        if (((i + j + k) & 1) != color) continue;
-        T diag, off;
-        stencil(s, i, j, k, q, diag, off);
-        s.x[q] = (s.b[q] + off) / diag;
+__device__ __forceinline__ LvlArgs<T> small_level(const SmallLevels<T>& S, T* sm, int l) {
+    LvlArgs<T> a = S.lv[l];
+    T* base = sm + S.off[l];
+    const int N = (int)a.N;
+    a.x = base;
+    a.b = base + N;
+    a.D = base + 2 * N;
+    return a;
+}
+
+// One red-black half-sweep of a level held in shared memory: with an even
+// row length the threads run over the colour's cells only (row r = j + n1 k
+// holds them at i = 2 i2 + ((j + k + colour) & 1)), else over every cell.
+template <typename T>
+__device__ __forceinline__ void small_half_sweep(const LvlArgs<T>& s, unsigned m0, unsigned m1,
+                                                 unsigned mh, int color) {
+    const int n0 = s.n[0], n1 = s.n[1], N = (int)s.N;
+    if ((n0 & 1) == 0) {
+        const int h = n0 >> 1;
+#pragma unroll 1
+        for (int q2 = threadIdx.x; q2 < (N >> 1); q2 += blockDim.x) {
+            const int r = small_div(q2, mh, h);
+            const int k = small_div(r, m1, n1), j = r - k * n1;
+            const int i = 2 * (q2 - r * h) + ((j + k + color) & 1);
+            const int q = r * n0 + i;
+            T diag, off;
+            stencil(s, i, j, k, q, diag, off);
+            s.x[q] = (s.b[q] + off) / diag;
+        }
+    } else {
+#pragma unroll 1
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+            const int t = small_div(q, m0, n0), i = q - t * n0;
+            const int k = small_div(t, m1, n1), j = t - k * n1;
+            if (((i + j + k) & 1) != color) continue;
+            T diag, off;
+            stencil(s, i, j, k, q, diag, off);
+            s.x[q] = (s.b[q] + off) / diag;
+        }
     }
     __syncthreads();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) small_vcycle_kernel(const SmallLevels<T> S) {
+__global__ void __launch_bounds__(FLD_SMALL_THREADS)
+small_vcycle_kernel(const __grid_constant__ SmallLevels<T> S) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char fld_smem[];
     T* sm = reinterpret_cast<T*>(fld_smem);
-    LvlArgs<T> L[FLD_SMALL_MAX];
     for (int l = 0; l < S.count; ++l) {
-        L[l] = S.lv[l];
+        const int N = (int)S.lv[l].N;
         T* base = sm + S.off[l];
-        const int N = (int)L[l].N;
-        L[l].x = base;
-        L[l].b = base + N;
-        L[l].D = base + 2 * N;
-        T* bb = base + N;
-        T* DD = base + 2 * N;
-        for (int q = threadIdx.x; q < N; q += blockDim.x) {
-            DD[q] = S.lv[l].D[q];
-            if (l == 0) {
+        const T* Dg = S.lv[l].D;
+        for (int q = threadIdx.x; q < N; q += blockDim.x) base[2 * N + q] = Dg[q];
+        if (l == 0) {
+            for (int q = threadIdx.x; q < N; q += blockDim.x) {
                 base[q] = S.lv[0].x[q];
-                bb[q] = S.lv[0].b[q];
+                base[N + q] = S.lv[0].b[q];
             }
         }
     }
     __syncthreads();
     // down: smooth, then the children's mean residual as the next b, x = 0
     for (int l = 0; l + 1 < S.count; ++l) {
+        const LvlArgs<T> F = small_level(S, sm, l);
         for (int it = 0; it < S.pre; ++it) {
-            small_half_sweep(L[l], 0);
-            small_half_sweep(L[l], 1);
+            small_half_sweep(F, S.mg[l][0], S.mg[l][1], S.mg[l][2], 0);
+            small_half_sweep(F, S.mg[l][0], S.mg[l][1], S.mg[l][2], 1);
         }
-        const LvlArgs<T>& F = L[l];
-        const LvlArgs<T>& C = L[l + 1];
+        const LvlArgs<T> C = small_level(S, sm, l + 1);
         const int h0 = S.h[l][0], h1 = S.h[l][1], h2 = S.h[l][2];
+        const int c0 = C.n[0], c1 = C.n[1];
         T* cb = const_cast<T*>(C.b);
         for (int Q = threadIdx.x; Q < (int)C.N; Q += blockDim.x) {
-            const int I = Q % C.n[0], t = Q / C.n[0];
-            const int J = t % C.n[1], K = t / C.n[1];
+            const int t = small_div(Q, S.mg[l + 1][0], c0), I = Q - t * c0;
+            const int K = small_div(t, S.mg[l + 1][1], c1), J = t - K * c1;
             T sum = T(0);
             for (int cz = 0; cz < h2; ++cz)
                 for (int cy = 0; cy < h1; ++cy)
@@ -481,16 +552,17 @@ __global__ void __launch_bounds__(1024) small_vcycle_kernel(const SmallLevels<T>
     // (every later sweep would return the same values) or `coarse` sweeps
     {
         __shared__ int changed[2];
-        const LvlArgs<T>& s = L[S.count - 1];
-        const int N = (int)s.N;
+        const int lc = S.count - 1;
+        const LvlArgs<T> s = small_level(S, sm, lc);
+        const int N = (int)s.N, n0 = s.n[0], n1 = s.n[1];
         if (threadIdx.x == 0) changed[0] = 0;
         __syncthreads();
         for (int it = 0; it < S.coarse; ++it) {
             for (int color = 0; color < 2; ++color) {
                 if (color == 1 && threadIdx.x == 0) changed[(it + 1) & 1] = 0;
                 for (int q = threadIdx.x; q < N; q += blockDim.x) {
-                    const int i = q % s.n[0], t = q / s.n[0];
-                    const int j = t % s.n[1], k = t / s.n[1];
+                    const int t = small_div(q, S.mg[lc][0], n0), i = q - t * n0;
+                    const int k = small_div(t, S.mg[lc][1], n1), j = t - k * n1;
                     if (((i + j + k) & 1) != color) continue;
                     T diag, off;
                     stencil(s, i, j, k, q, diag, off);
@@ -505,43 +577,42 @@ __global__ void __launch_bounds__(1024) small_vcycle_kernel(const SmallLevels<T>
     }
     // up: add the coarse correction to the children, smooth
     for (int l = S.count - 2; l >= 0; --l) {
-        const LvlArgs<T>& F = L[l];
-        const LvlArgs<T>& C = L[l + 1];
+        const LvlArgs<T> F = small_level(S, sm, l);
+        const LvlArgs<T> C = small_level(S, sm, l + 1);
         const int h0 = S.h[l][0], h1 = S.h[l][1], h2 = S.h[l][2];
+        const int n0 = F.n[0], n1 = F.n[1];
         for (int q = threadIdx.x; q < (int)F.N; q += blockDim.x) {
-            const int i = q % F.n[0], t = q / F.n[0];
-            const int j = t % F.n[1], k = t / F.n[1];
+            const int t = small_div(q, S.mg[l][0], n0), i = q - t * n0;
+            const int k = small_div(t, S.mg[l][1], n1), j = t - k * n1;
             F.x[q] += C.x[((k / h2) * C.n[1] + j / h1) * C.n[0] + i / h0];
         }
         __syncthreads();
         for (int it = 0; it < S.post; ++it) {
-            small_half_sweep(F, 0);
-            small_half_sweep(F, 1);
+            small_half_sweep(F, S.mg[l][0], S.mg[l][1], S.mg[l][2], 0);
+            small_half_sweep(F, S.mg[l][0], S.mg[l][1], S.mg[l][2], 1);
         }
     }
-    for (int q = threadIdx.x; q < (int)L[0].N; q += blockDim.x) S.lv[0].x[q] = L[0].x[q];
+    {
+        const int N = (int)S.lv[0].N;
+        for (int q = threadIdx.x; q < N; q += blockDim.x) S.lv[0].x[q] = sm[S.off[0] + q];
+    }
     griddep_launch_dependents();
 }
 
-// coarse[I] = mean of the children fine[...] (restriction of r, and of D)
+// coarse[I] = mean of the children fine[...] (restriction of D): one thread
+// per coarse x cell, a coarse row per blockIdx.y, a coarse plane per blockIdx.z
 template <typename T>
-__global__ void __launch_bounds__(256) restrict_kernel(const T* fine, T* coarse, int nf0, int nf1,
-                                                       int nc0, int nc1, int nc2, int h0, int h1,
-                                                       int h2, long long Nc) {
+__global__ void __launch_bounds__(128) restrict_kernel(const T* fine, T* coarse, int nf0, int nf1,
+                                                       int nc0, int nc1, int h0, int h1, int h2) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= nc0) return;
     const T inv = T(1) / T(h0 * h1 * h2);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Nc;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(q % nc0);
-        const long long t = q / nc0;
-        const int J = (int)(t % nc1), K = (int)(t / nc1);
-        T s = T(0);
-        for (int c = 0; c < h2; ++c)
-            for (int b = 0; b < h1; ++b)
-                for (int a = 0; a < h0; ++a)
-                    s += fine[((long long)(K * h2 + c) * nf1 + (J * h1 + b)) * nf0 + (I * h0 + a)];
-        coarse[q] = s * inv;
-        (void)nc2;
-    }
+    T s = T(0);
+    for (int c = 0; c < h2; ++c)
+        for (int b = 0; b < h1; ++b)
+            for (int a = 0; a < h0; ++a)
+                s += fine[((long long)(K * h2 + c) * nf1 + (J * h1 + b)) * nf0 + (I * h0 + a)];
+    coarse[((long long)K * nc1 + J) * nc0 + I] = s * inv;
 }
 
 // fine[i] += coarse[parent(i)]
@@ -574,37 +645,62 @@ __global__ void __launch_bounds__(128) prolong_kernel(T* fine, const T* coarse, 
     griddep_launch_dependents();
 }
 
-// D = c lambda(R) / (kappa rho), R = |grad E| / (rho kappa E), on level 0
+// D = c lambda(R) / (kappa rho), R = |grad E| / (rho kappa E), on level 0:
+// each thread takes its x cell in SMOOTH_ROWS consecutive rows of a plane
+// (x along threads, a row group per blockIdx.y, a plane per blockIdx.z), the
+// rows' loads issued before their arithmetic; neighbours across a periodic
+// wrap or clamped at a wall by selects.  h0, h1, h2: 1 / (2 dx) per axis; the
+// limiter's quotient and the last one are taken together,
+// D = c (2 + R) / ((6 + 3R + R^2) kappa rho).
 template <typename T>
-__global__ void __launch_bounds__(256) coeff_kernel(const T* U, const T* E, T* D, LvlArgs<T> a,
-                                                    T c, T kappa, T dx0, T dx1, T dx2) {
-    const T dxa[3] = {dx0, dx1, dx2};
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < a.N;
-         q += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(q, a.n, i, j, k);
-        const int cc[3] = {i, j, k};
-        const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+__global__ void __launch_bounds__(128) coeff_kernel(const T* U, const T* E, T* D, LvlArgs<T> a,
+                                                    T c, T kappa, T h0, T h1, T h2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.z;
+    if (i >= a.n[0]) return;
+    const T hx[3] = {h0, h1, h2};
+    const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+    T Eu[SMOOTH_ROWS][3], Ed[SMOOTH_ROWS][3], Ec[SMOOTH_ROWS], rho[SMOOTH_ROWS];
+    long long qs[SMOOTH_ROWS];
+    bool on[SMOOTH_ROWS];
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r) {
+        const int j = blockIdx.y * SMOOTH_ROWS + r;
+        on[r] = j < a.n[1];
+        const int jj = on[r] ? j : 0;                // a row outside the level is not stored
+        const int cc[3] = {i, jj, k};
+        const long long q = ((long long)k * a.n[1] + jj) * a.n[0] + i;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const int n = a.n[ax];
+            Eu[r][ax] = Ed[r][ax] = T(0);
+            if (n <= 1) continue;
+            int up = cc[ax] + 1, dn = cc[ax] - 1;
+            if (a.per[ax]) {
+                up = up == n ? 0 : up;
+                dn = dn < 0 ? n - 1 : dn;
+            } else {
+                up = up > n - 1 ? n - 1 : up;
+                dn = dn < 0 ? 0 : dn;
+            }
+            Eu[r][ax] = E[q + (long long)(up - cc[ax]) * stride[ax]];
+            Ed[r][ax] = E[q + (long long)(dn - cc[ax]) * stride[ax]];
+        }
+        Ec[r] = E[q];
+        rho[r] = U[q];
+        qs[r] = q;
+    }
+#pragma unroll
+    for (int r = 0; r < SMOOTH_ROWS; ++r) {
         T grad2 = T(0);
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             if (a.n[ax] <= 1) continue;
-            int up = cc[ax] + 1, dn = cc[ax] - 1;
-            if (a.per[ax]) {
-                up = (up + a.n[ax]) % a.n[ax];
-                dn = (dn + a.n[ax]) % a.n[ax];
-            } else {
-                up = up > a.n[ax] - 1 ? a.n[ax] - 1 : up;
-                dn = dn < 0 ? 0 : dn;
-            }
-            const T g = (E[q + (long long)(up - cc[ax]) * stride[ax]] -
-                         E[q + (long long)(dn - cc[ax]) * stride[ax]]) / (T(2) * dxa[ax]);
+            const T g = (Eu[r][ax] - Ed[r][ax]) * hx[ax];
             grad2 += g * g;
         }
-        const T rho = U[q];
-        const T R = sqrt(grad2) / (rho * kappa * E[q]);
-        const T lam = (T(2) + R) / (T(6) + T(3) * R + R * R);
-        D[q] = c * lam / (kappa * rho);
+        const T R = sqrt(grad2) / (rho[r] * kappa * Ec[r]);
+        const T den = (T(6) + T(3) * R + R * R) * (kappa * rho[r]);
+        if (on[r]) D[qs[r]] = c * (T(2) + R) / den;
     }
 }
 
@@ -628,7 +724,7 @@ LvlArgs<T> level_args(const FldHierarchy* H, int l, double dt) {
     a.D = static_cast<const T*>(L.D);
     for (int ax = 0; ax < 3; ++ax) {
         a.n[ax] = L.n[ax];
-        a.idx2[ax] = L.n[ax] > 1 ? (T)(1.0 / (L.dx[ax] * L.dx[ax])) : T(0);
+        a.wk[ax] = L.n[ax] > 1 ? (T)(0.5 * dt / (L.dx[ax] * L.dx[ax])) : T(0);
         a.per[ax] = H->bc_lo[ax] == 0 && H->bc_hi[ax] == 0;
     }
     a.N = L.N;
@@ -639,11 +735,18 @@ LvlArgs<T> level_args(const FldHierarchy* H, int l, double dt) {
 template <typename T>
 cudaError_t smooth(const FldHierarchy* H, int l, double dt, int sweeps, cudaStream_t s) {
     const LvlArgs<T> a = level_args<T>(H, l, dt);
-    dim3 g = rows_grid(H->L[l], 2);
-    g.y = (g.y + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
+    const FldLevel& L = H->L[l];
+    const int hx = (L.n[0] + 1) / 2;                  // cells of a colour in a row (at most)
+    int lg = 0;
+    while (lg < 7 && (1 << lg) < hx) ++lg;
+    const int sr = l == 0 ? SMOOTH_ROWS : FLD_COARSE_ROWS;
+    const int rows = (128 >> lg) * sr;                // rows of a block
+    const dim3 g(lg == 7 ? (unsigned)((hx + 127) / 128) : 1u, (unsigned)((L.n[1] + rows - 1) / rows),
+                 (unsigned)L.n[2]);
+    auto kern = l == 0 ? smooth_kernel<T, SMOOTH_ROWS> : smooth_kernel<T, FLD_COARSE_ROWS>;
     for (int it = 0; it < sweeps; ++it)
         for (int color = 0; color < 2; ++color) {
-            const cudaError_t e = launch_pdl(smooth_kernel<T>, g, dim3(128), 0, s, a, color);
+            const cudaError_t e = launch_pdl(kern, g, dim3(128), 0, s, a, color, lg);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -653,9 +756,9 @@ template <typename T>
 void restrict_to(const FldHierarchy* H, int l, const void* fine, void* coarse, cudaStream_t s) {
     const FldLevel& F = H->L[l];
     const FldLevel& C = H->L[l + 1];
-    restrict_kernel<T><<<grid_for(C.N), 256, 0, s>>>(
+    restrict_kernel<T><<<rows_grid(C, 1), 128, 0, s>>>(
         static_cast<const T*>(fine), static_cast<T*>(coarse), F.n[0], F.n[1], C.n[0], C.n[1],
-        C.n[2], F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1, C.N);
+        F.coarsened[0] ? 2 : 1, F.coarsened[1] ? 2 : 1, F.coarsened[2] ? 2 : 1);
 }
 
 template <typename T>
@@ -668,9 +771,11 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
     if (e != cudaSuccess) return e;
     {
         const LvlArgs<T> a = level_args<T>(H, 0, dt);
-        coeff_kernel<T><<<grid_for(L0.N), 256, 0, s>>>(
+        dim3 g = rows_grid(L0, 1);
+        g.y = (g.y + SMOOTH_ROWS - 1) / SMOOTH_ROWS;
+        coeff_kernel<T><<<g, 128, 0, s>>>(
             static_cast<const T*>(U), static_cast<const T*>(L0.b), static_cast<T*>(L0.D), a,
-            (T)c, (T)kappa, (T)m.dxk[0], (T)m.dxk[1], (T)m.dxk[2]);
+            (T)c, (T)kappa, (T)(0.5 / m.dxk[0]), (T)(0.5 / m.dxk[1]), (T)(0.5 / m.dxk[2]));
     }
     for (int l = 0; l + 1 < H->nl; ++l) restrict_to<T>(H, l, H->L[l].D, H->L[l + 1].D, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -690,6 +795,9 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             const FldLevel& F = H->L[ls + i];
             S.lv[i] = level_args<T>(H, ls + i, dt);
             for (int a = 0; a < 3; ++a) S.h[i][a] = F.coarsened[a] ? 2 : 1;
+            const int dv[3] = {F.n[0], F.n[1], F.n[0] / 2 > 0 ? F.n[0] / 2 : 1};
+            for (int a = 0; a < 3; ++a)
+                S.mg[i][a] = dv[a] > 1 ? (unsigned)((1ull << 32) / (unsigned)dv[a] + 1) : 0u;
             S.off[i] = off;
             off += 3 * (int)F.N;
         }
@@ -739,7 +847,8 @@ cudaError_t solve_t(FldHierarchy* H, const MeshDesc& m, const void* U, void* Er,
             if (e != cudaSuccess) return e;
         }
         if (ls < H->nl) {
-            e = launch_pdl(small_vcycle_kernel<T>, dim3(1), dim3(1024), small_bytes, s, S);
+            e = launch_pdl(small_vcycle_kernel<T>, dim3(1), dim3(FLD_SMALL_THREADS), small_bytes, s,
+                           S);
             if (e != cudaSuccess) return e;
         } else if ((e = smooth<T>(H, H->nl - 1, dt, FLD_COARSE, s)) != cudaSuccess) {
             return e;                                // a coarsest level too large for one block

@@ -676,6 +676,8 @@ int hard_hydro_fld_step(hard_hydro_t h, const void* U, void* Er, double dt, doub
         return HARD_EINVAL;
     if (h->mesh.dim == 0) return HARD_EUNSUPPORTED;          // nothing to diffuse along
     if (h->mesh.N >= (1ll << 31)) return HARD_EUNSUPPORTED;  // 32-bit cell indices
+    // the level kernels take a row per blockIdx.y and a plane per blockIdx.z
+    if (h->mesh.n[1] > 65535 || h->mesh.n[2] > 65535) return HARD_EUNSUPPORTED;
     if (!hh::fld_matches(h->fld, h->mesh, h->dtype)) {
         hh::fld_destroy(h->fld);
         h->fld = hh::fld_create(h->mesh, h->dtype);

@@ -65,6 +65,11 @@ def test_host_only_calls_without_gpu(libpath):
     assert hh.hard_hydro_fld_step(h, None, None, 1.0, 1.0, 1.0, 1e-6, 10, None)[0] == hh.HARD_EINVAL
     assert hh.hard_hydro_fld_step(h, 16, 32, 1.0, 1.0, -1.0, 1e-6, 10, None)[0] == hh.HARD_EINVAL
     assert hh.hard_hydro_fld_step(h, 16, 32, 1.0, 1.0, 1.0, 1e-6, 0, None)[0] == hh.HARD_EINVAL
+    # more rows than a grid dimension holds: refused before any device work
+    hy = hh.hard_hydro_create(4, 70000, 1, 1.4, hh.HARD_BC_OUTFLOW)
+    assert hy
+    assert hh.hard_hydro_fld_step(hy, 16, 32, 1.0, 1.0, 1.0, 1e-6, 1, None)[0] == hh.HARD_EUNSUPPORTED
+    hh.hard_hydro_destroy(hy)
     assert hh.hard_hydro_advect_E(h, None, None, 1.0, None) == hh.HARD_EINVAL
     assert hh.hard_hydro_advect_E(h, 16, 32, 0.0, None) == hh.HARD_EINVAL
     # the split adjoint of a slab checks its arguments before touching the device
