@@ -686,16 +686,35 @@ def main():
     Uo = torch.empty_like(Uh).pin_memory()
     m32.advance_host(Uh, 1, CFL, out=Uo)                 # warm the handle's device buffer
     barrier()
-    e2e_runs = []                                        # three timed calls, the median reported
+    e2e_runs, e2e_dev = [], []                           # three timed calls, the median reported
     with ClockSampler(gpu_id) as clk_e2e:
         time.sleep(0.3)                                  # the sampler is up before the first call
         for _ in range(3):
             barrier()
             t0 = time.perf_counter()
+            ev0.record(stream)
             m32.advance_host(Uh, args.steps, CFL, out=Uo)
+            ev1.record(stream)
             barrier()
             e2e_runs.append(rank_max(time.perf_counter() - t0))
+            e2e_dev.append(ev0.elapsed_time(ev1))
     e2e_s = sorted(e2e_runs)[1]
+    # the pinned-buffer copy bandwidth of this host (it sets the gap between
+    # this figure and the device-timed one, and differs between machines)
+    Ud = torch.empty(Uh.shape, dtype=Uh.dtype, device=dev)
+    Ud.copy_(Uh, non_blocking=True)
+    Uo.copy_(Ud, non_blocking=True)
+    barrier()
+    ev0.record(stream)
+    Ud.copy_(Uh, non_blocking=True)
+    ev1.record(stream)
+    Uo.copy_(Ud, non_blocking=True)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    barrier()
+    copy_gbs = {"h2d": Uh.numel() * 4 / ev0.elapsed_time(ev1) / 1e6,
+                "d2h": Uo.numel() * 4 / ev1.elapsed_time(ev2) / 1e6}
+    del Ud
     e2e = {"value": whole_job_value(world, cells, 2 * args.steps, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": Uh.numel() * 4 / args.steps,
            "d2h_bytes_per_step": Uo.numel() * 4 / args.steps,
@@ -703,6 +722,8 @@ def main():
                    "t = 0, pinned host buffers, both copies in the timed region; the median of "
                    "three calls",
            "seconds_per_call": e2e_runs,
+           "device_ms_per_call": e2e_dev,               # the stream's span: copies and steps
+           "pinned_copy_gbs": copy_gbs,
            "clocks": clk_e2e.summary()}
     del Uh, Uo, U, U0, m32
 
