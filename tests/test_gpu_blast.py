@@ -15,6 +15,7 @@ import pytest
 
 import hydro_inputs as H
 import oracle
+import oracle_window
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -109,3 +110,54 @@ def test_blast_symmetry_f64():
     assert np.max(np.abs(mx - my.transpose(0, 2, 1))) <= tol * sm
     assert np.max(np.abs(mz - mx.transpose(2, 1, 0))) <= tol * sm
     assert np.max(np.abs(E - E.transpose(2, 1, 0))) <= tol * se
+
+
+# ---- the headline size: 512^3 in the launch configuration the bench times ----
+
+FULL_N = 512
+FULL_STEPS = 3
+FULL_HALF = 4 * FULL_STEPS        # a two-stage PLM step reaches 4 cells
+
+
+@pytest.fixture(scope="module")
+def blast_512_f32():
+    """The 512^3 blast as the bench builds it (seed 0), in FP32."""
+    return H.blast_3d(FULL_N, seed=0, gamma=GAMMA, dtype=np.float32)
+
+
+@pytest.mark.parametrize("dtype,kernel,tile,tol", [
+    (torch.float32, hh.HARD_KERNEL_FUSED, 2, 1e-5),     # the tile the bench's tuner picks
+    (torch.float32, hh.HARD_KERNEL_FUSED, 1, 1e-5),
+    (torch.float64, hh.HARD_KERNEL_PLAIN, -1, 1e-12),   # the FP64 leg of the bench
+])
+def test_blast_512_sampled_parity(blast_512_f32, dtype, kernel, tile, tol):
+    """The headline workload at its full size: three steps of the 512^3 blast
+    on the device time loop (CFL 0.3, reflecting walls), then 44 cells (the
+    blast centre and its front, random cells, walls, edges and corners)
+    against the oracle run on each cell's window with the device's dt
+    schedule; error relative to each field's largest magnitude after the
+    steps.  The FP64 kernel sees the FP32 input widened, like the oracle."""
+    U = blast_512_f32
+    n = FULL_N
+    m = hh.HardHydro((n, n, n), GAMMA, hh.HARD_BC_REFLECT, dtype=dtype, kernel=kernel)
+    if tile >= 0:
+        m.set_kernel(kernel, tile)
+    Ud = torch.tensor(U, dtype=dtype, device="cuda")
+    _, dtl, _ = m.advance(Ud, FULL_STEPS, CFL, log_dt=True)
+    assert m.get_error() == hh.HARD_OK
+    dts = [float(d) for d in dtl.cpu()]
+    rng = np.random.default_rng(11)
+    c0 = n // 2
+    cells = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(20)]
+    cells += [tuple(int(v) for v in c0 - 7 + rng.integers(0, 14, 3)) for _ in range(16)]
+    cells += [(0, 0, 0), (n - 1, n - 1, n - 1), (0, c0, n - 1), (n - 1, 0, c0),
+              (3, c0 - 1, 0), (n - 4, 4, 300), (c0, c0, c0), (c0 - 1, c0 - 1, c0 - 1)]
+    idx = torch.tensor(cells, device="cuda")
+    got = Ud[:, idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    scale = Ud.abs().amax(dim=(1, 2, 3)).double().cpu().numpy()
+    for q, c in enumerate(cells):
+        ref = oracle_window.cell_after(U, c, dts, GAMMA, FULL_HALF)
+        err = np.abs(got[:, q] - ref) / scale
+        assert np.all(err <= tol), (c, err)
+    # the blast has started: the cells next to the energy spot move
+    assert np.max(np.abs(got[1:4])) > 0.0
