@@ -889,9 +889,10 @@ def main():
     mf.fld_step(Uf, Ef, dt_fld, 1.0, 1.0, rtol=1e-5, max_cycles=40)      # builds the levels
     Ef.copy_(Ef0)
     barrier()
-    e0.record(stream)
-    cyc_f, res_f = mf.fld_step(Uf, Ef, dt_fld, 1.0, 1.0, rtol=1e-5, max_cycles=40)
-    e1.record(stream)
+    with nvtx_range("fld_step"):
+        e0.record(stream)
+        cyc_f, res_f = mf.fld_step(Uf, Ef, dt_fld, 1.0, 1.0, rtol=1e-5, max_cycles=40)
+        e1.record(stream)
     barrier()
     fld_ms = e0.elapsed_time(e1)
     # bytes per V-cycle: per level, two pre- and two post-smoothing red-black

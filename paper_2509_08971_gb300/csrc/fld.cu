@@ -82,28 +82,53 @@ struct StencilVals {
     int face;                 // bit 2 ax + (s > 0): that face carries a flux
 };
 
+// Neighbour offsets of a cell along one axis (coordinate c of n cells, the
+// axis' element stride): lo / hi are added to the cell's index (across the
+// wrap on a periodic axis; 0 at a wall, whose face carries no flux), face
+// bit 0 / 1 set when the low / high face carries a flux.
+struct AxisNb {
+    int lo, hi, face;
+};
+
+__device__ __forceinline__ AxisNb axis_nb(int c, int n, bool per, int stride) {
+    const bool inl = c > 0, inh = c + 1 < n;
+    AxisNb b;
+    b.lo = inl ? -stride : (per ? (n - 1) * stride : 0);
+    b.hi = inh ? stride : (per ? -(n - 1) * stride : 0);
+    b.face = (inl || per ? 1 : 0) | (inh || per ? 2 : 0);
+    return b;
+}
+
+// The loads of cell q with the z-axis neighbours given (nbz: the same for
+// every cell of a plane, so a kernel that takes several rows of one plane
+// per thread computes it once).
 template <typename T>
-__device__ __forceinline__ void stencil_load(const LvlArgs<T>& a, int i, int j, int k, int q,
-                                             StencilVals<T>& v) {
-    const int c[3] = {i, j, k};
-    const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
+__device__ __forceinline__ void stencil_load_z(const LvlArgs<T>& a, int i, int j, int q,
+                                               const AxisNb& nbz, StencilVals<T>& v) {
     v.Dc = a.D[q];
     v.face = 0;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const int n = a.n[ax];
         if (n <= 1) continue;                       // inactive axis: the same for every thread
-#pragma unroll
-        for (int s = -1; s <= 1; s += 2) {
-            const int m = c[ax] + s;
-            const bool in = m >= 0 && m < n;
-            const int wrap = q + (m < 0 ? (n - 1) : -(n - 1)) * stride[ax];
-            const int qn = in ? q + s * stride[ax] : (a.per[ax] ? wrap : q);
-            v.Dn[2 * ax + (s > 0)] = a.D[qn];
-            v.xn[2 * ax + (s > 0)] = a.x[qn];
-            v.face |= (in || a.per[ax]) ? 1 << (2 * ax + (s > 0)) : 0;
-        }
+        const AxisNb b = ax == 2 ? nbz : axis_nb(ax == 0 ? i : j, n, a.per[ax], ax == 0 ? 1 : a.n[0]);
+        v.Dn[2 * ax] = a.D[q + b.lo];
+        v.xn[2 * ax] = a.x[q + b.lo];
+        v.Dn[2 * ax + 1] = a.D[q + b.hi];
+        v.xn[2 * ax + 1] = a.x[q + b.hi];
+        v.face |= b.face << (2 * ax);
     }
+}
+
+template <typename T>
+__device__ __forceinline__ AxisNb plane_nb(const LvlArgs<T>& a, int k) {
+    return axis_nb(k, a.n[2], a.per[2], a.n[0] * a.n[1]);
+}
+
+template <typename T>
+__device__ __forceinline__ void stencil_load(const LvlArgs<T>& a, int i, int j, int k, int q,
+                                             StencilVals<T>& v) {
+    stencil_load_z(a, i, j, q, plane_nb(a, k), v);
 }
 
 template <typename T>
@@ -149,8 +174,12 @@ constexpr int SMOOTH_ROWS = 4;
 #define HH_FLD_COARSE_ROWS 2
 #endif
 constexpr int FLD_COARSE_ROWS = HH_FLD_COARSE_ROWS;   // the smoother's rows per thread below level 0
+#ifndef HH_FLD_FINE_ROWS
+#define HH_FLD_FINE_ROWS 4
+#endif
+constexpr int FLD_FINE_ROWS = HH_FLD_FINE_ROWS;       // and on level 0
 
-// SR rows per thread (SMOOTH_ROWS on the finest level; fewer on the coarser,
+// SR rows per thread (FLD_FINE_ROWS on the finest level; fewer on the coarser,
 // L2-resident levels, for more blocks).  lg: log2 of the threads per row.
 // Rows whose colour has at least 128 cells take whole blocks along x
 // (lg = 7); a shorter row takes 2^lg threads and a block serves 2^(7-lg)
@@ -165,6 +194,7 @@ __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int col
     T bq[SR];
     int qs[SR];
     bool on[SR];
+    const AxisNb nbz = plane_nb(a, k);
     // all rows' loads first (a row outside the level evaluates cell (0, 0, k)
     // and is not stored), then the arithmetic, then the stores
 #pragma unroll
@@ -175,7 +205,7 @@ __global__ void __launch_bounds__(128) smooth_kernel(const LvlArgs<T> a, int col
         on[r] = j < a.n[1] && i < a.n[0];
         const int ii = on[r] ? i : 0, jj = on[r] ? j : 0;
         qs[r] = (k * a.n[1] + jj) * a.n[0] + ii;
-        stencil_load(a, ii, jj, k, qs[r], v[r]);
+        stencil_load_z(a, ii, jj, qs[r], nbz, v[r]);
         bq[r] = a.b[qs[r]];
     }
 #pragma unroll
@@ -220,12 +250,14 @@ __global__ void __launch_bounds__(128) residual_restrict_kernel(const LvlArgs<T>
             constexpr int NC = RED ? 2 : 4;
             StencilVals<T> v[NC];
             T bq[NC], xq[NC];
+            const int k = 2 * K + cz;
+            const AxisNb nbz = plane_nb(a, k);
 #pragma unroll
             for (int n = 0; n < NC; ++n) {
                 const int c = RED ? (cz == 0 ? 3 * n : 1 + n) : n;
-                const int i = 2 * I + (c & 1), j = 2 * J + (c >> 1), k = 2 * K + cz;
+                const int i = 2 * I + (c & 1), j = 2 * J + (c >> 1);
                 const int q = (k * a.n[1] + j) * a.n[0] + i;
-                stencil_load(a, i, j, k, q, v[n]);
+                stencil_load_z(a, i, j, q, nbz, v[n]);
                 bq[n] = a.b[q];
                 xq[n] = a.x[q];
             }
@@ -278,13 +310,14 @@ __global__ void __launch_bounds__(128) residual_norms_kernel(const LvlArgs<T> a,
         StencilVals<T> v[SMOOTH_ROWS];
         T bq[SMOOTH_ROWS], xq[SMOOTH_ROWS];
         bool on[SMOOTH_ROWS];
+        const AxisNb nbz = plane_nb(a, k);
 #pragma unroll
         for (int r = 0; r < SMOOTH_ROWS; ++r) {
             const int j = grp * SMOOTH_ROWS + r;
             on[r] = j < a.n[1] && i < a.n[0];
             const int ii = on[r] ? i : 0, jj = on[r] ? j : 0;
             const int q = (k * a.n[1] + jj) * a.n[0] + ii;
-            stencil_load(a, ii, jj, k, q, v[r]);
+            stencil_load_z(a, ii, jj, q, nbz, v[r]);
             bq[r] = a.b[q];
             xq[r] = a.x[q];
         }
@@ -346,6 +379,7 @@ __global__ void __launch_bounds__(128) residual_norm_color_kernel(const LvlArgs<
     StencilVals<T> v[SMOOTH_ROWS];
     T bq[SMOOTH_ROWS], xq[SMOOTH_ROWS];
     bool on[SMOOTH_ROWS];
+    const AxisNb nbz = plane_nb(a, k);
 #pragma unroll
     for (int r = 0; r < SMOOTH_ROWS; ++r) {
         const int j = blockIdx.y * SMOOTH_ROWS + r;
@@ -353,7 +387,7 @@ __global__ void __launch_bounds__(128) residual_norm_color_kernel(const LvlArgs<
         on[r] = j < a.n[1] && i < a.n[0];
         const int ii = on[r] ? i : 0, jj = on[r] ? j : 0;
         const int q = (k * a.n[1] + jj) * a.n[0] + ii;
-        stencil_load(a, ii, jj, k, q, v[r]);
+        stencil_load_z(a, ii, jj, q, nbz, v[r]);
         bq[r] = a.b[q];
         xq[r] = a.x[q];
     }
@@ -739,11 +773,11 @@ cudaError_t smooth(const FldHierarchy* H, int l, double dt, int sweeps, cudaStre
     const int hx = (L.n[0] + 1) / 2;                  // cells of a colour in a row (at most)
     int lg = 0;
     while (lg < 7 && (1 << lg) < hx) ++lg;
-    const int sr = l == 0 ? SMOOTH_ROWS : FLD_COARSE_ROWS;
+    const int sr = l == 0 ? FLD_FINE_ROWS : FLD_COARSE_ROWS;
     const int rows = (128 >> lg) * sr;                // rows of a block
     const dim3 g(lg == 7 ? (unsigned)((hx + 127) / 128) : 1u, (unsigned)((L.n[1] + rows - 1) / rows),
                  (unsigned)L.n[2]);
-    auto kern = l == 0 ? smooth_kernel<T, SMOOTH_ROWS> : smooth_kernel<T, FLD_COARSE_ROWS>;
+    auto kern = l == 0 ? smooth_kernel<T, FLD_FINE_ROWS> : smooth_kernel<T, FLD_COARSE_ROWS>;
     for (int it = 0; it < sweeps; ++it)
         for (int color = 0; color < 2; ++color) {
             const cudaError_t e = launch_pdl(kern, g, dim3(128), 0, s, a, color, lg);
