@@ -660,16 +660,16 @@ __global__ void __launch_bounds__(128) prolong_kernel(T* fine, const T* coarse, 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf0) return;
     const int ic = i / h0;
-    const long long kc = (long long)(k / h2) * nc1;
+    const int kc = (k / h2) * nc1;                     // levels have fewer than 2^31 cells
     T f[SMOOTH_ROWS], c[SMOOTH_ROWS];
-    long long qs[SMOOTH_ROWS];
+    int qs[SMOOTH_ROWS];
     bool on[SMOOTH_ROWS];
 #pragma unroll
     for (int r = 0; r < SMOOTH_ROWS; ++r) {
         const int j = blockIdx.y * SMOOTH_ROWS + r;
         on[r] = j < nf1;
         const int jj = on[r] ? j : 0;
-        qs[r] = ((long long)k * nf1 + jj) * nf0 + i;
+        qs[r] = (k * nf1 + jj) * nf0 + i;
         f[r] = fine[qs[r]];
         c[r] = coarse[(kc + jj / h1) * nc0 + ic];
     }
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(128) prolong_kernel(T* fine, const T* coarse, 
 // each thread takes its x cell in SMOOTH_ROWS consecutive rows of a plane
 // (x along threads, a row group per blockIdx.y, a plane per blockIdx.z), the
 // rows' loads issued before their arithmetic; neighbours across a periodic
-// wrap or clamped at a wall by selects.  h0, h1, h2: 1 / (2 dx) per axis; the
+// wrap or, at a wall, the cell itself.  h0, h1, h2: 1 / (2 dx) per axis; the
 // limiter's quotient and the last one are taken together,
 // D = c (2 + R) / ((6 + 3R + R^2) kappa rho).
 template <typename T>
@@ -692,32 +692,27 @@ __global__ void __launch_bounds__(128) coeff_kernel(const T* U, const T* E, T* D
     const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.z;
     if (i >= a.n[0]) return;
     const T hx[3] = {h0, h1, h2};
-    const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
     T Eu[SMOOTH_ROWS][3], Ed[SMOOTH_ROWS][3], Ec[SMOOTH_ROWS], rho[SMOOTH_ROWS];
-    long long qs[SMOOTH_ROWS];
+    int qs[SMOOTH_ROWS];                              // the level has fewer than 2^31 cells
     bool on[SMOOTH_ROWS];
+    // the wall neighbour is the cell itself (the edge cell repeated), the
+    // periodic one across the wrap: the offsets of axis_nb
+    const AxisNb nbz = plane_nb(a, k);
 #pragma unroll
     for (int r = 0; r < SMOOTH_ROWS; ++r) {
         const int j = blockIdx.y * SMOOTH_ROWS + r;
         on[r] = j < a.n[1];
         const int jj = on[r] ? j : 0;                // a row outside the level is not stored
-        const int cc[3] = {i, jj, k};
-        const long long q = ((long long)k * a.n[1] + jj) * a.n[0] + i;
+        const int q = (k * a.n[1] + jj) * a.n[0] + i;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             const int n = a.n[ax];
             Eu[r][ax] = Ed[r][ax] = T(0);
             if (n <= 1) continue;
-            int up = cc[ax] + 1, dn = cc[ax] - 1;
-            if (a.per[ax]) {
-                up = up == n ? 0 : up;
-                dn = dn < 0 ? n - 1 : dn;
-            } else {
-                up = up > n - 1 ? n - 1 : up;
-                dn = dn < 0 ? 0 : dn;
-            }
-            Eu[r][ax] = E[q + (long long)(up - cc[ax]) * stride[ax]];
-            Ed[r][ax] = E[q + (long long)(dn - cc[ax]) * stride[ax]];
+            const AxisNb b =
+                ax == 2 ? nbz : axis_nb(ax == 0 ? i : jj, n, a.per[ax], ax == 0 ? 1 : a.n[0]);
+            Eu[r][ax] = E[q + b.hi];
+            Ed[r][ax] = E[q + b.lo];
         }
         Ec[r] = E[q];
         rho[r] = U[q];
