@@ -348,14 +348,14 @@ cudaError_t dispatch_tile(const MeshDesc& m, int kernel, int tile, const StageCa
 #ifdef HH_WS
             switch (tile) {
                 case 0: case 1: e = run_stage_ws<8>(m, td, c, s, used); break;
-                case 2: e = run_stage_ws<16>(m, td, c, s, used); break;
+                case 2: case 5: e = run_stage_ws<16>(m, td, c, s, used); break;
                 case 3: e = cudaSuccess; break;            // 64-wide tiles: no warp-per-row form
                 default: e = run_stage_ws<4>(m, td, c, s, used); break;
             }
 #else
             switch (tile) {
                 case 0: case 1: e = run_stage_tma<32, 8>(m, td, c, s, used); break;
-                case 2: e = run_stage_tma<32, 16>(m, td, c, s, used); break;
+                case 2: case 5: e = run_stage_tma<32, 16>(m, td, c, s, used); break;
                 case 3: e = run_stage_tma<64, 8>(m, td, c, s, used); break;
                 default: e = run_stage_tma<32, 4>(m, td, c, s, used); break;
             }
@@ -364,7 +364,7 @@ cudaError_t dispatch_tile(const MeshDesc& m, int kernel, int tile, const StageCa
         }
         switch (tile) {
             case 0: case 1: return run_stage<32, 8, 3, 0, 1>(m, td, c, s);
-            case 2: return run_stage<32, 16, 3, 0, 1>(m, td, c, s);
+            case 2: case 5: return run_stage<32, 16, 3, 0, 1>(m, td, c, s);
             case 3: return run_stage<64, 8, 3, 0, 1>(m, td, c, s);
             default: return run_stage<32, 4, 3, 0, 1>(m, td, c, s);
         }

@@ -44,12 +44,12 @@ struct StageCall {
 
 // Tile configurations per number of active axes (the autotuner's space).
 inline constexpr TileDesc TILES3[] = {{32, 8, 32}, {32, 8, 64}, {32, 16, 64}, {64, 8, 64},
-                                      {32, 4, 64}};
+                                      {32, 4, 64}, {32, 16, 32}};
 inline constexpr TileDesc TILES2[] = {{32, 8, 0}, {32, 16, 0}, {64, 8, 0}};
 inline constexpr TileDesc TILES1[] = {{128, 1, 0}, {256, 1, 0}};
 
 inline int tile_count(int dim) {
-    return dim == 3 ? 5 : dim == 2 ? 3 : dim == 1 ? 2 : 1;
+    return dim == 3 ? 6 : dim == 2 ? 3 : dim == 1 ? 2 : 1;
 }
 inline TileDesc tile_desc(int dim, int tile) {
     if (dim == 3) return TILES3[tile];

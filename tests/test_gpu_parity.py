@@ -110,7 +110,7 @@ def test_tiny_meshes_f64(shape):
         assert np.all(max_rel(got, g.step(U, dt)) <= F64_TOL)
 
 
-@pytest.mark.parametrize("tile", range(5))
+@pytest.mark.parametrize("tile", range(6))
 def test_every_3d_tile_f64(tile):
     shape = (67, 19, 70)
     gam = 5.0 / 3.0
