@@ -684,6 +684,25 @@ def main():
     # ---------------- the same workload end to end through the C ABI, host buffers ----------------
     Uh = torch.tensor(Ub).pin_memory()
     Uo = torch.empty_like(Uh).pin_memory()
+    Ud = torch.empty(Uh.shape, dtype=Uh.dtype, device=dev)
+    ev2 = torch.cuda.Event(enable_timing=True)
+
+    def copy_gbs():
+        # one copy of the state each way between the pinned buffers and the
+        # device, on their own (the host's pinned-memory copy rate varies:
+        # after other large jobs on the machine it was seen to start several
+        # times slower and recover within seconds)
+        barrier()
+        ev0.record(stream)
+        Ud.copy_(Uh, non_blocking=True)
+        ev1.record(stream)
+        Uo.copy_(Ud, non_blocking=True)
+        ev2.record(stream)
+        barrier()
+        return {"h2d": Uh.numel() * 4 / ev0.elapsed_time(ev1) / 1e6,
+                "d2h": Uo.numel() * 4 / ev1.elapsed_time(ev2) / 1e6}
+
+    copy_before = copy_gbs()
     m32.advance_host(Uh, 1, CFL, out=Uo)                 # warm the handle's device buffer
     barrier()
     e2e_runs, e2e_dev = [], []                           # three timed calls, the median reported
@@ -699,22 +718,7 @@ def main():
             e2e_runs.append(rank_max(time.perf_counter() - t0))
             e2e_dev.append(ev0.elapsed_time(ev1))
     e2e_s = sorted(e2e_runs)[1]
-    # the pinned-buffer copy bandwidth of this host (it sets the gap between
-    # this figure and the device-timed one, and differs between machines)
-    Ud = torch.empty(Uh.shape, dtype=Uh.dtype, device=dev)
-    Ud.copy_(Uh, non_blocking=True)
-    Uo.copy_(Ud, non_blocking=True)
-    barrier()
-    ev0.record(stream)
-    Ud.copy_(Uh, non_blocking=True)
-    ev1.record(stream)
-    Uo.copy_(Ud, non_blocking=True)
-    ev2 = torch.cuda.Event(enable_timing=True)
-    ev2.record(stream)
-    barrier()
-    copy_gbs = {"h2d": Uh.numel() * 4 / ev0.elapsed_time(ev1) / 1e6,
-                "d2h": Uo.numel() * 4 / ev1.elapsed_time(ev2) / 1e6}
-    del Ud
+    copy_after = copy_gbs()
     e2e = {"value": whole_job_value(world, cells, 2 * args.steps, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": Uh.numel() * 4 / args.steps,
            "d2h_bytes_per_step": Uo.numel() * 4 / args.steps,
@@ -723,9 +727,9 @@ def main():
                    "three calls",
            "seconds_per_call": e2e_runs,
            "device_ms_per_call": e2e_dev,               # the stream's span: copies and steps
-           "pinned_copy_gbs": copy_gbs,
+           "pinned_copy_gbs": {"before": copy_before, "after": copy_after},
            "clocks": clk_e2e.summary()}
-    del Uh, Uo, U, U0, m32
+    del Uh, Uo, Ud, U, U0, m32
 
     # ---------------- FP64 plain on the same workload ----------------
     m64 = hh.HardHydro(shape, GAMMA, hh.HARD_BC_REFLECT, dtype=torch.float64,
