@@ -71,7 +71,7 @@ enum {
     HARD_ECUDA = -3,         /* a CUDA runtime call failed                    */
     HARD_ENONPHYS = -4,      /* non-physical state met on the device          */
     HARD_ETIMEOUT = -5,      /* a bounded device wait ran out                 */
-    HARD_EUNSUPPORTED = -6   /* valid request this build does not support     */
+    HARD_EUNSUPPORTED = -6   /* valid request the library does not support   */
 };
 
 /* Create a handle for an nx x ny x nz mesh (each >= 1) on the unit box with
