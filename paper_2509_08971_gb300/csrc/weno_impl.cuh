@@ -69,7 +69,7 @@ cudaError_t run_weno_sweeps(const MeshDesc& m, const StageCall& c, cudaStream_t 
     const StageArgs<T> A = weno_args(m, WENO_SWEEP_CHUNK, c);
     T* L = static_cast<T*>(c.scratch);
     if (m.n[1] > 65535 || m.n[2] > 65535) return cudaErrorInvalidValue;
-    const dim3 gx(wcdiv(m.n[0], SWEEP_SEG), wcdiv(m.n[1], SWEEP_THREADS / 32), m.n[2]);
+    const dim3 gx(wcdiv(m.n[0], WX_SEG), wcdiv(m.n[1], SWEEP_THREADS / 32), m.n[2]);
     weno_x_kernel<T, 0><<<gx, SWEEP_THREADS, 0, s>>>(A, L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

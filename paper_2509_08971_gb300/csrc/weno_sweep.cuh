@@ -27,8 +27,10 @@
 
 namespace hh {
 
-constexpr int SWEEP_SEG = 30;                 // cells per warp in the x sweep
+constexpr int SWEEP_SEG = 30;                 // cells per warp in the advection x sweep
 constexpr int SWEEP_WIN = SWEEP_SEG + 6;      // its stencil window
+constexpr int WX_SEG = 62;                    // cells per warp in the stage's x sweep (two per lane)
+constexpr int WX_WIN = WX_SEG + 6;            // its stencil window
 constexpr int SWEEP_THREADS = WENO_SWEEP_THREADS;
 
 // Conserved -> primitive of cell m along kernel axis AX (extent nA, element
@@ -88,60 +90,71 @@ __device__ __forceinline__ void sweep_epilogue(const StageArgs<T>& A, bool bad, 
     }
 }
 
-// x sweep: one warp per 30-cell segment of a row (y', z' fixed); a block
-// takes one segment of four consecutive rows.  Writes L.
+// x sweep: one warp per 62-cell segment of a row (y', z' fixed), two cells
+// per lane; a block takes one segment of four consecutive rows.  Writes L.
 template <typename T, int PX>
 __global__ void __launch_bounds__(SWEEP_THREADS)
 weno_x_kernel(const StageArgs<T> A, T* __restrict__ L) {
-    __shared__ T win[SWEEP_THREADS / 32][NF][SWEEP_WIN];
+    __shared__ T win[SWEEP_THREADS / 32][NF][WX_WIN];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int n0 = A.n[0], n1 = A.n[1];
     // segment blockIdx.x of rows y' = 4 blockIdx.y + warp, z' = blockIdx.z
     const int yr = blockIdx.y * (SWEEP_THREADS / 32) + wq;
     const bool active = yr < n1;                       // warp-uniform
     const long long base = ((long long)blockIdx.z * n1 + (active ? yr : 0)) * n0;
-    const int xs = blockIdx.x * SWEEP_SEG;
+    const int xs = blockIdx.x * WX_SEG;
     const T gamma = A.gamma;
     const T gx = sizeof(T) == 4 ? A.igm1 : A.gm1;     // the HLL energy closure
     bool bad = false;                                  // reported by the combining sweep
 
-    // the window: cells xs-3 .. xs+32 (lane l loads cell xs-3+l, and lanes
-    // 0..3 also cell xs+29+l)
+    // the window: cells xs-3 .. xs+64 (lane l loads cells xs-3+l and
+    // xs+29+l, and lanes 0..3 also cell xs+61+l)
     {
         T W[NF];
-        sweep_load<T, 0, PX>(A, base, xs - 3 + lane, n0, 1, W, bad);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) win[wq][f][lane] = W[f];
-        if (lane < SWEEP_WIN - 32) {
-            sweep_load<T, 0, PX>(A, base, xs + 29 + lane, n0, 1, W, bad);
+        for (int h = 0; h < 2; ++h) {
+            sweep_load<T, 0, PX>(A, base, xs - 3 + 32 * h + lane, n0, 1, W, bad);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) win[wq][f][32 + lane] = W[f];
+            for (int f = 0; f < NF; ++f) win[wq][f][32 * h + lane] = W[f];
+        }
+        if (lane < WX_WIN - 64) {
+            sweep_load<T, 0, PX>(A, base, xs + 61 + lane, n0, 1, W, bad);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) win[wq][f][64 + lane] = W[f];
         }
     }
     __syncwarp();
-    // lane l: cell xs-1+l, its stencil win[l .. l+4]; its left face takes the
-    // left state from lane l-1
-    T rv[NF], lv[NF];
+    // lane l: cells c0 = xs-1+2l and c1 = c0+1, their stencils win[2l .. 2l+4]
+    // and win[2l+1 .. 2l+5]; the face left of c0 takes its left state from
+    // c1 of lane l-1, the face right of c1 is lane l+1's face left of its c0
+    T rv0[NF], lv0[NF], rv1[NF], lv1[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        const T* v = &win[wq][f][lane];
-        weno5z_pair(v[0], v[1], v[2], v[3], v[4], rv[f], lv[f]);
+        const T* v = &win[wq][f][2 * lane];
+        weno5z_pair(v[0], v[1], v[2], v[3], v[4], rv0[f], lv0[f]);
+        weno5z_pair(v[1], v[2], v[3], v[4], v[5], rv1[f], lv1[f]);
     }
-    T qL[NF], Fl[NF];
+    T qL[NF], Fl[NF], Fm[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) qL[f] = __shfl_up_sync(0xffffffffu, rv[f], 1);
-    hll_face<PX>(qL, lv, gamma, gx, Fl);
-    T D[NF];
+    for (int f = 0; f < NF; ++f) qL[f] = __shfl_up_sync(0xffffffffu, rv1[f], 1);
+    hll_face<PX>(qL, lv0, gamma, gx, Fl);              // face c0 - 1/2
+    hll_face<PX>(rv0, lv1, gamma, gx, Fm);             // face c0 + 1/2
+    T D0[NF], D1[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        const T Fr = __shfl_down_sync(0xffffffffu, Fl[f], 1);
-        D[f] = sub_over_dx(T(0), Fr - Fl[f], A.dxk[0]);
+        const T Fr = __shfl_down_sync(0xffffffffu, Fl[f], 1);   // face c1 + 1/2
+        D0[f] = sub_over_dx(T(0), Fm[f] - Fl[f], A.dxk[0]);
+        D1[f] = sub_over_dx(T(0), Fr - Fm[f], A.dxk[0]);
     }
-    const int x = xs - 1 + lane;
-    const bool owner = active && lane >= 1 && lane <= SWEEP_SEG && x < n0;
-    if (owner) {
+    // cells xs .. xs+61: c1 of lanes 0..30, c0 of lanes 1..31
+    const int x0 = xs - 1 + 2 * lane;
+    if (active && lane >= 1 && x0 < n0) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) L[f * A.N + base + x] = D[f];
+        for (int f = 0; f < NF; ++f) L[f * A.N + base + x0] = D0[f];
+    }
+    if (active && lane <= 30 && x0 + 1 < n0) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) L[f * A.N + base + x0 + 1] = D1[f];
     }
 }
 
