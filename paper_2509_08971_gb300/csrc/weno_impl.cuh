@@ -98,7 +98,7 @@ cudaError_t run_advect(const MeshDesc& m, const AdvectArgs<T>& A, cudaStream_t s
 // The three sweeps of one advection stage on a 3D mesh (weno_sweep.cuh).
 cudaError_t run_advect_sweeps(const MeshDesc& m, const AdvectArgs<T>& A, T* L, cudaStream_t s) {
     if (m.n[1] > 65535 || m.n[2] > 65535) return cudaErrorInvalidValue;
-    const dim3 gx(wcdiv(m.n[0], SWEEP_SEG), wcdiv(m.n[1], SWEEP_THREADS / 32), m.n[2]);
+    const dim3 gx(wcdiv(m.n[0], WX_SEG), wcdiv(m.n[1], SWEEP_THREADS / 32), m.n[2]);
     advect_x_kernel<T, 0><<<gx, SWEEP_THREADS, 0, s>>>(A, L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -12,10 +12,10 @@
 // The sweeps serve 3D meshes (1D and 2D meshes, small enough to be bound by
 // launch latency, keep the fused kernel).  Each sweep reconstructs the two
 // face values of every cell once (weno5z_pair) and evaluates every face's
-// HLL flux once.  The x sweep gives each warp a 30-cell segment of a row:
-// lane l holds cell x_s - 1 + l, the window of its five-cell stencils sits
-// in shared memory, and the face between two lanes takes its left state from
-// the lower lane by a shuffle.  The marches give each lane one x column and
+// HLL flux once.  The x sweep gives each warp a 62-cell segment of a row:
+// lane l holds cells x_s - 1 + 2l and x_s + 2l, the window of their
+// five-cell stencils sits in shared memory, and the face between two lanes
+// takes its left state from the lower lane by a shuffle.  The marches give each lane one x column and
 // walk the march axis with the five-cell stencil, the pending face state and
 // the last face flux in registers: no block barrier and no shared plane.
 // Against the fused kernel this moves L through HBM between the sweeps
@@ -27,10 +27,8 @@
 
 namespace hh {
 
-constexpr int SWEEP_SEG = 30;                 // cells per warp in the advection x sweep
-constexpr int SWEEP_WIN = SWEEP_SEG + 6;      // its stencil window
-constexpr int WX_SEG = 62;                    // cells per warp in the stage's x sweep (two per lane)
-constexpr int WX_WIN = WX_SEG + 6;            // its stencil window
+constexpr int WX_SEG = 62;                    // cells per warp in the x sweeps (two per lane)
+constexpr int WX_WIN = WX_SEG + 6;            // their stencil window
 constexpr int SWEEP_THREADS = WENO_SWEEP_THREADS;
 
 // Conserved -> primitive of cell m along kernel axis AX (extent nA, element
@@ -339,36 +337,44 @@ __device__ __forceinline__ void sweep_ev(const AdvectArgs<T>& A, long long base,
 template <typename T, int PX>
 __global__ void __launch_bounds__(SWEEP_THREADS)
 advect_x_kernel(const AdvectArgs<T> A, T* __restrict__ L) {
-    __shared__ T win[SWEEP_THREADS / 32][2][SWEEP_WIN];
+    __shared__ T win[SWEEP_THREADS / 32][2][WX_WIN];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int n0 = A.n[0], n1 = A.n[1];
     const int yr = blockIdx.y * (SWEEP_THREADS / 32) + wq;     // as in weno_x_kernel
     const bool active = yr < n1;
     const long long base = ((long long)blockIdx.z * n1 + (active ? yr : 0)) * n0;
-    const int xs = blockIdx.x * SWEEP_SEG;
+    const int xs = blockIdx.x * WX_SEG;
     {
         T e, u;
-        sweep_ev<T, 0, PX>(A, base, xs - 3 + lane, n0, 1, e, u);
-        win[wq][0][lane] = e;
-        win[wq][1][lane] = u;
-        if (lane < SWEEP_WIN - 32) {
-            sweep_ev<T, 0, PX>(A, base, xs + 29 + lane, n0, 1, e, u);
-            win[wq][0][32 + lane] = e;
-            win[wq][1][32 + lane] = u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            sweep_ev<T, 0, PX>(A, base, xs - 3 + 32 * h + lane, n0, 1, e, u);
+            win[wq][0][32 * h + lane] = e;
+            win[wq][1][32 * h + lane] = u;
+        }
+        if (lane < WX_WIN - 64) {
+            sweep_ev<T, 0, PX>(A, base, xs + 61 + lane, n0, 1, e, u);
+            win[wq][0][64 + lane] = e;
+            win[wq][1][64 + lane] = u;
         }
     }
     __syncwarp();
-    const T* ve = &win[wq][0][lane];
-    const T* vu = &win[wq][1][lane];
-    T er, el, ur, ul;
-    weno5z_pair(ve[0], ve[1], ve[2], ve[3], ve[4], er, el);
-    weno5z_pair(vu[0], vu[1], vu[2], vu[3], vu[4], ur, ul);
-    const T eL = __shfl_up_sync(0xffffffffu, er, 1), uL = __shfl_up_sync(0xffffffffu, ur, 1);
-    const T Fl = rusanov_e(eL, el, uL, ul);
-    const T Fr = __shfl_down_sync(0xffffffffu, Fl, 1);
-    const int x = xs - 1 + lane;
-    if (active && lane >= 1 && lane <= SWEEP_SEG && x < n0)
-        L[base + x] = sub_over_dx(T(0), Fr - Fl, A.dxk[0]);
+    // two cells per lane, as in weno_x_kernel
+    const T* ve = &win[wq][0][2 * lane];
+    const T* vu = &win[wq][1][2 * lane];
+    T er0, el0, ur0, ul0, er1, el1, ur1, ul1;
+    weno5z_pair(ve[0], ve[1], ve[2], ve[3], ve[4], er0, el0);
+    weno5z_pair(vu[0], vu[1], vu[2], vu[3], vu[4], ur0, ul0);
+    weno5z_pair(ve[1], ve[2], ve[3], ve[4], ve[5], er1, el1);
+    weno5z_pair(vu[1], vu[2], vu[3], vu[4], vu[5], ur1, ul1);
+    const T eL = __shfl_up_sync(0xffffffffu, er1, 1), uL = __shfl_up_sync(0xffffffffu, ur1, 1);
+    const T Fl = rusanov_e(eL, el0, uL, ul0);                   // face c0 - 1/2
+    const T Fm = rusanov_e(er0, el1, ur0, ul1);                 // face c0 + 1/2
+    const T Fr = __shfl_down_sync(0xffffffffu, Fl, 1);          // face c1 + 1/2
+    const int x0 = xs - 1 + 2 * lane;
+    if (active && lane >= 1 && x0 < n0) L[base + x0] = sub_over_dx(T(0), Fm - Fl, A.dxk[0]);
+    if (active && lane <= 30 && x0 + 1 < n0)
+        L[base + x0 + 1] = sub_over_dx(T(0), Fr - Fm, A.dxk[0]);
 }
 
 template <typename T, int AX, int PA, bool LAST>
